@@ -1,0 +1,196 @@
+"""Pins for the oracle's low-rank primitives and butterfly factorization."""
+import os
+
+import numpy as np
+import pytest
+
+from mbf_synth import complex_normal, sample_outputs
+from oracle import bf as B
+from oracle import direct as D
+from oracle import lowrank as LR
+from oracle import problem as P
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rand_lowrank(m, n, r, seed, decay=None):
+    rng = np.random.default_rng(seed)
+    U = np.linalg.qr(rng.standard_normal((m, r)) + 1j * rng.standard_normal((m, r)))[0]
+    V = np.linalg.qr(rng.standard_normal((n, r)) + 1j * rng.standard_normal((n, r)))[0]
+    s = np.logspace(0, -3, r) if decay is None else decay
+    return (U * s) @ V.conj().T, s
+
+
+# ---------------------------------------------------------------- §2.1
+
+
+def test_truncated_svd_eckart_young():
+    """2-norm error of the rank-r truncation equals sigma_{r+1}."""
+    A, s = _rand_lowrank(60, 40, 20, seed=1)
+    U0, sig, V0 = LR.truncated_svd(A, 7)
+    err = np.linalg.norm(A - (U0 * sig) @ V0.conj().T, 2)
+    assert abs(err - s[7]) < 1e-12
+
+
+def test_three_forms_reconstruct():
+    A, _ = _rand_lowrank(30, 25, 6, seed=2)
+    U0, s, V0 = LR.truncated_svd(A, 6)
+    U, S, V = LR.forms(U0, s, V0, 1)
+    assert np.allclose((U * S) @ V.conj().T, A, atol=1e-12)
+    for w in (2, 3):
+        U, _, V = LR.forms(U0, s, V0, w)
+        assert np.allclose(U @ V.conj().T, A, atol=1e-12)
+    # form 1 carries the singular values on both sides (eq. lowrank1)
+    U, S, V = LR.forms(U0, s, V0, 1)
+    assert np.allclose(np.linalg.norm(U, axis=0), s) and np.allclose(np.linalg.norm(V, axis=0), s)
+
+
+def test_svd_sampling_recovers_exact_low_rank():
+    A, s = _rand_lowrank(300, 250, 10, seed=3)
+    rng = np.random.default_rng(0)
+    U0, sig, V0 = LR.svd_sampling(lambda a, b: A[np.ix_(a, b)], 300, 250, 10, rng)
+    assert np.allclose(sig, s, rtol=1e-9)
+    assert np.abs((U0 * sig) @ V0.conj().T - A).max() < 1e-10
+
+
+def test_svd_matvec_recovers_exact_low_rank():
+    A, s = _rand_lowrank(200, 180, 12, seed=4)
+    rng = np.random.default_rng(0)
+    U0, sig, V0 = LR.svd_matvec(lambda C: A @ C, lambda R: A.conj().T @ R, 200, 180, 12, rng)
+    assert np.allclose(sig, s, rtol=1e-9)
+    assert np.abs((U0 * sig) @ V0.conj().T - A).max() < 1e-10
+
+
+def test_svd_sampling_near_optimal_on_kernel_block():
+    """On a smooth kernel block the sampled rank-r error is within a small factor of
+    the optimal sigma_{r+1}."""
+    n = 64
+    X, W = P.grid_x(n, 2), P.grid_omega(n, 2)
+    rows, cols = np.arange(0, 1024), np.arange(2048, 3072)
+    A = P.kernel_block(P.kernel_fio_iso, X, W, rows, cols)
+    s_opt = np.linalg.svd(A, compute_uv=False)
+    rng = np.random.default_rng(5)
+    U0, sig, V0 = LR.svd_sampling(lambda a, b: A[np.ix_(a, b)], 1024, 1024, 24, rng)
+    err = np.linalg.norm(A - (U0 * sig) @ V0.conj().T, 2)
+    assert err < 20 * s_opt[24]
+
+
+# ---------------------------------------------------------------- §2.3-2.4
+
+
+EXACT_CASES = [
+    ("dft", 8, 2, 2, 16, "none"),
+    ("dft", 16, 2, 4, 16, "none"),
+    ("fio_iso", 16, 2, 2, 64, "polar"),
+    ("fio_ellip", 16, 2, 4, 16, "polar"),
+    ("dft", 4, 3, 2, 64, "none"),
+]
+
+
+def _make(kern, n, d, L, r, tr, seed=7):
+    X, W = P.grid_x(n, d), P.grid_omega(n, d)
+    xt = P.uniform_tree(n, d, L)
+    wt = P.polar_tree(n, L) if tr == "polar" else P.uniform_tree(n, d, L)
+    fs = B.build(P.KERNELS[kern], X, W, xt, wt, r, seed=seed)
+    return X, W, fs
+
+
+@pytest.mark.parametrize("case", EXACT_CASES)
+def test_bf_exact_when_rank_covers_blocks(case):
+    """With r at least every block dimension each truncation is exact, so the
+    product of the factors of eq. (gbf) equals K to rounding."""
+    kern, n, d, L, r, tr = case
+    X, W, fs = _make(*case)
+    K = P.kernel_block(P.KERNELS[kern], X, W, np.arange(n ** d), np.arange(n ** d))
+    Kf = B.SparseBF(fs).dense()
+    assert np.abs(Kf - K).max() < 1e-12
+
+
+def test_bf_exact_dft_matches_closed_form():
+    X, W, fs = _make("dft", 16, 2, 4, 16, "none")
+    g = complex_normal(256, 3, seed=0)
+    u = B.SparseBF(fs).apply(g)
+    ref = D.dft_closed_form(g, 16, 2)
+    assert np.abs(u - ref).max() / np.abs(ref).max() < 1e-12
+
+
+@pytest.mark.parametrize("case", [("dft", 32, 2, 4, 6, "none"), ("fio_iso", 32, 2, 4, 8, "polar"),
+                                  ("dft", 8, 3, 2, 12, "none")])
+def test_bf_adjoint_identity(case):
+    """<K_f g, w> = <g, K_f^* w> for the truncated factors (any factors satisfy it)."""
+    X, W, fs = _make(*case)
+    sb = B.SparseBF(fs)
+    N = X.shape[0]
+    g = complex_normal(N, 2, seed=1)
+    w = complex_normal(N, 2, seed=2)
+    lhs = np.vdot(w, sb.apply(g))
+    rhs = np.vdot(sb.adjoint(w), g)
+    assert abs(lhs - rhs) <= 1e-13 * abs(lhs)
+
+
+def test_bf_apply_equals_dense_product():
+    """Brute force (N <= 1024): the sparse-chain apply equals the dense product of
+    the assembled factor matrices, for truncated factors and several RHS."""
+    X, W, fs = _make("fio_iso", 32, 2, 4, 8, "polar")
+    sb = B.SparseBF(fs)
+    Dn = sb.dense()
+    g = complex_normal(1024, 3, seed=4)
+    assert np.abs(sb.apply(g) - (Dn @ g.T).T).max() < 1e-12
+    w = complex_normal(1024, 2, seed=5)
+    assert np.abs(sb.adjoint(w) - (Dn.conj().T @ w.T).T).max() < 1e-12
+
+
+def test_bf_middle_level_structure():
+    """§2.3, Fig. 2 (N = 4^2, r = 1): M^h is the perfect-shuffle permutation (block
+    (i,j) nonzero only in its (j,i) sub-block) and U^h block diagonal with n x rn blocks."""
+    n, L, h = 4, 2, 1
+    X, W, fs = _make("dft", n, 2, L, 1, "none")
+    sb = B.SparseBF(fs)
+    M = sb.M.toarray()
+    pattern = np.zeros((16, 16), bool)
+    for i in range(4):
+        for j in range(4):
+            pattern[i * 4 + j, j * 4 + i] = True
+    assert np.array_equal(M != 0, pattern)
+    # U^1 = U^2 G^1: the 4 X-nodes at level 1 each own 4 rows and 4 columns (r n = 4)
+    U1 = (sb.UL @ sb.G[0]).toarray()
+    mask = np.zeros((16, 16), bool)
+    xperm = fs.x_perm
+    for i in range(4):
+        rows = xperm[4 * i:4 * i + 4]
+        mask[np.ix_(rows, range(4 * i, 4 * i + 4))] = True
+    assert not np.any(U1[~mask])
+
+
+def test_bf_factor_counts_and_nnz():
+    """Every level G^l holds c^L blocks of r x c r (§2.4, 'O(N) nonzero entries in
+    each G^l'); the algorithmic nnz counts them plus the leaves and S."""
+    X, W, fs = _make("dft", 64, 2, 4, 16, "none")
+    c, L, h = 4, 4, 2
+    assert [A.shape for A in fs.G] == [(16, 4, 4, 16, 4, 16), (64, 1, 4, 16, 4, 16)]
+    # 2 sides x 2 levels x 4^4 blocks of 16 x 64, leaves 4096 x 16 each side, S 256 x 16
+    expect = 2 * 2 * 256 * 16 * 64 + 2 * 4096 * 16 + 256 * 16
+    assert fs.nnz_algorithmic() == expect
+
+
+@pytest.mark.slow
+def test_bf_error_against_table_2():
+    """§3.3, Table 2: PBF-s on the Example-1 FIO at n = 64 (depth log2 n = 6).
+
+    Loose pin.  The error falls at least fourfold for 8 more ranks (the paper's
+    discussion of Tables 2/4 reports about tenfold); its level at a given r lies
+    within [1/5, 60] x Table 2 -- this construction is 20-40x above the printed
+    values at the same r and reaches the printed 7e-5 near r = 30."""
+    tab = np.loadtxt(os.path.join(GOLDEN, "table2_pbf_s.txt"))
+    n = 64
+    S = sample_outputs(n * n, 256, seed=1)
+    g = complex_normal(n * n, 1, seed=0)
+    X, W = P.grid_x(n, 2), P.grid_omega(n, 2)
+    u = D.direct_sum(P.kernel_fio_ellip, X, W, g, rows=S)
+    errs = {}
+    for r in (14, 22):
+        _, _, fs = _make("fio_ellip", n, 2, 6, r, "polar")
+        errs[r] = D.rel_err(B.SparseBF(fs).apply(g)[:, S], u)
+        paper = tab[(tab[:, 0] == n) & (tab[:, 1] == r), 2][0]
+        assert paper / 5 < errs[r] < paper * 60, (r, errs[r], paper)
+    assert 4 < errs[14] / errs[22] < 60
