@@ -1,0 +1,304 @@
+"""Benchmark of the butterfly-factorization apply on GB300.
+
+Default workload: 2-D FIO K = exp(2 pi i (x.xi + c(x)|xi|)), polar tree on Omega,
+n = 256 (N = 65,536), depth L = 6, rank r = 24, one right-hand side.  One *step*
+is one full apply u = K_f g (all stages: (V^L)^*, (H^l)^*, M^h, G^l, U^L) of one
+batch of synthetic input already resident in HBM.  Factors (about 420 MB of
+complex64) exceed the 129 MB L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle's FP64
+factor apply on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from mbf_synth import WORKLOADS, complex_normal  # noqa: E402
+
+METRIC = "MBF apply points·RHS/s & %HBM/TC roofline; serve p50/p99 at rel err ≤1e-4"
+UNIT = "points*RHS/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="mbf", choices=["mbf", "reference"])
+    p.add_argument("--workload", default="fio2_polar_n256_L6_r24")
+    p.add_argument("--nrhs", type=int, default=0, help="override the workload's RHS count")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("apply_simt.cu", "layout.hpp", "apply.hpp"):
+        with open(os.path.join(ROOT, "paper_1509_07925_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload, nrhs):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the
+    current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    ent = d.get(f"{workload}/nrhs{nrhs}")
+    if not ent or ent.get("kernel_hash") != kernel_source_hash():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def build_factors(bd, wl):
+    tree = {"none": bd.MBF_TREE_UNIFORM, "polar": bd.MBF_TREE_POLAR}[wl.transform]
+    return bd.HostFactors.build(wl.dim, wl.n, wl.L, wl.r, tree=tree, kernel=wl.kernel,
+                                seed=wl.seed_build)
+
+
+def oracle_apply_rate(hf, wl, nrhs, budget_s=15.0):
+    """Time the oracle's FP64 sparse factor apply (as it stands) on the same factors:
+    bounded by `budget_s` of CPU work.  Returns (points*RHS/s, sample text, threads)."""
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from gpu_util import export_factors  # noqa: WPS433
+    from oracle import bf as B
+    sb = B.SparseBF(export_factors(hf.arrays()))
+    g = complex_normal(wl.N, nrhs, seed=wl.seed_g)
+    sb.apply(g[:1])                           # warm-up
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        sb.apply(g)
+        reps += 1
+        if time.perf_counter() - t0 > budget_s or reps >= 50:
+            break
+    dt = (time.perf_counter() - t0) / reps
+    sample = f"{reps} FP64 sparse factor applies of {nrhs} RHS (N={wl.N}), scipy CSR"
+    return wl.N * nrhs / dt, sample, 1
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_1509_07925_gb300 import binding as bd
+    from paper_1509_07925_gb300 import buildlib
+    buildlib.build()
+    wl = WORKLOADS[args.workload]
+    nrhs = args.nrhs or wl.nrhs
+    hf = build_factors(bd, wl)
+    rates = []
+    for k in range(args.warmup + args.steps):
+        r, sample, cores = oracle_apply_rate(hf, wl, nrhs, budget_s=2.0)
+        if k >= args.warmup:
+            rates.append(r)
+    v = statistics.median(rates)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wl.N * nrhs / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic", "config": {"workload": wl.name, "n": wl.n, "N": wl.N, "L": wl.L,
+                                            "r": wl.r, "nrhs": nrhs, "tree": wl.transform,
+                                            "kernel": wl.kernel},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1509_07925_gb300 import binding as bd
+    from paper_1509_07925_gb300 import buildlib
+    if rank == 0:
+        buildlib.build()
+    if world > 1:
+        torch.distributed.barrier()
+    buildlib.build()
+    wl = WORKLOADS[args.workload]
+    nrhs = args.nrhs or wl.nrhs
+    N = wl.N
+    hf = build_factors(bd, wl)
+    op = bd.Operator(hf)
+    info = op.info()
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    g = torch.from_numpy(complex_normal(N, nrhs, seed=wl.seed_g).astype(np.complex64)).cuda()
+    u = torch.empty((nrhs, N), dtype=torch.complex64, device="cuda")
+    prec = bd.MBF_PREC_FP32_SIMT
+    for _ in range(max(3, args.warmup)):
+        op.apply(g.data_ptr(), u.data_ptr(), nrhs, prec, sp)
+    op.check(sp)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        op.apply(g.data_ptr(), u.data_ptr(), nrhs, prec, sp)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    op.check(sp)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    g_host = torch.from_numpy(complex_normal(N, nrhs, seed=wl.seed_g).astype(np.complex64)).pin_memory()
+    u_host = torch.empty((nrhs, N), dtype=torch.complex64).pin_memory()
+    import ctypes as C
+    lib = bd.lib()
+    for _ in range(2):
+        bd._check(lib.mbf_apply_host(op.handle, C.c_void_p(g_host.data_ptr()),
+                                     C.c_void_p(u_host.data_ptr()), nrhs, prec, C.c_void_p(sp)))
+    t0 = time.perf_counter()
+    n_e2e = max(3, args.steps // 2)
+    for _ in range(n_e2e):
+        bd._check(lib.mbf_apply_host(op.handle, C.c_void_p(g_host.data_ptr()),
+                                     C.c_void_p(u_host.data_ptr()), nrhs, prec, C.c_void_p(sp)))
+    e2e_s = (time.perf_counter() - t0) / n_e2e
+
+    value = world * N * nrhs / (ms * 1e-3)
+    peak, peak_kind = measured_peaks()
+    alg_bytes = info.bytes_algorithmic + 16 * N * nrhs
+    achieved = alg_bytes / (ms * 1e-3) / 1e9
+    traffic = recorded_traffic(wl.name, nrhs)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (complex64)", "data": "synthetic",
+        "config": {"workload": wl.name, "kernel": wl.kernel, "tree": wl.transform, "n": wl.n, "N": N,
+                   "L": wl.L, "r": wl.r, "nrhs": nrhs, "precision": "fp32_simt",
+                   "parallelism": f"replicas{world}",
+                   "l2": f"inputs larger than L2: packed factors {info.bytes_packed / 1e6:.0f} MB > 129 MB",
+                   "factor_bytes_algorithmic": info.bytes_algorithmic,
+                   "factor_bytes_packed": info.bytes_packed},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_kind": f"{peak_kind} hbm_gbs (burst copy)",
+                     "algorithmic_bytes_per_launch": alg_bytes},
+        "e2e": {"value": world * N * nrhs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * N * nrhs,
+                "d2h_bytes_per_step": 8 * N * nrhs},
+        "gpu_launches": args.steps,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            v, sample, cores = oracle_apply_rate(hf, wl, nrhs)
+            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                    "sample": sample}
+        except Exception as e:  # the baseline must not hide the GPU number
+            line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 0, "kind": "oracle",
+                                    "sample": f"failed: {e}"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    op.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,195 @@
+/*
+ * mbf.h -- C ABI of the GB300 butterfly-factorization apply library (libmbf.so).
+ *
+ * The library applies a multidimensional butterfly factorization (BF)
+ *     K ~ U^L G^{L-1} ... G^h M^h (H^h)^* ... (H^{L-1})^* (V^L)^*,   h = L/2,
+ * of a complementary low-rank kernel matrix K = (K(x, xi))_{x in X, xi in Omega}
+ * (Li, Yang & Ying, "Multidimensional Butterfly Factorization", §1.1 eq. (GBF),
+ * §2.3 eq. (gbf)) to vectors on one GPU, and its adjoint K^*.  Factors are built
+ * once on the host in FP64 (§2.3 middle level by SVD via random sampling, §2.1;
+ * §2.4 recursive factorization), packed into a per-level tile layout and kept
+ * resident in device memory.
+ *
+ * Conventions shared by every call:
+ *   - Points.  X = {(n_1/n, .., n_d/n)}, Omega = {(n_1, .., n_d) : -n/2 <= n_k < n/2}
+ *     (§1.1, eqs. X, Omega).  Natural index of x: sum_k n_k n^(d-1-k); of xi:
+ *     sum_k (xi_k + n/2) n^(d-1-k) (row-major).
+ *   - Vectors.  Complex single precision, interleaved (re, im) float pairs, laid out
+ *     [nrhs][N] in natural order.  Device pointers unless a call says "host".
+ *   - Ownership.  Callers own every buffer they pass; the library never frees them.
+ *     Handles returned by *_create / *_build own their memory until *_destroy.
+ *   - Errors.  Every call returns an mbf_status (MBF_OK = 0).  No exception crosses
+ *     the ABI.  mbf_last_error() returns a thread-local message for the last failure.
+ *   - Streams.  `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream.  Applies are asynchronous with respect to the host.
+ */
+#ifndef MBF_H
+#define MBF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum mbf_status {
+  MBF_OK = 0,
+  MBF_ERR_INVALID = 1,   /* bad argument, unsupported size or layout            */
+  MBF_ERR_OOM = 2,       /* host or device allocation failed                    */
+  MBF_ERR_CUDA = 3,      /* a CUDA runtime call failed                          */
+  MBF_ERR_BUSY = 4,      /* server has no free slot or memory budget right now  */
+  MBF_ERR_TIMEOUT = 5,   /* a device-side wait ran past its limit; see status   */
+  MBF_ERR_IO = 6,        /* factor file could not be read or written            */
+  MBF_ERR_NOT_FOUND = 7  /* unknown ticket                                      */
+} mbf_status;
+
+typedef enum mbf_tree_kind {
+  MBF_TREE_UNIFORM = 0,  /* Omega tree over the uniform grid (§2.2)                     */
+  MBF_TREE_POLAR = 1,    /* Omega tree over the polar image p(xi) in [0,1]^2 (§3.1-3.2)  */
+  MBF_TREE_SQUARE = 2    /* Omega tree over a square holding an explicit point subset,   */
+                         /* e.g. one corona Omega_t of the multiscale split (§4.2)        */
+} mbf_tree_kind;
+
+typedef enum mbf_precision {
+  MBF_PREC_AUTO = 0,     /* FP32 SIMT for nrhs < 8, split-BF16x3 tensor path otherwise */
+  MBF_PREC_FP32_SIMT = 1,/* complex64 factors, FP32 FMA, FP32 accumulate               */
+  MBF_PREC_TF32 = 2,     /* tensor cores, TF32-rounded operands, FP32 accumulate       */
+  MBF_PREC_BF16X3 = 3    /* tensor cores, split-BF16 (hi*hi + hi*lo + lo*hi), FP32 acc  */
+} mbf_precision;
+
+/* Problem description for the builder (§1.1 and §2.2). */
+typedef struct mbf_problem {
+  int32_t dim;          /* d = 2 or 3                                                   */
+  int32_t n;            /* grid points per axis, a power of two                          */
+  int32_t L;            /* tree depth: even, 2 <= L <= log2(n) for the X tree            */
+  int32_t r;            /* maximum rank r of every low-rank block                        */
+  int32_t tree;         /* mbf_tree_kind for the Omega side; the X tree is uniform        */
+  int32_t reserved0;
+  /* MBF_TREE_SQUARE only: the Omega points kept (natural indices, host, n_w entries)
+   * and the square [w_lo, w_lo + w_side)^d, in frequency units, that roots the tree. */
+  int64_t n_w;
+  const int64_t* w_index;
+  double w_lo;
+  double w_side;
+} mbf_problem_t;
+
+/* Kernel entry evaluation, Case (ii) of §1.1: fill the m x n block
+ *   out[2*(a + m*b) + 0/1] = Re/Im K(x_a, xi_b),  a < m, b < n  (column-major)
+ * x: host [m][dim] doubles in [0,1)^d; xi: host [n][dim] doubles (integer-valued).
+ * Called from several host threads at once; must be thread safe. */
+typedef void (*mbf_entry_fn)(const double* x, int64_t m, const double* xi, int64_t n,
+                             int32_t dim, double* out, void* ctx);
+
+/* Built-in kernels (ctx unused):
+ *  mbf_kernel_dft       exp(-2 pi i x.xi)                               (§1.1)
+ *  mbf_kernel_fio_iso   exp(2 pi i (x.xi + c(x)|xi|)),
+ *                       c(x) = (2 + sin 2pi x_1 sin 2pi x_2)/16           (§3.3, c_1 = c_2)
+ *  mbf_kernel_fio_ellip exp(2 pi i (x.xi + sqrt(c_1^2 xi_1^2 + c_2^2 xi_2^2))), eq. example1phi */
+void mbf_kernel_dft(const double* x, int64_t m, const double* xi, int64_t n, int32_t dim,
+                    double* out, void* ctx);
+void mbf_kernel_fio_iso(const double* x, int64_t m, const double* xi, int64_t n, int32_t dim,
+                        double* out, void* ctx);
+void mbf_kernel_fio_ellip(const double* x, int64_t m, const double* xi, int64_t n, int32_t dim,
+                          double* out, void* ctx);
+
+typedef struct mbf_build_opts {
+  uint64_t seed;        /* per-block generators are seeded from (seed, side, i, j)        */
+  int32_t sample_factor;/* sample sets of size sample_factor * r (default 3)              */
+  int32_t max_rounds;   /* representative-set iterations of §2.1 (default 3)              */
+  double tol;           /* drop singular values below tol * sigma_1 (default 1e-14)       */
+  int32_t threads;      /* host threads (0 = all cores)                                   */
+  int32_t reserved;
+} mbf_build_opts_t;
+
+/* Padded FP64 factor set: the interchange layout shared by the builder, the packer
+ * and factor import.  c = 2^dim, h = L/2.  Complex arrays are interleaved doubles.
+ * Blocks of one level share a padded rank R; entries beyond a block's true rank,
+ * or beyond a leaf's true point count, are zero.  Host memory throughout.
+ *   x_perm[n_out]  tree order -> natural index of X; x_off[c^L + 1] leaf offsets
+ *   w_perm[n_w]    tree order -> natural index into the input vector; w_off[c^L + 1]
+ *   RU[L+1], RV[L+1]  padded ranks of levels h..L on the X / Omega side (RU[h] == RV[h])
+ *   UL  [c^L][max_leaf_x][RU[L]]   rows of U^L_i (eq. expression-U at level L)
+ *   VL  [c^L][max_leaf_w][RV[L]]   rows of V^L_j
+ *   G[l-h]  [c^l][c^(L-l-1)][c][RU[l+1]][c][RU[l]]  : G[..][i][jp][t][k2][tp][k] is entry
+ *           (k2, k) of column block tp of G^l_{c i + t, jp} (eq. RSh2), l = h..L-1
+ *   H[l-h]  same shape with RV: blocks H^l_{c j + t, ip} of eq. (VF)
+ *   S   [c^h][c^h][RU[h]] real: diagonal of S^h_{i,j} (eq. Kij, form of eq. lowrank1) */
+typedef struct mbf_factors {
+  int32_t dim, L;
+  int64_t n_out, n_in, n_w;
+  const int64_t* x_perm;
+  const int64_t* x_off;
+  const int64_t* w_perm;
+  const int64_t* w_off;
+  const int32_t* RU;
+  const int32_t* RV;
+  int32_t max_leaf_x, max_leaf_w;
+  const double* UL;
+  const double* VL;
+  const double* const* G;
+  const double* const* H;
+  const double* S;
+  int64_t nnz;          /* algorithmic nonzeros (true ranks, no padding); 0 if unknown */
+} mbf_factors_t;
+
+typedef struct mbf_factors_s* mbf_factors_h;  /* host FP64 factors owned by the library */
+typedef struct mbf_op_s* mbf_op_t;            /* device-resident packed operator        */
+typedef struct mbf_server_s* mbf_server_t;    /* serving loop                           */
+
+/* Build the FP64 factors on the host (§2.3-2.4, Case (ii)); threads per opts.
+ * The builder keeps O(N log N) memory by recomputing each middle-level block for the
+ * V side instead of storing U^h, V^h (§2.5, interleaved construction). */
+mbf_status mbf_build_factors(const mbf_problem_t* prob, mbf_entry_fn fn, void* ctx,
+                             const mbf_build_opts_t* opts, mbf_factors_h* out);
+/* Read-only view of built factors (pointers valid until mbf_factors_destroy). */
+mbf_status mbf_factors_view(mbf_factors_h f, mbf_factors_t* view);
+mbf_status mbf_factors_destroy(mbf_factors_h f);
+
+/* Pack a factor set (built here or supplied by the caller) into the device tile
+ * layout on the current CUDA device and return a resident operator.  The factor
+ * arrays are only read during the call. */
+mbf_status mbf_op_create(const mbf_factors_t* f, mbf_op_t* out);
+/* mbf_build_factors + mbf_op_create + mbf_factors_destroy. */
+mbf_status mbf_build_from_entries(const mbf_problem_t* prob, mbf_entry_fn fn, void* ctx,
+                                  const mbf_build_opts_t* opts, mbf_op_t* out);
+mbf_status mbf_op_destroy(mbf_op_t op);
+
+typedef struct mbf_op_info {
+  int32_t dim, L, c, n_stages;
+  int64_t n_out, n_in;
+  int32_t RU[32], RV[32];
+  int64_t nnz_algorithmic;      /* nonzeros of the unpadded factors (the §2.5 apply cost) */
+  int64_t bytes_algorithmic;    /* 8 * nnz_algorithmic (complex64)                        */
+  int64_t bytes_packed;         /* device bytes of the packed tiles incl. padding         */
+  int64_t bytes_stage[32];      /* packed bytes streamed by each forward stage            */
+  int32_t grid, threads, smem;  /* persistent launch shape of the SIMT apply              */
+} mbf_op_info_t;
+mbf_status mbf_op_info(mbf_op_t op, mbf_op_info_t* info);
+
+/* u = K_f g (forward) for nrhs vectors.  g: device [nrhs][n_in] complex64, u: device
+ * [nrhs][n_out] complex64 (fully overwritten).  Asynchronous on `stream`.  Calls on
+ * one operator must not overlap on the device (they share its workspace); use the
+ * server, or several operators, for concurrent applies.  A device wait that runs
+ * out of time sets the operator's status word; mbf_op_check() reports it. */
+mbf_status mbf_apply(mbf_op_t op, const void* g, void* u, int64_t nrhs, int32_t precision,
+                     void* stream);
+/* g = K_f^* u (adjoint): the same factors conjugate-transposed in reverse order. */
+mbf_status mbf_apply_adjoint(mbf_op_t op, const void* u, void* g, int64_t nrhs,
+                             int32_t precision, void* stream);
+/* Same as mbf_apply but g and u are HOST buffers: copies in, applies, copies out,
+ * and synchronizes `stream` before returning. */
+mbf_status mbf_apply_host(mbf_op_t op, const void* g_host, void* u_host, int64_t nrhs,
+                          int32_t precision, void* stream);
+/* Synchronize `stream` and return MBF_ERR_TIMEOUT if a device wait of a previous
+ * apply on this operator ran out of time (and clear the flag), else MBF_OK. */
+mbf_status mbf_op_check(mbf_op_t op, void* stream);
+
+/* Thread-local text of the last error ("" if none). */
+const char* mbf_last_error(void);
+/* Library version string. */
+const char* mbf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MBF_H */

@@ -201,14 +201,13 @@ def leaf_matrix(A: np.ndarray, perm: np.ndarray, off: np.ndarray, n_points: int)
     """U^L (or V^L): block diagonal, block i = the leaf basis of leaf i, with rows
     placed at the natural indices of that leaf's points (eq. expression-U at l = L)."""
     n_leaves, mx, R = A.shape
-    i, a, k = np.meshgrid(np.arange(n_leaves), np.arange(mx), np.arange(R), indexing="ij")
+    i, a, k = np.nonzero(A)
     sizes = np.diff(off)
-    valid = a < sizes[i]
-    pos = np.where(valid, off[i] + a, 0)
-    rows = perm[pos]
+    keep = a < sizes[i]
+    i, a, k = i[keep], a[keep], k[keep]
+    rows = perm[off[i] + a]
     cols = i * R + k
-    vals = np.where(valid, A, 0)
-    return _coo(vals.ravel(), rows.ravel(), cols.ravel(), (n_points, n_leaves * R))
+    return _coo(A[i, a, k], rows, cols, (n_points, n_leaves * R))
 
 
 def transfer_matrix(A: np.ndarray, c: int, L: int, l: int):
@@ -216,13 +215,12 @@ def transfer_matrix(A: np.ndarray, c: int, L: int, l: int):
     columns of U^{l+1} -- and columns by (i, c jp + tp, k) -- the columns of U^l.
     Block (c i + t, i) is G^l_{c i + t} = blockdiag_jp(G^l_{c i + t, jp})."""
     ni, njp, _, R2, _, R1 = A.shape
-    i, jp, t, k2, tp, k = np.meshgrid(np.arange(ni), np.arange(njp), np.arange(c), np.arange(R2),
-                                      np.arange(c), np.arange(R1), indexing="ij")
+    i, jp, t, k2, tp, k = np.nonzero(A)
     B = c ** (L - l - 1)
     rows = ((c * i + t) * B + jp) * R2 + k2
     cols = (i * c ** (L - l) + c * jp + tp) * R1 + k
     n = c ** L
-    return _coo(A.ravel(), rows.ravel(), cols.ravel(), (n * R2, n * R1))
+    return _coo(A[i, jp, t, k2, tp, k], rows, cols, (n * R2, n * R1))
 
 
 def middle_matrix(S: np.ndarray, c: int, h: int):

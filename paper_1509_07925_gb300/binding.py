@@ -1,0 +1,274 @@
+"""ctypes binding of libmbf.so (argument marshalling only).
+
+Every name mirrors the C ABI of include/mbf.h.  The binding holds no arithmetic of
+the method: construction, packing and every apply run in the library (host FP64
+builder, sm_103a kernels).  Loading fails loudly if the library has not been
+built; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(_HERE, "_lib", "libmbf.so")
+
+MBF_OK, MBF_ERR_INVALID, MBF_ERR_OOM, MBF_ERR_CUDA, MBF_ERR_BUSY, MBF_ERR_TIMEOUT, MBF_ERR_IO, \
+    MBF_ERR_NOT_FOUND = range(8)
+MBF_TREE_UNIFORM, MBF_TREE_POLAR, MBF_TREE_SQUARE = 0, 1, 2
+MBF_PREC_AUTO, MBF_PREC_FP32_SIMT, MBF_PREC_TF32, MBF_PREC_BF16X3 = 0, 1, 2, 3
+
+_STATUS_NAMES = {0: "MBF_OK", 1: "MBF_ERR_INVALID", 2: "MBF_ERR_OOM", 3: "MBF_ERR_CUDA",
+                 4: "MBF_ERR_BUSY", 5: "MBF_ERR_TIMEOUT", 6: "MBF_ERR_IO", 7: "MBF_ERR_NOT_FOUND"}
+
+
+class MbfError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Problem(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("n", C.c_int32), ("L", C.c_int32), ("r", C.c_int32),
+                ("tree", C.c_int32), ("reserved0", C.c_int32), ("n_w", C.c_int64),
+                ("w_index", C.POINTER(C.c_int64)), ("w_lo", C.c_double), ("w_side", C.c_double)]
+
+
+class BuildOpts(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("sample_factor", C.c_int32), ("max_rounds", C.c_int32),
+                ("tol", C.c_double), ("threads", C.c_int32), ("reserved", C.c_int32)]
+
+
+class Factors(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("L", C.c_int32), ("n_out", C.c_int64), ("n_in", C.c_int64),
+                ("n_w", C.c_int64), ("x_perm", C.POINTER(C.c_int64)), ("x_off", C.POINTER(C.c_int64)),
+                ("w_perm", C.POINTER(C.c_int64)), ("w_off", C.POINTER(C.c_int64)),
+                ("RU", C.POINTER(C.c_int32)), ("RV", C.POINTER(C.c_int32)),
+                ("max_leaf_x", C.c_int32), ("max_leaf_w", C.c_int32),
+                ("UL", C.POINTER(C.c_double)), ("VL", C.POINTER(C.c_double)),
+                ("G", C.POINTER(C.POINTER(C.c_double))), ("H", C.POINTER(C.POINTER(C.c_double))),
+                ("S", C.POINTER(C.c_double)), ("nnz", C.c_int64)]
+
+
+class OpInfo(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("L", C.c_int32), ("c", C.c_int32), ("n_stages", C.c_int32),
+                ("n_out", C.c_int64), ("n_in", C.c_int64), ("RU", C.c_int32 * 32),
+                ("RV", C.c_int32 * 32), ("nnz_algorithmic", C.c_int64),
+                ("bytes_algorithmic", C.c_int64), ("bytes_packed", C.c_int64),
+                ("bytes_stage", C.c_int64 * 32), ("grid", C.c_int32), ("threads", C.c_int32),
+                ("smem", C.c_int32)]
+
+
+ENTRY_FN = C.CFUNCTYPE(None, C.POINTER(C.c_double), C.c_int64, C.POINTER(C.c_double), C.c_int64,
+                       C.c_int32, C.POINTER(C.c_double), C.c_void_p)
+
+# name -> (restype, argtypes); every entry point declared in include/mbf.h
+SIGNATURES = {
+    "mbf_build_factors": (C.c_int, [C.POINTER(Problem), C.c_void_p, C.c_void_p, C.POINTER(BuildOpts),
+                                    C.POINTER(C.c_void_p)]),
+    "mbf_factors_view": (C.c_int, [C.c_void_p, C.POINTER(Factors)]),
+    "mbf_factors_destroy": (C.c_int, [C.c_void_p]),
+    "mbf_op_create": (C.c_int, [C.POINTER(Factors), C.POINTER(C.c_void_p)]),
+    "mbf_build_from_entries": (C.c_int, [C.POINTER(Problem), C.c_void_p, C.c_void_p,
+                                         C.POINTER(BuildOpts), C.POINTER(C.c_void_p)]),
+    "mbf_op_destroy": (C.c_int, [C.c_void_p]),
+    "mbf_op_info": (C.c_int, [C.c_void_p, C.POINTER(OpInfo)]),
+    "mbf_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p]),
+    "mbf_apply_adjoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32,
+                                    C.c_void_p]),
+    "mbf_apply_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32,
+                                 C.c_void_p]),
+    "mbf_op_check": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "mbf_last_error": (C.c_char_p, []),
+    "mbf_version": (C.c_char_p, []),
+    "mbf_kernel_dft": (None, [C.POINTER(C.c_double), C.c_int64, C.POINTER(C.c_double), C.c_int64,
+                              C.c_int32, C.POINTER(C.c_double), C.c_void_p]),
+    "mbf_kernel_fio_iso": (None, [C.POINTER(C.c_double), C.c_int64, C.POINTER(C.c_double), C.c_int64,
+                                  C.c_int32, C.POINTER(C.c_double), C.c_void_p]),
+    "mbf_kernel_fio_ellip": (None, [C.POINTER(C.c_double), C.c_int64, C.POINTER(C.c_double),
+                                    C.c_int64, C.c_int32, C.POINTER(C.c_double), C.c_void_p]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libmbf.so (once).  Raises if it is missing: there is no CPU fallback."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIBPATH):
+            raise ImportError(f"{LIBPATH} not built; run __graft_entry__.build() first")
+        L = C.CDLL(LIBPATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(code):
+    if code != MBF_OK:
+        raise MbfError(code, lib().mbf_last_error().decode())
+
+
+def builtin_kernel(name: str):
+    """Address of a built-in entry function: 'dft', 'fio_iso' or 'fio_ellip'."""
+    fn = getattr(lib(), {"dft": "mbf_kernel_dft", "fio_iso": "mbf_kernel_fio_iso",
+                         "fio_ellip": "mbf_kernel_fio_ellip"}[name])
+    return C.cast(fn, C.c_void_p).value
+
+
+def _ptr(x, ctype):
+    return x.ctypes.data_as(C.POINTER(ctype))
+
+
+class HostFactors:
+    """Padded FP64 factor set in host memory: built by the library
+    (`build`) or supplied by the caller (`from_arrays`)."""
+
+    def __init__(self):
+        self._handle = None
+        self._keep = []
+        self.view = Factors()
+
+    @classmethod
+    def build(cls, dim, n, L, r, tree=MBF_TREE_UNIFORM, kernel="dft", seed=7, threads=0,
+              w_index=None, w_lo=0.0, w_side=0.0, sample_factor=3, max_rounds=3, tol=1e-14):
+        self = cls()
+        prob = Problem(dim=dim, n=n, L=L, r=r, tree=tree)
+        if w_index is not None:
+            wi = np.ascontiguousarray(w_index, dtype=np.int64)
+            self._keep.append(wi)
+            prob.n_w, prob.w_index, prob.w_lo, prob.w_side = wi.size, _ptr(wi, C.c_int64), w_lo, w_side
+        opts = BuildOpts(seed=seed, sample_factor=sample_factor, max_rounds=max_rounds, tol=tol,
+                         threads=threads)
+        fn = builtin_kernel(kernel) if isinstance(kernel, str) else kernel
+        h = C.c_void_p()
+        _check(lib().mbf_build_factors(C.byref(prob), fn, None, C.byref(opts), C.byref(h)))
+        self._handle = h
+        _check(lib().mbf_factors_view(h, C.byref(self.view)))
+        return self
+
+    @classmethod
+    def from_arrays(cls, d, L, n_out, n_in, x_perm, x_off, w_perm, w_off, RU, RV, UL, VL, G, H, S,
+                    nnz=0):
+        """Wrap caller arrays (numpy) in the mbf_factors_t layout of include/mbf.h."""
+        self = cls()
+        k = self._keep
+        c64 = lambda a: np.ascontiguousarray(a, dtype=np.complex128)
+        arrs = dict(x_perm=np.ascontiguousarray(x_perm, np.int64), x_off=np.ascontiguousarray(x_off, np.int64),
+                    w_perm=np.ascontiguousarray(w_perm, np.int64), w_off=np.ascontiguousarray(w_off, np.int64),
+                    RU=np.ascontiguousarray(RU, np.int32), RV=np.ascontiguousarray(RV, np.int32),
+                    UL=c64(UL), VL=c64(VL), S=np.ascontiguousarray(S, np.float64))
+        k.extend(arrs.values())
+        Gs = [c64(a) for a in G]
+        Hs = [c64(a) for a in H]
+        k.extend(Gs + Hs)
+        Gp = (C.POINTER(C.c_double) * len(Gs))(*[a.ctypes.data_as(C.POINTER(C.c_double)) for a in Gs])
+        Hp = (C.POINTER(C.c_double) * len(Hs))(*[a.ctypes.data_as(C.POINTER(C.c_double)) for a in Hs])
+        k.extend([Gp, Hp])
+        v = self.view
+        v.dim, v.L, v.n_out, v.n_in = d, L, n_out, n_in
+        v.n_w = arrs["w_perm"].size
+        v.x_perm, v.x_off = _ptr(arrs["x_perm"], C.c_int64), _ptr(arrs["x_off"], C.c_int64)
+        v.w_perm, v.w_off = _ptr(arrs["w_perm"], C.c_int64), _ptr(arrs["w_off"], C.c_int64)
+        v.RU, v.RV = _ptr(arrs["RU"], C.c_int32), _ptr(arrs["RV"], C.c_int32)
+        v.max_leaf_x, v.max_leaf_w = arrs["UL"].shape[1], arrs["VL"].shape[1]
+        v.UL = arrs["UL"].ctypes.data_as(C.POINTER(C.c_double))
+        v.VL = arrs["VL"].ctypes.data_as(C.POINTER(C.c_double))
+        v.G = C.cast(Gp, C.POINTER(C.POINTER(C.c_double)))
+        v.H = C.cast(Hp, C.POINTER(C.POINTER(C.c_double)))
+        v.S = _ptr(arrs["S"], C.c_double)
+        v.nnz = nnz
+        return self
+
+    # ---- read-only numpy views of the padded arrays (library-built factors)
+    def arrays(self):
+        v = self.view
+        d, L = v.dim, v.L
+        c, h = 2 ** d, L // 2
+        nL = c ** L
+        RU = np.ctypeslib.as_array(v.RU, shape=(L + 1,)).copy()
+        RV = np.ctypeslib.as_array(v.RV, shape=(L + 1,)).copy()
+
+        def carr(p, shape):
+            n = int(np.prod(shape))
+            return np.ctypeslib.as_array(p, shape=(2 * n,)).view(np.complex128).reshape(shape).copy()
+
+        out = dict(d=d, L=L, n_out=v.n_out, n_in=v.n_in,
+                   x_perm=np.ctypeslib.as_array(v.x_perm, shape=(v.n_out,)).copy(),
+                   x_off=np.ctypeslib.as_array(v.x_off, shape=(nL + 1,)).copy(),
+                   w_perm=np.ctypeslib.as_array(v.w_perm, shape=(v.n_w,)).copy(),
+                   w_off=np.ctypeslib.as_array(v.w_off, shape=(nL + 1,)).copy(), RU=RU, RV=RV,
+                   UL=carr(v.UL, (nL, v.max_leaf_x, RU[L])), VL=carr(v.VL, (nL, v.max_leaf_w, RV[L])),
+                   S=np.ctypeslib.as_array(v.S, shape=(c ** h * c ** h * RU[h],)).reshape(
+                       c ** h, c ** h, RU[h]).copy(), nnz=v.nnz)
+        out["G"] = [carr(v.G[q], (c ** l, c ** (L - l - 1), c, RU[l + 1], c, RU[l]))
+                    for q, l in enumerate(range(h, L))]
+        out["H"] = [carr(v.H[q], (c ** l, c ** (L - l - 1), c, RV[l + 1], c, RV[l]))
+                    for q, l in enumerate(range(h, L))]
+        return out
+
+    def close(self):
+        if self._handle is not None:
+            lib().mbf_factors_destroy(self._handle)
+            self._handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Operator:
+    """Device-resident packed factorization (mbf_op_t)."""
+
+    def __init__(self, factors: HostFactors):
+        self._h = C.c_void_p()
+        _check(lib().mbf_op_create(C.byref(factors.view), C.byref(self._h)))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> OpInfo:
+        inf = OpInfo()
+        _check(lib().mbf_op_info(self._h, C.byref(inf)))
+        return inf
+
+    def apply(self, g_ptr: int, u_ptr: int, nrhs: int, precision=MBF_PREC_AUTO, stream: int = 0):
+        """u = K_f g on device pointers (complex64, [nrhs][N])."""
+        _check(lib().mbf_apply(self._h, C.c_void_p(g_ptr), C.c_void_p(u_ptr), nrhs, precision,
+                               C.c_void_p(stream)))
+
+    def apply_adjoint(self, u_ptr: int, g_ptr: int, nrhs: int, precision=MBF_PREC_AUTO,
+                      stream: int = 0):
+        _check(lib().mbf_apply_adjoint(self._h, C.c_void_p(u_ptr), C.c_void_p(g_ptr), nrhs,
+                                       precision, C.c_void_p(stream)))
+
+    def apply_host(self, g: np.ndarray, nrhs: int, precision=MBF_PREC_AUTO, stream: int = 0):
+        """Host complex64 [nrhs][n_in] -> host complex64 [nrhs][n_out] (copies included)."""
+        inf = self.info()
+        g = np.ascontiguousarray(g, dtype=np.complex64)
+        u = np.empty((nrhs, inf.n_out), dtype=np.complex64)
+        _check(lib().mbf_apply_host(self._h, g.ctypes.data_as(C.c_void_p),
+                                    u.ctypes.data_as(C.c_void_p), nrhs, precision, C.c_void_p(stream)))
+        return u
+
+    def check(self, stream: int = 0):
+        _check(lib().mbf_op_check(self._h, C.c_void_p(stream)))
+
+    def close(self):
+        if self._h:
+            lib().mbf_op_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

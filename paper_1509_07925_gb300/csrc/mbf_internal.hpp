@@ -1,0 +1,90 @@
+// Internal declarations shared by the host translation units of libmbf.
+#pragma once
+
+#include <complex>
+#include <cstdint>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/mbf.h"
+
+namespace mbf {
+
+using cd = std::complex<double>;
+
+// Error carried to the C ABI boundary, where it becomes an mbf_status.
+struct Error : std::runtime_error {
+  mbf_status code;
+  Error(mbf_status c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+[[noreturn]] inline void fail(mbf_status c, const std::string& m) { throw Error(c, m); }
+void set_last_error(const std::string& m);
+
+// ---------------------------------------------------------------- trees (§2.2)
+// A Z-order tree of depth L stored as the permutation tree order -> point index
+// plus the c^L + 1 leaf offsets.  Node i of level l owns leaves
+// [i c^(L-l), (i+1) c^(L-l)) and the tree-order range [off[..], off[..]).
+struct Tree {
+  int d = 2, L = 0, c = 4;
+  std::vector<int64_t> perm;   // tree order -> natural index
+  std::vector<int64_t> off;    // leaf offsets
+  int64_t begin(int level, int64_t i) const { return off[i * ipow(c, L - level)]; }
+  int64_t end(int level, int64_t i) const { return off[(i + 1) * ipow(c, L - level)]; }
+  int64_t size(int level, int64_t i) const { return end(level, i) - begin(level, i); }
+  static int64_t ipow(int64_t b, int e) { int64_t r = 1; while (e-- > 0) r *= b; return r; }
+};
+Tree tree_uniform(int n, int d, int L);
+Tree tree_polar(int n, int L);
+Tree tree_square(const std::vector<double>& xi, const std::vector<int64_t>& index, int d,
+                 double lo, double side, int L);
+int64_t morton(const int64_t* cell, int d, int L);
+
+// ---------------------------------------------------------------- host factor set
+// Owning version of mbf_factors_t (same layout).
+struct FactorSet {
+  int d = 2, L = 0;
+  int64_t n_out = 0, n_in = 0, n_w = 0;
+  std::vector<int64_t> x_perm, x_off, w_perm, w_off;
+  std::vector<int32_t> RU, RV;
+  int32_t max_leaf_x = 1, max_leaf_w = 1;
+  std::vector<cd> UL, VL;
+  std::vector<std::vector<cd>> G, H;
+  std::vector<double> S;
+  int64_t nnz = 0;
+  std::vector<const double*> Gp, Hp;   // pointer tables for the view
+  mbf_factors_t view();
+};
+
+// ---------------------------------------------------------------- dense linear algebra
+// Column-major complex matrix.
+struct Mat {
+  int64_t m = 0, n = 0;
+  std::vector<cd> a;
+  Mat() = default;
+  Mat(int64_t m_, int64_t n_) : m(m_), n(n_), a(size_t(m_ * n_)) {}
+  cd& operator()(int64_t i, int64_t j) { return a[size_t(i + m * j)]; }
+  const cd& operator()(int64_t i, int64_t j) const { return a[size_t(i + m * j)]; }
+  cd* col(int64_t j) { return a.data() + m * j; }
+  const cd* col(int64_t j) const { return a.data() + m * j; }
+};
+Mat matmul(const Mat& A, const Mat& B);                 // A B
+Mat matmul_hn(const Mat& A, const Mat& B);              // A^* B
+Mat adjoint(const Mat& A);
+Mat rows_of(const Mat& A, const std::vector<int64_t>& rows);
+// Householder QR with column pivoting, stopped after kmax steps or when the
+// largest remaining column norm falls below tol * the first.  Returns pivots and,
+// if Q != nullptr, the first k orthonormal columns.
+std::vector<int64_t> pivoted_qr(const Mat& A, int64_t kmax, double tol, Mat* Q);
+// Hermitian eigendecomposition (cyclic Jacobi): A = V diag(w) V^*, w descending.
+void eig_herm(const Mat& A, std::vector<double>& w, Mat& V);
+// Thin SVD A = U diag(s) V^* (s descending) via one-sided Jacobi; small matrices.
+void svd_small(const Mat& A, Mat& U, std::vector<double>& s, Mat& V);
+// Moore-Penrose pseudo-inverse with relative cutoff rcond * s_max.
+Mat pinv(const Mat& A, double rcond);
+
+// ---------------------------------------------------------------- builder
+FactorSet build_factors(const mbf_problem_t& prob, mbf_entry_fn fn, void* ctx,
+                        const mbf_build_opts_t& opts);
+
+}  // namespace mbf

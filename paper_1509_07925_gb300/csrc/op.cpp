@@ -1,0 +1,560 @@
+// Packer, resident operator and the C ABI of libmbf.
+//
+// The packer turns a padded FP64 factor set into the stage/item/chunk layout of
+// layout.hpp: complex64 tiles with split real/imaginary planes, 128-byte aligned,
+// the tree permutations kept as int32 index tables that the kernels fold into
+// their leaf loads and stores, and M^h folded into the columns of the first G
+// block (G^h_{c i + t, jp} diag(S^h_{i, c jp + tp}), §2.3 and eq. RSh2).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "apply.hpp"
+#include "mbf_internal.hpp"
+
+struct mbf_factors_s {
+  mbf::FactorSet fs;
+};
+
+struct mbf_op_s {
+  int device = 0;
+  int d = 2, c = 4, L = 0, h = 0;
+  int64_t n_out = 0, n_in = 0, n_w = 0;
+  std::vector<int32_t> RU, RV;
+  mbf::Plan plan{};
+  int64_t nnz = 0, bytes_packed = 0;
+  int64_t positions = 0;            // longest coefficient vector (c^L max R)
+  uint8_t* d_arena = nullptr;
+  mbf::Item* d_items = nullptr;
+  int32_t *d_x_perm = nullptr, *d_x_off = nullptr, *d_w_perm = nullptr, *d_w_off = nullptr;
+  float2 *d_buf0 = nullptr, *d_buf1 = nullptr;
+  unsigned* d_barrier = nullptr;
+  int* d_status = nullptr;
+  int grid = 0, ns[5] = {0, 0, 0, 0, 0};
+  size_t smem[5] = {0, 0, 0, 0, 0};
+  // staging for mbf_apply_host
+  float2 *d_stage_in = nullptr, *d_stage_out = nullptr;
+  size_t stage_in_bytes = 0, stage_out_bytes = 0;
+};
+
+namespace mbf {
+
+namespace {
+thread_local std::string g_last_error;
+
+void cuda_check(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) fail(MBF_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+template <class T>
+T* dev_upload(const std::vector<T>& v, const char* what) {
+  T* p = nullptr;
+  const size_t bytes = std::max<size_t>(sizeof(T), v.size() * sizeof(T));
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) fail(MBF_ERR_OOM, std::string("cudaMalloc ") + what + ": " + cudaGetErrorString(e));
+  if (!v.empty()) cuda_check(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice), what);
+  return p;
+}
+
+int64_t ipow(int64_t b, int e) { return Tree::ipow(b, e); }
+
+struct Packer {
+  const mbf_factors_t& f;
+  int d, c, L, h;
+  std::vector<uint8_t> arena;
+  std::vector<Item> items;
+
+  explicit Packer(const mbf_factors_t& fa) : f(fa) {}
+
+  // Append one item: `nlines` lines of `len` entries, value(line, e) -> complex.
+  template <class F>
+  Item add_item(int nlines, int len, uint8_t kind, uint8_t t, F value) {
+    Item it{};
+    size_t off = (arena.size() + 127) & ~size_t(127);
+    arena.resize(off, 0);
+    it.offset = off;
+    it.nlines = uint16_t(nlines);
+    it.len = uint16_t(len);
+    it.lpc = uint16_t(lines_per_chunk(len));
+    it.kind = kind;
+    it.t = t;
+    const int64_t bytes = item_bytes(nlines, len, it.lpc);
+    arena.resize(off + size_t(bytes), 0);
+    uint8_t* p = arena.data() + off;
+    for (int l0 = 0; l0 < nlines; l0 += it.lpc) {
+      const int nl = std::min<int>(it.lpc, nlines - l0);
+      float* re = reinterpret_cast<float*>(p);
+      float* im = re + pad4(int64_t(nl) * len);
+      for (int l = 0; l < nl; ++l)
+        for (int e = 0; e < len; ++e) {
+          const cd v = value(l0 + l, e);
+          re[l * len + e] = float(v.real());
+          im[l * len + e] = float(v.imag());
+        }
+      p += chunk_bytes(nl, len);
+    }
+    return it;
+  }
+
+  void run(mbf_op_s& op) {
+    d = f.dim;
+    L = f.L;
+    c = 1 << d;
+    h = L / 2;
+    const int64_t nL = ipow(c, L);
+    const int32_t* RU = f.RU;
+    const int32_t* RV = f.RV;
+    auto cplx = [](const double* a, int64_t i) { return cd(a[2 * i], a[2 * i + 1]); };
+    Plan& plan = op.plan;
+    plan = Plan{};
+    plan.c = c;
+    plan.d = d;
+    plan.L = L;
+    int ns = 0;
+    auto begin_stage = [&](int level, int side) -> Stage& {
+      Stage& st = plan.st[ns++];
+      st.level = level;
+      st.side = side;
+      st.n_groups = int32_t(ipow(c, L - 1));
+      st.B = int32_t(ipow(c, L - level - 1));
+      st.ch = int32_t(ipow(c, h));
+      st.item_base = int64_t(items.size());
+      return st;
+    };
+    // ---- H-stages l = L-1 .. h: (H^l)^*, the first one fused with (V^L)^*
+    for (int l = L - 1; l >= h; --l) {
+      Stage& st = begin_stage(l, 1);
+      const int R2 = RV[l + 1], R1 = RV[l];
+      st.R_in = R2;
+      st.R_out = R1;
+      st.in_pat = l == L - 1 ? PAT_LEAF : PAT_SPLIT;
+      st.out_pat = PAT_CONTIG;
+      const bool leaves = l == L - 1;
+      st.n_items = leaves ? c + 1 : 1;
+      st.main_idx = leaves ? c : 0;
+      const double* Hl = f.H[l - h];
+      const size_t a0 = arena.size();
+      for (int64_t g = 0; g < st.n_groups; ++g) {
+        if (leaves) {
+          for (int t = 0; t < c; ++t) {
+            const int64_t leaf = c * g + t;
+            const int np = int(f.w_off[leaf + 1] - f.w_off[leaf]);
+            items.push_back(add_item(np, RV[L], ITEM_LEAF_W, uint8_t(t), [&](int b, int k) {
+              return std::conj(cplx(f.VL, (leaf * f.max_leaf_w + b) * RV[L] + k));
+            }));
+          }
+        }
+        // T[(tp,k)][(t,k2)] = conj(H^l_{c j + t, ip}[k2][(tp,k)]), lines = (t,k2)
+        items.push_back(add_item(c * R2, c * R1, ITEM_MAIN, 0, [&](int line, int e) {
+          const int t = line / R2, k2 = line % R2, tp = e / R1, k = e % R1;
+          return std::conj(cplx(Hl, ((((g * c + t) * R2 + k2) * c + tp) * R1) + k));
+        }));
+      }
+      st.bytes = int64_t(arena.size() - a0);
+    }
+    // ---- G-stages l = h .. L-1: G^l, the first with M^h folded in, the last fused with U^L
+    for (int l = h; l < L; ++l) {
+      Stage& st = begin_stage(l, 0);
+      const int R1 = RU[l], R2 = RU[l + 1];
+      st.R_in = R1;
+      st.R_out = R2;
+      st.in_pat = l == h ? PAT_CORNER : PAT_CONTIG;
+      st.out_pat = l == L - 1 ? PAT_LEAF : PAT_SPLIT;
+      const bool leaves = l == L - 1;
+      st.n_items = leaves ? c + 1 : 1;
+      st.main_idx = 0;
+      const double* Gl = f.G[l - h];
+      const int64_t B = st.B, ch = st.ch;
+      const size_t a0 = arena.size();
+      for (int64_t g = 0; g < st.n_groups; ++g) {
+        const int64_t i = g / B, jp = g % B;
+        items.push_back(add_item(c * R1, c * R2, ITEM_MAIN, 0, [&](int line, int e) {
+          const int tp = line / R1, k = line % R1, t = e / R2, k2 = e % R2;
+          cd v = cplx(Gl, ((((g * c + t) * R2 + k2) * c + tp) * R1) + k);
+          if (l == h) v *= f.S[(i * ch + (c * jp + tp)) * R1 + k];
+          return v;
+        }));
+        if (leaves) {
+          for (int t = 0; t < c; ++t) {
+            const int64_t leaf = c * g + t;
+            const int np = int(f.x_off[leaf + 1] - f.x_off[leaf]);
+            items.push_back(add_item(np, RU[L], ITEM_LEAF_X, uint8_t(t), [&](int a, int k) {
+              return cplx(f.UL, (leaf * f.max_leaf_x + a) * RU[L] + k);
+            }));
+          }
+        }
+      }
+      st.bytes = int64_t(arena.size() - a0);
+    }
+    plan.n_stages = ns;
+    (void)nL;
+  }
+};
+
+void validate(const mbf_factors_t& f) {
+  if (f.dim != 2 && f.dim != 3) fail(MBF_ERR_INVALID, "dim must be 2 or 3");
+  if (f.L < 2 || f.L % 2 || f.L > 20) fail(MBF_ERR_INVALID, "L must be even, 2..20");
+  const int c = 1 << f.dim, h = f.L / 2;
+  if (2 * (f.L - h) > kMaxStages) fail(MBF_ERR_INVALID, "too many stages");
+  if (!f.x_perm || !f.x_off || !f.w_perm || !f.w_off || !f.RU || !f.RV || !f.UL || !f.VL || !f.G ||
+      !f.H || !f.S)
+    fail(MBF_ERR_INVALID, "factor set has a NULL array");
+  if (f.RU[h] != f.RV[h]) fail(MBF_ERR_INVALID, "RU[h] must equal RV[h]");
+  for (int l = h; l <= f.L; ++l) {
+    if (f.RU[l] < 1 || f.RV[l] < 1) fail(MBF_ERR_INVALID, "ranks must be >= 1");
+    if (int64_t(c) * f.RU[l] > kMaxLen || int64_t(c) * f.RV[l] > kMaxLen)
+      fail(MBF_ERR_INVALID, "c * rank exceeds " + std::to_string(kMaxLen));
+  }
+  if (f.max_leaf_x > kMaxLeaf || f.max_leaf_w > kMaxLeaf)
+    fail(MBF_ERR_INVALID, "leaf with more than " + std::to_string(kMaxLeaf) + " points");
+  const int64_t nL = Tree::ipow(c, f.L);
+  if (f.x_off[0] != 0 || f.x_off[nL] != f.n_out) fail(MBF_ERR_INVALID, "x_off must span n_out");
+  if (f.w_off[0] != 0 || f.w_off[nL] != f.n_w) fail(MBF_ERR_INVALID, "w_off must span n_w");
+  for (int64_t q = 0; q < nL; ++q) {
+    if (f.x_off[q + 1] - f.x_off[q] > f.max_leaf_x || f.x_off[q + 1] < f.x_off[q])
+      fail(MBF_ERR_INVALID, "x_off inconsistent with max_leaf_x");
+    if (f.w_off[q + 1] - f.w_off[q] > f.max_leaf_w || f.w_off[q + 1] < f.w_off[q])
+      fail(MBF_ERR_INVALID, "w_off inconsistent with max_leaf_w");
+  }
+  std::vector<char> seen(size_t(f.n_out), 0);
+  for (int64_t q = 0; q < f.n_out; ++q) {
+    const int64_t v = f.x_perm[q];
+    if (v < 0 || v >= f.n_out || seen[size_t(v)]) fail(MBF_ERR_INVALID, "x_perm is not a permutation");
+    seen[size_t(v)] = 1;
+  }
+  std::vector<char> seenw(size_t(f.n_in), 0);
+  for (int64_t q = 0; q < f.n_w; ++q) {
+    const int64_t v = f.w_perm[q];
+    if (v < 0 || v >= f.n_in || seenw[size_t(v)]) fail(MBF_ERR_INVALID, "w_perm: index out of range or repeated");
+    seenw[size_t(v)] = 1;
+  }
+  if (f.n_out > INT32_MAX || f.n_in > INT32_MAX) fail(MBF_ERR_INVALID, "too many points");
+}
+
+// Host check of the packed plan, run before any device work: every gather and
+// scatter the kernels will do stays inside the coefficient workspace, the positions
+// each stage writes are exactly those the next stage reads (so forward and adjoint
+// never read an unwritten entry), and every item lies inside the arena with the
+// shape its stage expects.
+void check_plan(const Plan& plan, const std::vector<Item>& items, size_t arena_bytes, int64_t positions,
+                const mbf_factors_t& f) {
+  const int c = plan.c;
+  std::vector<char> wrote, read;
+  for (int e = 0; e < plan.n_stages; ++e) {
+    const Stage& st = plan.st[e];
+    std::vector<char> rd(size_t(positions), 0), wr(size_t(positions), 0);
+    auto mark = [&](int pat, int R, std::vector<char>& bm) {
+      if (pat == PAT_LEAF) return;
+      for (int64_t g = 0; g < st.n_groups; ++g)
+        for (int t = 0; t < c; ++t) {
+          const int64_t a = g / st.B, b = g % st.B;
+          int64_t off;
+          if (pat == PAT_SPLIT) off = ((c * a + t) * st.B + b) * R;
+          else if (pat == PAT_CONTIG) off = (int64_t(c) * g + t) * R;
+          else off = ((c * b + t) * int64_t(st.ch) + a) * R;
+          if (off < 0 || off + R > positions) fail(MBF_ERR_INVALID, "plan: vector offset out of range");
+          for (int k = 0; k < R; ++k) {
+            if (bm[size_t(off + k)]) fail(MBF_ERR_INVALID, "plan: position touched twice in one stage");
+            bm[size_t(off + k)] = 1;
+          }
+        }
+    };
+    mark(st.in_pat, st.R_in, rd);
+    mark(st.out_pat, st.R_out, wr);
+    if (e > 0 && st.in_pat != PAT_LEAF && rd != wrote)
+      fail(MBF_ERR_INVALID, "plan: stage reads differ from the previous stage's writes");
+    wrote = wr;
+    const int64_t nL = Tree::ipow(c, plan.L);
+    for (int64_t g = 0; g < st.n_groups; ++g)
+      for (int m = 0; m < st.n_items; ++m) {
+        const Item& it = items[size_t(st.item_base + g * st.n_items + m)];
+        if (it.offset % 128 || it.offset + size_t(item_bytes(it.nlines, it.len, it.lpc)) > arena_bytes)
+          fail(MBF_ERR_INVALID, "plan: item outside the arena");
+        if (chunk_bytes(std::min<int64_t>(it.lpc, std::max<int64_t>(it.nlines, 1)), it.len) > kSlotBytes)
+          fail(MBF_ERR_INVALID, "plan: chunk larger than a pipeline slot");
+        const int64_t leaf = c * g + it.t;
+        if (it.kind == ITEM_MAIN) {
+          if (it.nlines != c * st.R_in || it.len != c * st.R_out) fail(MBF_ERR_INVALID, "plan: main block shape");
+        } else if (it.kind == ITEM_LEAF_W) {
+          if (st.in_pat != PAT_LEAF || leaf >= nL || it.len != st.R_in ||
+              it.nlines != f.w_off[leaf + 1] - f.w_off[leaf])
+            fail(MBF_ERR_INVALID, "plan: Omega leaf item");
+        } else if (it.kind == ITEM_LEAF_X) {
+          if (st.out_pat != PAT_LEAF || leaf >= nL || it.len != st.R_out ||
+              it.nlines != f.x_off[leaf + 1] - f.x_off[leaf])
+            fail(MBF_ERR_INVALID, "plan: X leaf item");
+        } else {
+          fail(MBF_ERR_INVALID, "plan: unknown item kind");
+        }
+      }
+  }
+}
+
+void op_free(mbf_op_s* op) {
+  if (!op) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(op->device);
+  cudaFree(op->d_arena);
+  cudaFree(op->d_items);
+  cudaFree(op->d_x_perm);
+  cudaFree(op->d_x_off);
+  cudaFree(op->d_w_perm);
+  cudaFree(op->d_w_off);
+  cudaFree(op->d_buf0);
+  cudaFree(op->d_buf1);
+  cudaFree(op->d_barrier);
+  cudaFree(op->d_status);
+  cudaFree(op->d_stage_in);
+  cudaFree(op->d_stage_out);
+  cudaSetDevice(prev);
+  delete op;
+}
+
+mbf_op_s* op_create(const mbf_factors_t& f) {
+  validate(f);
+  auto* op = new mbf_op_s();
+  try {
+    op->d = f.dim;
+    op->c = 1 << f.dim;
+    op->L = f.L;
+    op->h = f.L / 2;
+    op->n_out = f.n_out;
+    op->n_in = f.n_in;
+    op->n_w = f.n_w;
+    op->RU.assign(f.RU, f.RU + f.L + 1);
+    op->RV.assign(f.RV, f.RV + f.L + 1);
+    op->nnz = f.nnz;
+    Packer pk(f);
+    pk.run(*op);
+    op->bytes_packed = int64_t(pk.arena.size());
+    int64_t rmax = 1;
+    for (int l = op->h; l <= op->L; ++l) rmax = std::max<int64_t>({rmax, op->RU[size_t(l)], op->RV[size_t(l)]});
+    op->positions = Tree::ipow(op->c, op->L) * rmax;
+    check_plan(op->plan, pk.items, pk.arena.size(), op->positions, f);
+    // ---- device side
+    cuda_check(cudaGetDevice(&op->device), "cudaGetDevice");
+    op->d_arena = dev_upload(pk.arena, "factor arena");
+    op->d_items = dev_upload(pk.items, "item table");
+    auto to32 = [](const int64_t* p, int64_t n) {
+      std::vector<int32_t> v(static_cast<size_t>(n));
+      for (int64_t q = 0; q < n; ++q) v[size_t(q)] = int32_t(p[q]);
+      return v;
+    };
+    const int64_t nL = Tree::ipow(op->c, op->L);
+    op->d_x_perm = dev_upload(to32(f.x_perm, f.n_out), "x_perm");
+    op->d_x_off = dev_upload(to32(f.x_off, nL + 1), "x_off");
+    op->d_w_perm = dev_upload(to32(f.w_perm, std::max<int64_t>(f.n_w, 1)), "w_perm");
+    op->d_w_off = dev_upload(to32(f.w_off, nL + 1), "w_off");
+    const size_t vbytes = size_t(op->positions) * 4 * sizeof(float2);
+    if (cudaMalloc(&op->d_buf0, vbytes) != cudaSuccess || cudaMalloc(&op->d_buf1, vbytes) != cudaSuccess)
+      fail(MBF_ERR_OOM, "cudaMalloc workspace");
+    if (cudaMalloc(&op->d_barrier, 256) != cudaSuccess || cudaMalloc(&op->d_status, 256) != cudaSuccess)
+      fail(MBF_ERR_OOM, "cudaMalloc barrier");
+    cuda_check(cudaMemset(op->d_status, 0, 256), "cudaMemset status");
+    for (int nrb : {1, 2, 4}) cuda_check(simt_config(nrb, &op->grid, &op->ns[nrb], &op->smem[nrb]), "simt_config");
+  } catch (...) {
+    op_free(op);
+    throw;
+  }
+  return op;
+}
+
+void apply_impl(mbf_op_s* op, const void* in, void* out, int64_t nrhs, int32_t precision, void* stream,
+                bool adj) {
+  if (!op) fail(MBF_ERR_INVALID, "operator is NULL");
+  if (nrhs < 0) fail(MBF_ERR_INVALID, "nrhs < 0");
+  if (nrhs == 0) return;
+  if ((!in || !out)) fail(MBF_ERR_INVALID, "NULL vector");
+  if (precision != MBF_PREC_AUTO && precision != MBF_PREC_FP32_SIMT)
+    fail(MBF_ERR_INVALID, "precision not available on this path");
+  if (nrhs > (int64_t(1) << 24)) fail(MBF_ERR_INVALID, "nrhs too large");
+  const int nrb = nrhs >= 4 ? 4 : (nrhs >= 2 ? 2 : 1);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ApplyArgs a{};
+  a.arena = op->d_arena;
+  a.items = op->d_items;
+  a.x_perm = op->d_x_perm;
+  a.x_off = op->d_x_off;
+  a.w_perm = op->d_w_perm;
+  a.w_off = op->d_w_off;
+  a.in = static_cast<const float2*>(in);
+  a.out = static_cast<float2*>(out);
+  a.in_len = adj ? op->n_out : op->n_in;
+  a.out_len = adj ? op->n_in : op->n_out;
+  a.buf0 = op->d_buf0;
+  a.buf1 = op->d_buf1;
+  a.barrier = op->d_barrier;
+  a.status = op->d_status;
+  a.nrhs = int32_t(nrhs);
+  a.n_pass = int32_t((nrhs + nrb - 1) / nrb);
+  a.n_slots = op->ns[nrb];
+  a.plan = op->plan;
+  if (adj && op->n_w < op->n_in)
+    cuda_check(cudaMemsetAsync(out, 0, size_t(nrhs) * size_t(op->n_in) * sizeof(float2), st), "cudaMemsetAsync");
+  cuda_check(launch_apply_simt(a, nrb, adj, op->grid, op->smem[nrb], st), "apply launch");
+}
+
+template <class F>
+mbf_status guard(F&& fn) {
+  try {
+    fn();
+    g_last_error.clear();
+    return MBF_OK;
+  } catch (const Error& e) {
+    g_last_error = e.what();
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    g_last_error = "host allocation failed";
+    return MBF_ERR_OOM;
+  } catch (const std::exception& e) {
+    g_last_error = e.what();
+    return MBF_ERR_INVALID;
+  }
+}
+
+}  // namespace
+
+void set_last_error(const std::string& m) { g_last_error = m; }
+
+}  // namespace mbf
+
+using namespace mbf;
+
+extern "C" {
+
+const char* mbf_last_error(void) { return g_last_error.c_str(); }
+const char* mbf_version(void) { return "mbf-gb300 0.1 (sm_103a)"; }
+
+mbf_status mbf_build_factors(const mbf_problem_t* prob, mbf_entry_fn fn, void* ctx,
+                             const mbf_build_opts_t* opts, mbf_factors_h* out) {
+  return guard([&] {
+    if (!prob || !out) fail(MBF_ERR_INVALID, "NULL argument");
+    mbf_build_opts_t o{};
+    if (opts) o = *opts;
+    auto* h = new mbf_factors_s();
+    try {
+      h->fs = build_factors(*prob, fn, ctx, o);
+    } catch (...) {
+      delete h;
+      throw;
+    }
+    *out = h;
+  });
+}
+
+mbf_status mbf_factors_view(mbf_factors_h f, mbf_factors_t* view) {
+  return guard([&] {
+    if (!f || !view) fail(MBF_ERR_INVALID, "NULL argument");
+    *view = f->fs.view();
+  });
+}
+
+mbf_status mbf_factors_destroy(mbf_factors_h f) {
+  return guard([&] { delete f; });
+}
+
+mbf_status mbf_op_create(const mbf_factors_t* f, mbf_op_t* out) {
+  return guard([&] {
+    if (!f || !out) fail(MBF_ERR_INVALID, "NULL argument");
+    *out = op_create(*f);
+  });
+}
+
+mbf_status mbf_build_from_entries(const mbf_problem_t* prob, mbf_entry_fn fn, void* ctx,
+                                  const mbf_build_opts_t* opts, mbf_op_t* out) {
+  return guard([&] {
+    if (!prob || !out) fail(MBF_ERR_INVALID, "NULL argument");
+    mbf_build_opts_t o{};
+    if (opts) o = *opts;
+    FactorSet fs = build_factors(*prob, fn, ctx, o);
+    mbf_factors_t v = fs.view();
+    *out = op_create(v);
+  });
+}
+
+mbf_status mbf_op_destroy(mbf_op_t op) {
+  return guard([&] { op_free(op); });
+}
+
+mbf_status mbf_op_info(mbf_op_t op, mbf_op_info_t* info) {
+  return guard([&] {
+    if (!op || !info) fail(MBF_ERR_INVALID, "NULL argument");
+    std::memset(info, 0, sizeof(*info));
+    info->dim = op->d;
+    info->L = op->L;
+    info->c = op->c;
+    info->n_stages = op->plan.n_stages;
+    info->n_out = op->n_out;
+    info->n_in = op->n_in;
+    for (int l = 0; l <= op->L && l < 32; ++l) {
+      info->RU[l] = op->RU[size_t(l)];
+      info->RV[l] = op->RV[size_t(l)];
+    }
+    info->nnz_algorithmic = op->nnz;
+    info->bytes_algorithmic = 8 * op->nnz;
+    info->bytes_packed = op->bytes_packed;
+    for (int s = 0; s < op->plan.n_stages && s < 32; ++s) info->bytes_stage[s] = op->plan.st[s].bytes;
+    info->grid = op->grid;
+    info->threads = kThreads;
+    info->smem = int(op->smem[1]);
+  });
+}
+
+mbf_status mbf_apply(mbf_op_t op, const void* g, void* u, int64_t nrhs, int32_t precision, void* stream) {
+  return guard([&] { apply_impl(op, g, u, nrhs, precision, stream, false); });
+}
+
+mbf_status mbf_apply_adjoint(mbf_op_t op, const void* u, void* g, int64_t nrhs, int32_t precision,
+                             void* stream) {
+  return guard([&] { apply_impl(op, u, g, nrhs, precision, stream, true); });
+}
+
+mbf_status mbf_apply_host(mbf_op_t op, const void* g_host, void* u_host, int64_t nrhs, int32_t precision,
+                          void* stream) {
+  return guard([&] {
+    if (!op || !g_host || !u_host) fail(MBF_ERR_INVALID, "NULL argument");
+    if (nrhs <= 0) return;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t in_b = size_t(nrhs) * size_t(op->n_in) * sizeof(float2);
+    const size_t out_b = size_t(nrhs) * size_t(op->n_out) * sizeof(float2);
+    if (in_b > op->stage_in_bytes) {
+      cuda_check(cudaStreamSynchronize(st), "sync");
+      cudaFree(op->d_stage_in);
+      op->d_stage_in = nullptr;
+      if (cudaMalloc(&op->d_stage_in, in_b) != cudaSuccess) fail(MBF_ERR_OOM, "cudaMalloc staging");
+      op->stage_in_bytes = in_b;
+    }
+    if (out_b > op->stage_out_bytes) {
+      cuda_check(cudaStreamSynchronize(st), "sync");
+      cudaFree(op->d_stage_out);
+      op->d_stage_out = nullptr;
+      if (cudaMalloc(&op->d_stage_out, out_b) != cudaSuccess) fail(MBF_ERR_OOM, "cudaMalloc staging");
+      op->stage_out_bytes = out_b;
+    }
+    cuda_check(cudaMemcpyAsync(op->d_stage_in, g_host, in_b, cudaMemcpyHostToDevice, st), "H2D");
+    apply_impl(op, op->d_stage_in, op->d_stage_out, nrhs, precision, stream, false);
+    cuda_check(cudaMemcpyAsync(u_host, op->d_stage_out, out_b, cudaMemcpyDeviceToHost, st), "D2H");
+    cuda_check(cudaStreamSynchronize(st), "sync");
+  });
+}
+
+mbf_status mbf_op_check(mbf_op_t op, void* stream) {
+  return guard([&] {
+    if (!op) fail(MBF_ERR_INVALID, "NULL operator");
+    cuda_check(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)), "cudaStreamSynchronize");
+    int st = 0;
+    cuda_check(cudaMemcpy(&st, op->d_status, sizeof(int), cudaMemcpyDeviceToHost), "read status");
+    if (st != ST_OK) {
+      cuda_check(cudaMemset(op->d_status, 0, sizeof(int)), "clear status");
+      static const char* names[] = {"ok", "grid barrier", "full mbarrier", "empty mbarrier", "bad item"};
+      fail(MBF_ERR_TIMEOUT, std::string("device wait gave up: ") + (st >= 0 && st <= 4 ? names[st] : "unknown"));
+    }
+  });
+}
+
+}  // extern "C"
