@@ -83,10 +83,11 @@ def test_adjoint_identity_on_gpu(ops):
 
 
 def test_exact_bf_equals_closed_form_dft(ops):
-    """Full-rank factors: the GPU apply equals the closed-form DFT to FP32 accuracy."""
-    op, fs, sb = ops(("dft", 8, 3, 2, 16, "none"))
+    """Full-rank factors (r covers every block of the 4^3 grid): the GPU apply equals
+    the closed-form 3-D DFT to FP32 accuracy."""
+    op, fs, sb = ops(("dft", 4, 3, 2, 64, "none"))
     g = complex_normal(fs.n_in, 2, seed=5)
-    ref = D.dft_closed_form(g, 8, 3)
+    ref = D.dft_closed_form(g, 4, 3)
     assert rel(gpu_apply(torch, op, g), ref) <= TOL_SIMT
 
 
