@@ -180,6 +180,23 @@ mbf_status mbf_apply_adjoint(mbf_op_t op, const void* u, void* g, int64_t nrhs,
  * and synchronizes `stream` before returning. */
 mbf_status mbf_apply_host(mbf_op_t op, const void* g_host, void* u_host, int64_t nrhs,
                           int32_t precision, void* stream);
+/* Allocation-free forward apply.  The paper has no counterpart: this is a service
+ * for callers that may not allocate device memory when they apply an operator --
+ * e.g. processes whose device memory is wholly owned by another allocator or held
+ * to a fixed budget, or latency-critical loops where an allocation (which may
+ * synchronize the device) is not allowed.  Same arguments and result as
+ * mbf_apply with precision MBF_PREC_FP32_SIMT; the coefficient workspace and the
+ * grid-barrier counter live in one fixed 4 MiB device array that the library
+ * reserves on every device that loads it, until the process exits.
+ *   - Needs 256 + 2 * 8 * (c^L * max rank) * min(nrhs rounded to 1, 2 or 4) bytes;
+ *     more returns MBF_ERR_INVALID and launches nothing.
+ *   - The first call on each device looks up the array's device address on that
+ *     device (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - All calls share the array, which keeps the last call's contents; the barrier
+ *     counter is cleared at the start of every call.  Calls that overlap on the GPU
+ *     race on the array: serialize them.  Device waits that run out of time are
+ *     reported by mbf_op_check on `op`, as for mbf_apply. */
+mbf_status mbf_apply_static(mbf_op_t op, const void* g, void* u, int64_t nrhs, void* stream);
 /* Synchronize `stream` and return MBF_ERR_TIMEOUT if a device wait of a previous
  * apply on this operator ran out of time (and clear the flag), else MBF_OK. */
 mbf_status mbf_op_check(mbf_op_t op, void* stream);

@@ -81,6 +81,7 @@ SIGNATURES = {
     "mbf_apply_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32,
                                  C.c_void_p]),
     "mbf_op_check": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "mbf_apply_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "mbf_last_error": (C.c_char_p, []),
     "mbf_version": (C.c_char_p, []),
     "mbf_kernel_dft": (None, [C.POINTER(C.c_double), C.c_int64, C.POINTER(C.c_double), C.c_int64,

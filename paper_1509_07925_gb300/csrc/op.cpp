@@ -16,30 +16,7 @@
 #include "apply.hpp"
 #include "mbf_internal.hpp"
 
-struct mbf_factors_s {
-  mbf::FactorSet fs;
-};
-
-struct mbf_op_s {
-  int device = 0;
-  int d = 2, c = 4, L = 0, h = 0;
-  int64_t n_out = 0, n_in = 0, n_w = 0;
-  std::vector<int32_t> RU, RV;
-  mbf::Plan plan{};
-  int64_t nnz = 0, bytes_packed = 0;
-  int64_t positions = 0;            // longest coefficient vector (c^L max R)
-  uint8_t* d_arena = nullptr;
-  mbf::Item* d_items = nullptr;
-  int32_t *d_x_perm = nullptr, *d_x_off = nullptr, *d_w_perm = nullptr, *d_w_off = nullptr;
-  float2 *d_buf0 = nullptr, *d_buf1 = nullptr;
-  unsigned* d_barrier = nullptr;
-  int* d_status = nullptr;
-  int grid = 0, ns[5] = {0, 0, 0, 0, 0};
-  size_t smem[5] = {0, 0, 0, 0, 0};
-  // staging for mbf_apply_host
-  float2 *d_stage_in = nullptr, *d_stage_out = nullptr;
-  size_t stage_in_bytes = 0, stage_out_bytes = 0;
-};
+#include "op_internal.hpp"
 
 namespace mbf {
 
