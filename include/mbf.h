@@ -188,8 +188,9 @@ mbf_status mbf_apply_host(mbf_op_t op, const void* g_host, void* u_host, int64_t
  * mbf_apply with precision MBF_PREC_FP32_SIMT; the coefficient workspace and the
  * grid-barrier counter live in one fixed 4 MiB device array that the library
  * reserves on every device that loads it, until the process exits.
- *   - Needs 256 + 2 * 8 * (c^L * max rank) * min(nrhs rounded to 1, 2 or 4) bytes;
- *     more returns MBF_ERR_INVALID and launches nothing.
+ *   - Needs 256 + 4 * (stages * c^(L-1)) (rounded up to 256) + stages * 8 * (c^L * max
+ *     rank) * (RHS per pass: 1, 2 or 4) bytes, stages = 2 (L - L/2) + 1; more returns
+ *     MBF_ERR_INVALID and launches nothing.
  *   - The first call on each device looks up the array's device address on that
  *     device (cudaGetSymbolAddress); make that first call before any stream capture.
  *   - All calls share the array, which keeps the last call's contents; the barrier

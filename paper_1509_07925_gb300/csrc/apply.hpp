@@ -19,9 +19,10 @@ struct ApplyArgs {
   const float2* in;        // forward: g [nrhs][n_in]; adjoint: u [nrhs][n_out]
   float2* out;             // forward: u; adjoint: g
   int64_t in_len, out_len;
-  float2* buf0;            // ping-pong coefficient vectors [pos][NRB]
-  float2* buf1;
-  unsigned int* barrier;   // zeroed before every launch
+  float2* bufs;            // stage e writes bufs + e * buf_stride ([pos][NRB]); stage e+1 reads it
+  int64_t buf_stride;
+  unsigned int* counters;  // [stage][group]: input segments written so far (zeroed per launch)
+  unsigned int* barrier;   // grid barrier between passes (zeroed per launch)
   int* status;             // 0 = ok; nonzero = a device wait ran out of time (sticky)
   int32_t nrhs, n_pass, n_slots, pad_;
   Plan plan;
@@ -32,12 +33,16 @@ enum DeviceStatus : int {
   ST_BARRIER_TIMEOUT = 1,
   ST_FULL_TIMEOUT = 2,
   ST_EMPTY_TIMEOUT = 3,
-  ST_BAD_ITEM = 4
+  ST_BAD_ITEM = 4,
+  ST_DEP_TIMEOUT = 5
 };
 
 size_t simt_smem_bytes(int nrb, int ns);
+int simt_threads(int nrb);
 cudaError_t simt_config(int nrb, int* grid, int* ns, size_t* smem);
 cudaError_t launch_apply_simt(const ApplyArgs& a, int nrb, bool adj, int grid, size_t smem,
                               cudaStream_t stream);
+// Bytes of dependency counters for a plan (S stages x groups, rounded up to 256).
+size_t counter_bytes(const Plan& plan);
 
 }  // namespace mbf

@@ -10,9 +10,10 @@
 // resident operator using only memory the library reserved when it was loaded.
 //
 // Limits and sharing: the array holds kStaticScratchBytes (4 MiB) on every device
-// that loads the library, for the life of the process.  A call needs 256 bytes plus
-// two coefficient vectors of (c^L * max rank) entries for each of up to 4 RHS per
-// pass; larger needs are rejected with MBF_ERR_INVALID.  Every call on a device
+// that loads the library, for the life of the process.  A call needs 256 bytes, one
+// dependency counter per group of every stage, and one coefficient vector of
+// (c^L * max rank) entries per stage for each of up to 4 RHS per pass; larger needs
+// are rejected with MBF_ERR_INVALID.  Every call on a device
 // shares the one array and leaves its contents behind; the barrier counter is
 // cleared at the start of each call.  Calls that overlap on the GPU (on different
 // streams, or with an mbf_apply_static on another operator) race on the array.
@@ -61,7 +62,8 @@ void apply_static_impl(mbf_op_s* op, const void* g, void* u, int64_t nrhs, void*
   if (nrhs > (int64_t(1) << 24)) mbf::fail(MBF_ERR_INVALID, "nrhs too large");
   const int nrb = nrhs >= 4 ? 4 : (nrhs >= 2 ? 2 : 1);
   const size_t vec_bytes = size_t(op->positions) * size_t(nrb) * sizeof(float2);
-  const size_t need = kBarrierBytes + 2 * vec_bytes;
+  const size_t sync_bytes = kBarrierBytes + mbf::counter_bytes(op->plan);
+  const size_t need = sync_bytes + size_t(op->plan.n_stages) * vec_bytes;
   if (need > kStaticScratchBytes)
     mbf::fail(MBF_ERR_INVALID, "operator needs " + std::to_string(need) + " bytes of scratch for " +
                                    std::to_string(nrb) + " RHS per pass; the static scratch holds " +
@@ -89,9 +91,10 @@ void apply_static_impl(mbf_op_s* op, const void* g, void* u, int64_t nrhs, void*
   a.out = static_cast<float2*>(u);
   a.in_len = op->n_in;
   a.out_len = op->n_out;
-  a.barrier = reinterpret_cast<unsigned*>(base);                       // cleared by the launch
-  a.buf0 = reinterpret_cast<float2*>(base + kBarrierBytes);
-  a.buf1 = reinterpret_cast<float2*>(base + kBarrierBytes + vec_bytes);
+  a.barrier = reinterpret_cast<unsigned*>(base);            // barrier + counters, cleared by the launch
+  a.counters = a.barrier + kBarrierBytes / sizeof(unsigned);
+  a.bufs = reinterpret_cast<float2*>(base + sync_bytes);     // one vector per stage
+  a.buf_stride = op->positions * nrb;
   a.status = op->d_status;
   a.nrhs = int32_t(nrhs);
   a.n_pass = int32_t((nrhs + nrb - 1) / nrb);

@@ -3,7 +3,7 @@
 // large |xi| keep full relative accuracy.
 #include <cmath>
 
-#include "../../include/mbf.h"
+#include "mbf.h"
 
 namespace {
 constexpr double kTwoPi = 6.283185307179586476925286766559;

@@ -23,13 +23,11 @@
 
 namespace mbf {
 
-constexpr int kSlotBytes = 16384;      // one pipeline slot = one chunk at most
+constexpr int kSlotBytes = 8192;       // one pipeline slot = one chunk at most
 constexpr int kMaxStages = 24;
 constexpr int kMaxLen = 256;           // longest line (c R) the consumers handle
 constexpr int kMaxLeaf = 1024;         // most points in one leaf
-constexpr int kConsumerWarps = 8;
-constexpr int kConsumers = kConsumerWarps * 32;
-constexpr int kThreads = kConsumers + 32;   // + one producer warp
+constexpr int kMaxChunkLines = 256;   // lines per chunk (bounds the per-chunk leaf gather)
 constexpr uint64_t kTimeoutNs = 2000000000ull;   // 2 s limit on every device-side wait
 
 enum Pattern : int32_t {
@@ -42,17 +40,19 @@ enum Pattern : int32_t {
 enum ItemKind : uint8_t {
   ITEM_MAIN = 0,    // lines = forward inputs, len = forward outputs (column-major)
   ITEM_LEAF_W = 1,  // (V^L_j)^*: lines = Omega points (inputs), len = R_L
-  ITEM_LEAF_X = 2   // U^L_i: lines = X points (outputs), len = R_L (row-major)
+  ITEM_LEAF_X = 2   // U^L_i of the group's c leaves: lines = R_L columns, len = the points
 };
 
 struct Item {            // 16 bytes
-  uint64_t offset;       // bytes into the arena, 128-byte aligned
+  uint32_t off128;       // offset into the arena in units of 128 bytes
+  int32_t base;          // leaf items: first tree-order point of the leaf; else 0
   uint16_t nlines;
   uint16_t len;
   uint16_t lpc;          // lines per chunk
   uint8_t kind;
   uint8_t t;             // child index of a leaf item
 };
+constexpr int kMaxGroupPoints = 256;   // points of the c leaves of one group
 
 struct Stage {
   int32_t n_groups, n_items, main_idx;
@@ -60,6 +60,7 @@ struct Stage {
   int32_t R_in, R_out;       // forward sense segment lengths
   int32_t B, ch;             // c^(L-l-1), c^h
   int32_t level, side;       // factor level l; side 0 = G (X tree), 1 = H (Omega tree)
+  int32_t leaf_only, pad_;   // 1: the stage applies only the (V^L)^* leaf products
   int64_t item_base;         // items of group g start at item_base + g * n_items
   int64_t bytes;             // packed bytes streamed by this stage
 };
@@ -73,6 +74,7 @@ MBF_HD int64_t pad4(int64_t x) { return (x + 3) & ~int64_t(3); }
 MBF_HD int64_t chunk_bytes(int64_t nl, int64_t len) { return 2 * pad4(nl * len) * 4; }
 MBF_HD int64_t lines_per_chunk(int64_t len) {
   int64_t l = (kSlotBytes / 8 - 4) / len;
+  if (l > kMaxChunkLines) l = kMaxChunkLines;
   return l < 1 ? 1 : l;
 }
 MBF_HD int64_t item_bytes(int64_t nlines, int64_t len, int64_t lpc) {

@@ -7,7 +7,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/mbf.h"
+#include "mbf.h"
 
 namespace mbf {
 

@@ -52,8 +52,9 @@ struct Packer {
   Item add_item(int nlines, int len, uint8_t kind, uint8_t t, F value) {
     Item it{};
     size_t off = (arena.size() + 127) & ~size_t(127);
+    if (off / 128 > UINT32_MAX) fail(MBF_ERR_INVALID, "factor arena larger than 512 GB");
     arena.resize(off, 0);
-    it.offset = off;
+    it.off128 = uint32_t(off / 128);
     it.nlines = uint16_t(nlines);
     it.len = uint16_t(len);
     it.lpc = uint16_t(lines_per_chunk(len));
@@ -102,29 +103,46 @@ struct Packer {
       st.item_base = int64_t(items.size());
       return st;
     };
-    // ---- H-stages l = L-1 .. h: (H^l)^*, the first one fused with (V^L)^*
+    // ---- leaf stage: (V^L_j)^* for the c leaves of each group, written to the
+    // coefficient vector of level L (leaf j at position j * RV[L])
+    {
+      Stage& st = begin_stage(L, 1);
+      st.B = 1;
+      st.R_in = RV[L];
+      st.R_out = RV[L];
+      st.in_pat = PAT_LEAF;
+      st.out_pat = PAT_CONTIG;
+      st.n_items = 1;
+      st.main_idx = -1;
+      st.leaf_only = 1;
+      const size_t a0 = arena.size();
+      for (int64_t g = 0; g < st.n_groups; ++g) {
+        // all points of the group's c leaves in one item: line = a point (tree order),
+        // entry k = column k of its leaf's V^L
+        const int64_t p0 = f.w_off[c * g], p1 = f.w_off[c * g + c];
+        items.push_back(add_item(int(p1 - p0), RV[L], ITEM_LEAF_W, 0, [&](int b, int k) {
+          int64_t leaf = c * g;
+          while (f.w_off[leaf + 1] <= p0 + b) ++leaf;
+          const int64_t row = p0 + b - f.w_off[leaf];
+          return std::conj(cplx(f.VL, (leaf * f.max_leaf_w + row) * RV[L] + k));
+        }));
+        items.back().base = int32_t(p0);
+      }
+      st.bytes = int64_t(arena.size() - a0);
+    }
+    // ---- H-stages l = L-1 .. h: (H^l)^*
     for (int l = L - 1; l >= h; --l) {
       Stage& st = begin_stage(l, 1);
       const int R2 = RV[l + 1], R1 = RV[l];
       st.R_in = R2;
       st.R_out = R1;
-      st.in_pat = l == L - 1 ? PAT_LEAF : PAT_SPLIT;
+      st.in_pat = PAT_SPLIT;
       st.out_pat = PAT_CONTIG;
-      const bool leaves = l == L - 1;
-      st.n_items = leaves ? c + 1 : 1;
-      st.main_idx = leaves ? c : 0;
+      st.n_items = 1;
+      st.main_idx = 0;
       const double* Hl = f.H[l - h];
       const size_t a0 = arena.size();
       for (int64_t g = 0; g < st.n_groups; ++g) {
-        if (leaves) {
-          for (int t = 0; t < c; ++t) {
-            const int64_t leaf = c * g + t;
-            const int np = int(f.w_off[leaf + 1] - f.w_off[leaf]);
-            items.push_back(add_item(np, RV[L], ITEM_LEAF_W, uint8_t(t), [&](int b, int k) {
-              return std::conj(cplx(f.VL, (leaf * f.max_leaf_w + b) * RV[L] + k));
-            }));
-          }
-        }
         // T[(tp,k)][(t,k2)] = conj(H^l_{c j + t, ip}[k2][(tp,k)]), lines = (t,k2)
         items.push_back(add_item(c * R2, c * R1, ITEM_MAIN, 0, [&](int line, int e) {
           const int t = line / R2, k2 = line % R2, tp = e / R1, k = e % R1;
@@ -142,7 +160,7 @@ struct Packer {
       st.in_pat = l == h ? PAT_CORNER : PAT_CONTIG;
       st.out_pat = l == L - 1 ? PAT_LEAF : PAT_SPLIT;
       const bool leaves = l == L - 1;
-      st.n_items = leaves ? c + 1 : 1;
+      st.n_items = leaves ? 2 : 1;
       st.main_idx = 0;
       const double* Gl = f.G[l - h];
       const int64_t B = st.B, ch = st.ch;
@@ -156,13 +174,17 @@ struct Packer {
           return v;
         }));
         if (leaves) {
-          for (int t = 0; t < c; ++t) {
-            const int64_t leaf = c * g + t;
-            const int np = int(f.x_off[leaf + 1] - f.x_off[leaf]);
-            items.push_back(add_item(np, RU[L], ITEM_LEAF_X, uint8_t(t), [&](int a, int k) {
-              return cplx(f.UL, (leaf * f.max_leaf_x + a) * RU[L] + k);
-            }));
-          }
+          // U^L_i for the c leaves i = c g + t in one item, stored by columns: line = a
+          // column k (an input of the leaf products), entry a = a point of the group
+          const int64_t p0 = f.x_off[c * g], p1 = f.x_off[c * g + c];
+          const int np = int(p1 - p0);
+          items.push_back(add_item(np > 0 ? RU[L] : 0, std::max(np, 1), ITEM_LEAF_X, 0, [&](int k, int a) {
+            int64_t leaf = c * g;
+            while (f.x_off[leaf + 1] <= p0 + a) ++leaf;
+            const int64_t row = p0 + a - f.x_off[leaf];
+            return cplx(f.UL, (leaf * f.max_leaf_x + row) * RU[L] + k);
+          }));
+          items.back().base = int32_t(p0);
         }
       }
       st.bytes = int64_t(arena.size() - a0);
@@ -176,7 +198,7 @@ void validate(const mbf_factors_t& f) {
   if (f.dim != 2 && f.dim != 3) fail(MBF_ERR_INVALID, "dim must be 2 or 3");
   if (f.L < 2 || f.L % 2 || f.L > 20) fail(MBF_ERR_INVALID, "L must be even, 2..20");
   const int c = 1 << f.dim, h = f.L / 2;
-  if (2 * (f.L - h) > kMaxStages) fail(MBF_ERR_INVALID, "too many stages");
+  if (2 * (f.L - h) + 1 > kMaxStages) fail(MBF_ERR_INVALID, "too many stages");
   if (!f.x_perm || !f.x_off || !f.w_perm || !f.w_off || !f.RU || !f.RV || !f.UL || !f.VL || !f.G ||
       !f.H || !f.S)
     fail(MBF_ERR_INVALID, "factor set has a NULL array");
@@ -217,9 +239,54 @@ void validate(const mbf_factors_t& f) {
 // each stage writes are exactly those the next stage reads (so forward and adjoint
 // never read an unwritten entry), and every item lies inside the arena with the
 // shape its stage expects.
+int64_t host_pat_off(int pat, int64_t g, int t, const Stage& s, int64_t R, int c) {
+  const int64_t a = g / s.B, b = g % s.B;
+  if (pat == PAT_SPLIT) return ((c * a + t) * s.B + b) * R;
+  if (pat == PAT_CONTIG) return (int64_t(c) * g + t) * R;
+  return ((c * b + t) * int64_t(s.ch) + a) * R;
+}
+// group of stage s whose input pattern reads segment P (the kernel's consumer map)
+int64_t host_pat_group(int pat, int64_t P, const Stage& s, int c) {
+  if (pat == PAT_CONTIG) return P / c;
+  if (pat == PAT_SPLIT) return (P / s.B / c) * s.B + P % s.B;
+  return (P % s.ch) * s.B + (P / s.ch) / c;
+}
+
+// The kernel replaces grid barriers by counting: each group adds 1 to the counter of
+// the consumer of each of its c output segments and a consumer starts at c.  Check,
+// forward and adjoint, that every consumer is told exactly c times and that the
+// group named for a segment is the one whose gather reads it.
+void check_dependencies(const Plan& plan) {
+  const int c = plan.c, S = plan.n_stages;
+  for (int adj = 0; adj < 2; ++adj) {
+    for (int e = 0; e + 1 < S; ++e) {
+      const Stage& st = plan.st[adj ? S - 1 - e : e];
+      const Stage& nx = plan.st[adj ? S - 2 - e : e + 1];
+      const int out_pat = adj ? st.in_pat : st.out_pat, in_pat = adj ? nx.out_pat : nx.in_pat;
+      const int64_t Rout = adj ? st.R_in : st.R_out, Rin = adj ? nx.R_out : nx.R_in;
+      if (in_pat == PAT_LEAF || out_pat == PAT_LEAF) fail(MBF_ERR_INVALID, "plan: leaf pattern between stages");
+      if (Rout != Rin) fail(MBF_ERR_INVALID, "plan: segment lengths differ between stages");
+      std::vector<int> cnt(size_t(nx.n_groups), 0);
+      for (int64_t g = 0; g < st.n_groups; ++g)
+        for (int t = 0; t < c; ++t) {
+          const int64_t P = host_pat_off(out_pat, g, t, st, Rout, c) / Rout;
+          const int64_t h = host_pat_group(in_pat, P, nx, c);
+          if (h < 0 || h >= nx.n_groups) fail(MBF_ERR_INVALID, "plan: consumer group out of range");
+          bool reads = false;
+          for (int tt = 0; tt < c; ++tt) reads |= host_pat_off(in_pat, h, tt, nx, Rin, c) == P * Rin;
+          if (!reads) fail(MBF_ERR_INVALID, "plan: consumer map names a group that does not read the segment");
+          ++cnt[size_t(h)];
+        }
+      for (int v : cnt)
+        if (v != c) fail(MBF_ERR_INVALID, "plan: a consumer group is not fed by exactly c segments");
+    }
+  }
+}
+
 void check_plan(const Plan& plan, const std::vector<Item>& items, size_t arena_bytes, int64_t positions,
                 const mbf_factors_t& f) {
   const int c = plan.c;
+  check_dependencies(plan);
   std::vector<char> wrote, read;
   for (int e = 0; e < plan.n_stages; ++e) {
     const Stage& st = plan.st[e];
@@ -246,23 +313,32 @@ void check_plan(const Plan& plan, const std::vector<Item>& items, size_t arena_b
       fail(MBF_ERR_INVALID, "plan: stage reads differ from the previous stage's writes");
     wrote = wr;
     const int64_t nL = Tree::ipow(c, plan.L);
+    if (st.n_items > 32) fail(MBF_ERR_INVALID, "plan: more than 32 items in a group");
+    if (st.in_pat == PAT_LEAF || st.out_pat == PAT_LEAF) {
+      const int64_t* off = st.in_pat == PAT_LEAF ? f.w_off : f.x_off;
+      for (int64_t g = 0; g < st.n_groups; ++g)
+        if (off[c * g + c] - off[c * g] > kMaxGroupPoints)
+          fail(MBF_ERR_INVALID, "plan: the leaves of one group hold more than " +
+                                    std::to_string(kMaxGroupPoints) + " points");
+    }
     for (int64_t g = 0; g < st.n_groups; ++g)
       for (int m = 0; m < st.n_items; ++m) {
         const Item& it = items[size_t(st.item_base + g * st.n_items + m)];
-        if (it.offset % 128 || it.offset + size_t(item_bytes(it.nlines, it.len, it.lpc)) > arena_bytes)
+        if (size_t(it.off128) * 128 + size_t(item_bytes(it.nlines, it.len, it.lpc)) > arena_bytes)
           fail(MBF_ERR_INVALID, "plan: item outside the arena");
         if (chunk_bytes(std::min<int64_t>(it.lpc, std::max<int64_t>(it.nlines, 1)), it.len) > kSlotBytes)
           fail(MBF_ERR_INVALID, "plan: chunk larger than a pipeline slot");
-        const int64_t leaf = c * g + it.t;
+        const int64_t leaf = c * g;
         if (it.kind == ITEM_MAIN) {
           if (it.nlines != c * st.R_in || it.len != c * st.R_out) fail(MBF_ERR_INVALID, "plan: main block shape");
         } else if (it.kind == ITEM_LEAF_W) {
-          if (st.in_pat != PAT_LEAF || leaf >= nL || it.len != st.R_in ||
-              it.nlines != f.w_off[leaf + 1] - f.w_off[leaf])
+          if (st.in_pat != PAT_LEAF || leaf + c > nL || it.len != st.R_in ||
+              it.nlines != f.w_off[leaf + c] - f.w_off[leaf] || it.base != f.w_off[leaf])
             fail(MBF_ERR_INVALID, "plan: Omega leaf item");
         } else if (it.kind == ITEM_LEAF_X) {
-          if (st.out_pat != PAT_LEAF || leaf >= nL || it.len != st.R_out ||
-              it.nlines != f.x_off[leaf + 1] - f.x_off[leaf])
+          const int64_t np = f.x_off[leaf + c] - f.x_off[leaf];
+          if (st.out_pat != PAT_LEAF || leaf + c > nL || it.len != std::max<int64_t>(np, 1) ||
+              it.nlines != (np > 0 ? st.R_out : 0) || it.base != f.x_off[leaf])
             fail(MBF_ERR_INVALID, "plan: X leaf item");
         } else {
           fail(MBF_ERR_INVALID, "plan: unknown item kind");
@@ -282,8 +358,7 @@ void op_free(mbf_op_s* op) {
   cudaFree(op->d_x_off);
   cudaFree(op->d_w_perm);
   cudaFree(op->d_w_off);
-  cudaFree(op->d_buf0);
-  cudaFree(op->d_buf1);
+  cudaFree(op->d_bufs);
   cudaFree(op->d_barrier);
   cudaFree(op->d_status);
   cudaFree(op->d_stage_in);
@@ -327,10 +402,10 @@ mbf_op_s* op_create(const mbf_factors_t& f) {
     op->d_x_off = dev_upload(to32(f.x_off, nL + 1), "x_off");
     op->d_w_perm = dev_upload(to32(f.w_perm, std::max<int64_t>(f.n_w, 1)), "w_perm");
     op->d_w_off = dev_upload(to32(f.w_off, nL + 1), "w_off");
-    const size_t vbytes = size_t(op->positions) * 4 * sizeof(float2);
-    if (cudaMalloc(&op->d_buf0, vbytes) != cudaSuccess || cudaMalloc(&op->d_buf1, vbytes) != cudaSuccess)
-      fail(MBF_ERR_OOM, "cudaMalloc workspace");
-    if (cudaMalloc(&op->d_barrier, 256) != cudaSuccess || cudaMalloc(&op->d_status, 256) != cudaSuccess)
+    const size_t vbytes = size_t(op->plan.n_stages) * size_t(op->positions) * 4 * sizeof(float2);
+    if (cudaMalloc(&op->d_bufs, vbytes) != cudaSuccess) fail(MBF_ERR_OOM, "cudaMalloc workspace");
+    if (cudaMalloc(&op->d_barrier, 256 + counter_bytes(op->plan)) != cudaSuccess ||
+        cudaMalloc(&op->d_status, 256) != cudaSuccess)
       fail(MBF_ERR_OOM, "cudaMalloc barrier");
     cuda_check(cudaMemset(op->d_status, 0, 256), "cudaMemset status");
     for (int nrb : {1, 2, 4}) cuda_check(simt_config(nrb, &op->grid, &op->ns[nrb], &op->smem[nrb]), "simt_config");
@@ -363,9 +438,10 @@ void apply_impl(mbf_op_s* op, const void* in, void* out, int64_t nrhs, int32_t p
   a.out = static_cast<float2*>(out);
   a.in_len = adj ? op->n_out : op->n_in;
   a.out_len = adj ? op->n_in : op->n_out;
-  a.buf0 = op->d_buf0;
-  a.buf1 = op->d_buf1;
+  a.bufs = op->d_bufs;
+  a.buf_stride = op->positions * nrb;
   a.barrier = op->d_barrier;
+  a.counters = op->d_barrier + 64;
   a.status = op->d_status;
   a.nrhs = int32_t(nrhs);
   a.n_pass = int32_t((nrhs + nrb - 1) / nrb);
@@ -477,7 +553,7 @@ mbf_status mbf_op_info(mbf_op_t op, mbf_op_info_t* info) {
     info->bytes_packed = op->bytes_packed;
     for (int s = 0; s < op->plan.n_stages && s < 32; ++s) info->bytes_stage[s] = op->plan.st[s].bytes;
     info->grid = op->grid;
-    info->threads = kThreads;
+    info->threads = simt_threads(1);
     info->smem = int(op->smem[1]);
   });
 }

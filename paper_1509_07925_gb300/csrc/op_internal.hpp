@@ -23,8 +23,8 @@ struct mbf_op_s {
   uint8_t* d_arena = nullptr;
   mbf::Item* d_items = nullptr;
   int32_t *d_x_perm = nullptr, *d_x_off = nullptr, *d_w_perm = nullptr, *d_w_off = nullptr;
-  float2 *d_buf0 = nullptr, *d_buf1 = nullptr;
-  unsigned* d_barrier = nullptr;
+  float2* d_bufs = nullptr;         // one coefficient vector per stage, 4 RHS wide
+  unsigned* d_barrier = nullptr;    // barrier word, then (256 bytes on) the dependency counters
   int* d_status = nullptr;
   int grid = 0, ns[5] = {0, 0, 0, 0, 0};
   size_t smem[5] = {0, 0, 0, 0, 0};

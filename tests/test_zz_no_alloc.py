@@ -70,8 +70,8 @@ def test_static_apply_matches_apply_twice(bd, case, nrhs):
 
 
 def test_static_apply_rejects_oversized_workspace(bd):
-    """2-D DFT n=128, depth 6, r=16: c^L * r = 65,536 entries, so 4 RHS per pass need
-    2 * 8 * 65,536 * 4 + 256 bytes > 4 MiB (rejected); 1 RHS fits and runs."""
+    """2-D DFT n=128, depth 6, r=16: 7 stages of c^L * r = 65,536 entries, so 4 RHS per
+    pass need 7 * 8 * 65,536 * 4 bytes > 4 MiB (rejected); 1 RHS (3.7 MB) fits and runs."""
     hf = bd.HostFactors.build(2, 128, 6, 16, kernel="dft")
     op = bd.Operator(hf)
     n = 128 * 128
