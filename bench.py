@@ -40,6 +40,8 @@ def parse():
     p.add_argument("--impl", default="mbf", choices=["mbf", "reference"])
     p.add_argument("--workload", default="fio2_polar_n256_L6_r24")
     p.add_argument("--nrhs", type=int, default=0, help="override the workload's RHS count")
+    p.add_argument("--precision", default="auto", choices=["auto", "fp32_simt", "bf16x3"],
+                   help="auto: FP32 SIMT below 8 RHS, split-BF16x3 tensor cores from 8 RHS")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
 
@@ -218,7 +220,9 @@ def main():
     sp = stream.cuda_stream
     g = torch.from_numpy(complex_normal(N, nrhs, seed=wl.seed_g).astype(np.complex64)).cuda()
     u = torch.empty((nrhs, N), dtype=torch.complex64, device="cuda")
-    prec = bd.MBF_PREC_FP32_SIMT
+    if args.precision == "auto":
+        args.precision = "bf16x3" if nrhs >= 8 else "fp32_simt"
+    prec = {"fp32_simt": bd.MBF_PREC_FP32_SIMT, "bf16x3": bd.MBF_PREC_BF16X3}[args.precision]
     for _ in range(max(3, args.warmup)):
         op.apply(g.data_ptr(), u.data_ptr(), nrhs, prec, sp)
     op.check(sp)
@@ -271,7 +275,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 (complex64)", "data": "synthetic",
         "config": {"workload": wl.name, "kernel": wl.kernel, "tree": wl.transform, "n": wl.n, "N": N,
-                   "L": wl.L, "r": wl.r, "nrhs": nrhs, "precision": "fp32_simt",
+                   "L": wl.L, "r": wl.r, "nrhs": nrhs, "precision": args.precision,
                    "parallelism": f"replicas{world}",
                    "l2": f"inputs larger than L2: packed factors {info.bytes_packed / 1e6:.0f} MB > 129 MB",
                    "factor_bytes_algorithmic": info.bytes_algorithmic,

@@ -70,6 +70,28 @@ struct Plan {
   Stage st[kMaxStages];
 };
 
+// Tensor-core path: one main stage (a G^l or (H^l)^* level) of c^(L-1) group tiles.
+// A tile is M_t = c R_out rows by K_t = c R_in columns, stored as K_pad/16 chunks; a
+// chunk is 4 planes (Re hi, Re lo, Im hi, Im lo in bf16, the split T = hi + lo), each
+// plane M8 = roundup(M_t, 8) rows by 16 columns in 8x8 core matrices (128 B), the two
+// core matrices of a row group adjacent (K-major, no swizzle).
+struct TCStage {
+  int32_t n_groups, M_t, K_t, M8, K_pad, MB;   // MB = ceil(M_t / 128) row blocks
+  int32_t in_pat, out_pat, R_in, R_out, B, ch;
+  int64_t base;          // arena offset of group 0
+  int64_t tile_bytes;    // bytes per group tile (K_pad / 16 chunks)
+  int32_t plane_bytes;   // M8 * 32
+  int32_t pad_;
+};
+
+struct TCPlan {
+  int32_t n_stages, c, d, L;
+  TCStage st[kMaxStages];
+};
+
+constexpr int kTcMaxRows = 256;   // M_t limit (two 128-row MMA blocks)
+constexpr int kTcMaxK = 256;      // K_t limit
+
 MBF_HD int64_t pad4(int64_t x) { return (x + 3) & ~int64_t(3); }
 MBF_HD int64_t chunk_bytes(int64_t nl, int64_t len) { return 2 * pad4(nl * len) * 4; }
 MBF_HD int64_t lines_per_chunk(int64_t len) {

@@ -194,6 +194,90 @@ struct Packer {
   }
 };
 
+// ---------------------------------------------------------------- tensor-core packing
+uint16_t bf16_rn(float x) {
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  if ((u & 0x7fffffffu) > 0x7f800000u) return 0x7fc0;
+  return uint16_t((u + 0x7fffu + ((u >> 16) & 1u)) >> 16);
+}
+float bf16_to_float(uint16_t h) {
+  const uint32_t u = uint32_t(h) << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+
+// Split-bf16 tiles of every G^l / (H^l)^* group product (the main stages of the SIMT
+// plan; the last G stage writes the level-L coefficient vector instead of applying U^L).
+// Tile element (m, k) of a group = output entry m, input entry k, exactly as the SIMT
+// main items; value x (FP64) is stored as hi = bf16(x), lo = bf16(x - hi) for the real and
+// imaginary parts.
+void pack_tc(const mbf_factors_t& f, const Plan& sp, TCPlan& tp, std::vector<uint8_t>& arena, int& mpad,
+             int& kpad_max) {
+  const int c = 1 << f.dim, L = f.L, h = L / 2;
+  auto cplx = [](const double* a, int64_t i) { return cd(a[2 * i], a[2 * i + 1]); };
+  tp = TCPlan{};
+  tp.c = c;
+  tp.d = f.dim;
+  tp.L = L;
+  mpad = 128;
+  kpad_max = 16;
+  int n = 0;
+  for (int e = 1; e < sp.n_stages; ++e) {
+    const Stage& st = sp.st[e];
+    TCStage& ts = tp.st[n++];
+    ts.n_groups = st.n_groups;
+    ts.M_t = c * st.R_out;
+    ts.K_t = c * st.R_in;
+    if (ts.M_t > kTcMaxRows || ts.K_t > kTcMaxK) fail(MBF_ERR_INVALID, "tile too large for the tensor path");
+    ts.M8 = (ts.M_t + 7) & ~7;
+    ts.K_pad = (ts.K_t + 15) & ~15;
+    ts.MB = (ts.M_t + 127) / 128;
+    ts.in_pat = st.in_pat;
+    ts.out_pat = st.out_pat == PAT_LEAF ? PAT_SPLIT : st.out_pat;   // B = 1: writes leaf c g + t
+    ts.R_in = st.R_in;
+    ts.R_out = st.R_out;
+    ts.B = st.B;
+    ts.ch = st.ch;
+    ts.plane_bytes = ts.M8 * 32;
+    ts.tile_bytes = int64_t(ts.K_pad / 16) * 4 * ts.plane_bytes;
+    size_t base = (arena.size() + 127) & ~size_t(127);
+    ts.base = int64_t(base);
+    arena.resize(base + size_t(ts.tile_bytes) * size_t(ts.n_groups), 0);
+    mpad = std::max(mpad, ts.MB * 128);
+    kpad_max = std::max(kpad_max, ts.K_pad);
+    const int l = st.level, R1 = st.side == 1 ? f.RV[l] : f.RU[l], R2 = st.side == 1 ? f.RV[l + 1] : f.RU[l + 1];
+    const double* M = st.side == 1 ? f.H[l - h] : f.G[l - h];
+    for (int64_t g = 0; g < ts.n_groups; ++g) {
+      uint8_t* tile = arena.data() + base + size_t(g) * size_t(ts.tile_bytes);
+      const int64_t i = g / st.B, jp = g % st.B;
+      for (int m = 0; m < ts.M_t; ++m)
+        for (int k = 0; k < ts.K_t; ++k) {
+          cd v;
+          if (st.side == 1) {   // T[(tp,k)][(t,k2)] = conj(H^l_{c j + t, ip}[k2][(tp,k)])
+            const int tp_ = m / R1, kk = m % R1, t = k / R2, k2 = k % R2;
+            v = std::conj(cplx(M, ((((g * c + t) * R2 + k2) * c + tp_) * R1) + kk));
+          } else {              // T[(t,k2)][(tp,k)] = G^l_{c i + t, jp}[k2][(tp,k)] (x S^h at l = h)
+            const int t = m / R2, k2 = m % R2, tp_ = k / R1, kk = k % R1;
+            v = cplx(M, ((((g * c + t) * R2 + k2) * c + tp_) * R1) + kk);
+            if (l == h) v *= f.S[(i * st.ch + (c * jp + tp_)) * R1 + kk];
+          }
+          const float re = float(v.real()), im = float(v.imag());
+          const uint16_t rh = bf16_rn(re), ih = bf16_rn(im);
+          const uint16_t rl = bf16_rn(float(v.real() - double(bf16_to_float(rh))));
+          const uint16_t il = bf16_rn(float(v.imag() - double(bf16_to_float(ih))));
+          const uint16_t vals[4] = {rh, rl, ih, il};
+          const int kk16 = k / 16, kc = k % 16;
+          const size_t in_plane = size_t(((m / 8) * 2 + kc / 8) * 128 + (m % 8) * 16 + (kc % 8) * 2);
+          for (int pl = 0; pl < 4; ++pl)
+            std::memcpy(tile + size_t(kk16 * 4 + pl) * size_t(ts.plane_bytes) + in_plane, &vals[pl], 2);
+        }
+    }
+  }
+  tp.n_stages = n;
+}
+
 void validate(const mbf_factors_t& f) {
   if (f.dim != 2 && f.dim != 3) fail(MBF_ERR_INVALID, "dim must be 2 or 3");
   if (f.L < 2 || f.L % 2 || f.L > 20) fail(MBF_ERR_INVALID, "L must be even, 2..20");
@@ -363,6 +447,9 @@ void op_free(mbf_op_s* op) {
   cudaFree(op->d_status);
   cudaFree(op->d_stage_in);
   cudaFree(op->d_stage_out);
+  cudaFree(op->d_tc_arena);
+  cudaFree(op->d_tc_bufs);
+  cudaFree(op->d_tc_counters);
   cudaSetDevice(prev);
   delete op;
 }
@@ -409,11 +496,123 @@ mbf_op_s* op_create(const mbf_factors_t& f) {
       fail(MBF_ERR_OOM, "cudaMalloc barrier");
     cuda_check(cudaMemset(op->d_status, 0, 256), "cudaMemset status");
     for (int nrb : {1, 2, 4}) cuda_check(simt_config(nrb, &op->grid, &op->ns[nrb], &op->smem[nrb]), "simt_config");
+    // tensor-core tiles (the multi-RHS path); an operator whose tiles do not fit keeps
+    // the SIMT path only and says why
+    try {
+      std::vector<uint8_t> tc_arena;
+      pack_tc(f, op->plan, op->tcplan, tc_arena, op->tc_mpad, op->tc_kpad_max);
+      const Stage& first = op->plan.st[0];
+      const Stage& last = op->plan.st[op->plan.n_stages - 1];
+      if (op->plan.n_stages < 2 || first.n_items != 1 || last.n_items != 2 || last.B != 1 ||
+          op->tcplan.st[0].in_pat != PAT_SPLIT || op->tcplan.st[0].B != 1)
+        fail(MBF_ERR_INVALID, "plan shape not supported by the tensor path");
+      int optin = 0;
+      cuda_check(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, op->device), "attr");
+      for (int R : {op->RU[size_t(op->L)], op->RV[size_t(op->L)]})
+        if (leaf_smem_bytes(R, op->c) > size_t(optin)) fail(MBF_ERR_INVALID, "leaf rank too large for the tensor path");
+      int mb_max = 1;
+      for (int e = 0; e < op->tcplan.n_stages; ++e) mb_max = std::max(mb_max, op->tcplan.st[e].MB);
+      if (4 * mb_max * 32 > 512 || tc_smem_bytes(3, op->tc_mpad, 32, op->tc_kpad_max) > size_t(optin))
+        fail(MBF_ERR_INVALID, "tiles too large for the tensor path");
+      op->tc_bytes = int64_t(tc_arena.size());
+      op->d_tc_arena = dev_upload(tc_arena, "tensor-core arena");
+    } catch (const Error& err) {
+      op->tc_unavailable = err.what();
+    }
   } catch (...) {
     op_free(op);
     throw;
   }
   return op;
+}
+
+// Tensor-core apply for panels of up to kTcMaxNR RHS: leaf kernel ((V^L)^*), the
+// persistent tcgen05 kernel over the G / H levels, leaf kernel (U^L), per panel.
+void apply_tc(mbf_op_s* op, const float2* g, float2* u, int64_t nrhs, cudaStream_t st) {
+  if (!op->tc_unavailable.empty()) fail(MBF_ERR_INVALID, "tensor path unavailable: " + op->tc_unavailable);
+  const TCPlan& tp = op->tcplan;
+  const int S = tp.n_stages;
+  const int64_t vec = op->positions * kTcMaxNR;
+  if (!op->d_tc_bufs) {
+    if (cudaMalloc(&op->d_tc_bufs, size_t(S + 1) * size_t(vec) * sizeof(float2)) != cudaSuccess)
+      fail(MBF_ERR_OOM, "cudaMalloc tensor-path workspace");
+    if (cudaMalloc(&op->d_tc_counters, tc_counter_bytes(tp)) != cudaSuccess)
+      fail(MBF_ERR_OOM, "cudaMalloc tensor-path counters");
+  }
+  int dev = 0, sms = 0, optin = 0;
+  cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+  cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "attr");
+  cuda_check(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "attr");
+  int mb_max = 1;
+  for (int e = 0; e < S; ++e) mb_max = std::max(mb_max, tp.st[e].MB);
+  const Stage& leaf_st = op->plan.st[0];
+  const Stage& last_st = op->plan.st[op->plan.n_stages - 1];
+  const int RL_w = op->RV[size_t(op->L)], RL_x = op->RU[size_t(op->L)];
+  // panel width: a multiple of 32 (the epilogue reads the accumulators 32 columns at a
+  // time), within the shared-memory and TMEM budgets (4 accumulator column blocks of NR
+  // per 128-row block, two accumulator sets)
+  int NR = int(std::min<int64_t>(kTcMaxNR, (nrhs + 31) / 32 * 32));
+  while (NR > 32 && (4 * mb_max * NR > 512 || tc_smem_bytes(3, op->tc_mpad, NR, op->tc_kpad_max) > size_t(optin)))
+    NR -= 32;
+  if (4 * mb_max * NR > 512 || tc_smem_bytes(3, op->tc_mpad, NR, op->tc_kpad_max) > size_t(optin))
+    fail(MBF_ERR_INVALID, "tensor path does not fit shared memory for this operator");
+  for (int64_t r0 = 0; r0 < nrhs; r0 += NR) {
+    int nsa = 3;
+    while (nsa < 8 && tc_smem_bytes(nsa + 1, op->tc_mpad, NR, op->tc_kpad_max) <= size_t(optin)) ++nsa;
+    // more than half the SM's shared memory: one CTA per SM, so that each CTA's
+    // 512-column TMEM allocation never waits on another CTA of the same launch
+    const size_t smem = std::max(tc_smem_bytes(nsa, op->tc_mpad, NR, op->tc_kpad_max), size_t(optin) / 2 + 1024);
+    float2* yl = op->d_tc_bufs;              // level-L input vector of the main stages
+    float2* bufs = op->d_tc_bufs + vec;      // main stage e writes bufs + e * vec
+    // (V^L)^*: g -> yl
+    LeafArgs la{};
+    la.arena = op->d_arena;
+    la.items = op->d_items;
+    la.item_base = leaf_st.item_base;
+    la.perm = op->d_w_perm;
+    la.off = op->d_w_off;
+    la.vec = g;
+    la.outp = yl;
+    la.len_vec = op->n_in;
+    la.nrhs = int32_t(nrhs);
+    la.rhs0 = int32_t(r0);
+    la.NR = NR;
+    la.c = op->c;
+    la.R = RL_w;
+    la.item_stride = leaf_st.n_items;
+    cuda_check(launch_leaf(la, false, leaf_st.n_groups, st), "leaf (V^L)^* launch");
+    // G / H levels on tensor cores
+    TCArgs ta{};
+    ta.arena = op->d_tc_arena;
+    ta.x_in = yl;
+    ta.bufs = bufs;
+    ta.buf_stride = int64_t(NR) * op->positions;
+    ta.counters = op->d_tc_counters;
+    ta.status = op->d_status;
+    ta.NR = NR;
+    ta.nsa = nsa;
+    ta.mpad = op->tc_mpad;
+    ta.kpad_max = op->tc_kpad_max;
+    ta.plan = tp;
+    cuda_check(launch_apply_tc(ta, sms, smem, st), "tensor-core launch");
+    // U^L: last main stage output -> u
+    LeafArgs lu{};
+    lu.arena = op->d_arena;
+    lu.items = op->d_items;
+    lu.item_base = last_st.item_base + 1;   // item 1 (the U^L item) of each group of the last stage
+    lu.item_stride = last_st.n_items;
+    lu.perm = op->d_x_perm;
+    lu.off = op->d_x_off;
+    lu.vec = bufs + int64_t(S - 1) * NR * op->positions;
+    lu.outp = u;
+    lu.len_out = op->n_out;
+    lu.nrhs = int32_t(nrhs);
+    lu.rhs0 = int32_t(r0);
+    lu.NR = NR;
+    lu.c = op->c;
+    lu.R = RL_x;
+    cuda_check(launch_leaf(lu, true, last_st.n_groups, st), "leaf U^L launch");
+  }
 }
 
 void apply_impl(mbf_op_s* op, const void* in, void* out, int64_t nrhs, int32_t precision, void* stream,
@@ -422,11 +621,18 @@ void apply_impl(mbf_op_s* op, const void* in, void* out, int64_t nrhs, int32_t p
   if (nrhs < 0) fail(MBF_ERR_INVALID, "nrhs < 0");
   if (nrhs == 0) return;
   if ((!in || !out)) fail(MBF_ERR_INVALID, "NULL vector");
-  if (precision != MBF_PREC_AUTO && precision != MBF_PREC_FP32_SIMT)
-    fail(MBF_ERR_INVALID, "precision not available on this path");
+  if (precision != MBF_PREC_AUTO && precision != MBF_PREC_FP32_SIMT && precision != MBF_PREC_BF16X3)
+    fail(MBF_ERR_INVALID, "precision not available");
   if (nrhs > (int64_t(1) << 24)) fail(MBF_ERR_INVALID, "nrhs too large");
-  const int nrb = nrhs >= 4 ? 4 : (nrhs >= 2 ? 2 : 1);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const bool tensor = precision == MBF_PREC_BF16X3 ||
+                      (precision == MBF_PREC_AUTO && nrhs >= 8 && !adj && op->tc_unavailable.empty());
+  if (tensor) {
+    if (adj) fail(MBF_ERR_INVALID, "the tensor-core path applies the forward operator only");
+    apply_tc(op, static_cast<const float2*>(in), static_cast<float2*>(out), nrhs, st);
+    return;
+  }
+  const int nrb = nrhs >= 4 ? 4 : (nrhs >= 2 ? 2 : 1);
   ApplyArgs a{};
   a.arena = op->d_arena;
   a.items = op->d_items;

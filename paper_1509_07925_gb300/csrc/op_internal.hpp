@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <string>
 #include <vector>
 
 #include "layout.hpp"
@@ -28,6 +29,15 @@ struct mbf_op_s {
   int* d_status = nullptr;
   int grid = 0, ns[5] = {0, 0, 0, 0, 0};
   size_t smem[5] = {0, 0, 0, 0, 0};
+  // tensor-core path: arena of split-bf16 tiles of the main stages, its plan, and the
+  // panel workspace (allocated on first use)
+  mbf::TCPlan tcplan{};
+  uint8_t* d_tc_arena = nullptr;
+  int64_t tc_bytes = 0;
+  int tc_mpad = 128, tc_kpad_max = 16, tc_grid = 0;
+  float2* d_tc_bufs = nullptr;        // [S_main + 1] vectors of positions x kTcMaxNR
+  unsigned* d_tc_counters = nullptr;
+  std::string tc_unavailable;         // why the tensor path cannot run for this operator ("" if it can)
   // staging for mbf_apply_host
   float2 *d_stage_in = nullptr, *d_stage_out = nullptr;
   size_t stage_in_bytes = 0, stage_out_bytes = 0;

@@ -8,6 +8,7 @@ from mbf_synth import complex_normal
 from oracle import bf as B
 from oracle import direct as D
 from oracle import problem as P
+from paper_1509_07925_gb300.binding import MBF_PREC_FP32_SIMT
 
 from gpu_util import export_factors, gpu_apply, import_factors, oracle_case, rel
 
@@ -53,7 +54,7 @@ def ops(bd):
 def test_forward_matches_oracle(ops, case, nrhs):
     op, fs, sb = ops(case)
     g = complex_normal(fs.n_in, nrhs, seed=11)
-    u = gpu_apply(torch, op, g)
+    u = gpu_apply(torch, op, g, precision=MBF_PREC_FP32_SIMT)
     ref = sb.apply(g)
     assert u.shape == ref.shape
     assert np.all(np.isfinite(u))
