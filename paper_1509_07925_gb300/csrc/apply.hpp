@@ -37,17 +37,27 @@ enum DeviceStatus : int {
   ST_DEP_TIMEOUT = 5
 };
 
-constexpr int kTcMaxNR = 64;   // RHS per tensor-core panel
+
+// Vectors between the tensor-core stages are "split blocks": block P of a level holds
+// the R8 coefficients of one tree-node pair for the kTcNR right-hand sides of a panel
+// as bf16 pairs hi = bf16(x), lo = bf16(x - hi), laid out as the MMA's K-major A
+// operand with the real and imaginary parts stacked on M (rows n and 64 + n):
+//   byte (hl, k, ri, n) = hl R8 256 + (k / 8) 2048 + (8 ri + n / 8) 128 + (n % 8) 16 + (k % 8) 2.
+// A consumer copies each hi / lo half of a block into shared memory as it is.
+constexpr int kTcNR = 64;   // RHS per tensor-core panel
+MBF_HD int64_t split_block_bytes(int R8) { return int64_t(R8) * kTcNR * 8; }
 
 struct TCArgs {
   const uint8_t* arena;
-  const float2* x_in;      // input of main stage 0: [pos][NR]
-  float2* bufs;            // output of main stage e: bufs + e * buf_stride, [pos][NR]
-  int64_t buf_stride;
+  const uint8_t* x_in;     // input of main stage 0 (split blocks)
+  uint8_t* bufs;           // output of main stage e < S - 1: bufs + e * buf_stride (split blocks)
+  float* y_out;            // output of the last main stage: row block * R + k, [re 64 | im 64] floats
+  int64_t buf_stride;      // bytes
   unsigned* counters;      // [stage][group], zeroed per launch
   int* status;
-  int32_t NR, nsa;         // RHS per panel (32 or 64); A ring slots
-  int32_t mpad, kpad_max;  // rows of an A slot plane (128 or 256); largest K_pad
+  int32_t nsa, nxb;        // A ring slots; panel buffers (1 or 2)
+  int32_t nsets, mt_max;   // accumulator sets (1 or 2, 2 mt_max TMEM columns each); largest M_t
+  int32_t kpad_max, pad_;  // largest K_pad
   TCPlan plan;
 };
 
@@ -55,13 +65,15 @@ struct LeafArgs {
   const uint8_t* arena;    // packed arena of the SIMT path (leaf items)
   const Item* items;
   int64_t item_base;       // item of group 0; group g's item is item_base + g * item_stride
-  const int32_t* perm;
-  const int32_t* off;
-  const float2* vec;       // forward: g [nrhs][len_vec]; U^L: input W [pos][NR]
-  float2* outp;            // forward: Y [pos][NR]; U^L: u [nrhs][len_out]
+  const int32_t* perm;     // U^L: tree -> natural x index; permute: natural -> tree Omega index
+  const int32_t* off;      // leaf offsets (tree order)
+  const float2* vec;       // (V^L)^*: panel in tree order [point][64]; permute: g [nrhs][len_vec]
+  const float* wl;         // U^L: level-L coefficients, row block * R + k, [re 64 | im 64] floats
+  float2* outp;            // U^L: u [nrhs][len_out]; permute: panel in tree order
+  uint8_t* outs;           // (V^L)^*: split blocks of the level-L vector (block c g + t)
   int64_t len_vec, len_out;
-  int32_t nrhs, rhs0, NR, c;
-  int32_t R, item_stride;
+  int32_t nrhs, rhs0, c, R;
+  int32_t R8, item_stride;
 };
 
 size_t simt_smem_bytes(int nrb, int ns);
@@ -73,10 +85,14 @@ cudaError_t launch_apply_simt(const ApplyArgs& a, int nrb, bool adj, int grid, s
 size_t counter_bytes(const Plan& plan);
 
 // tensor-core path (apply_tc.cu)
-size_t tc_smem_bytes(int nsa, int mpad, int NR, int kpad_max);
+size_t tc_smem_bytes(int nsa, int nxb, int nsets, int mt_max, int kpad_max);
 size_t tc_counter_bytes(const TCPlan& plan);
-size_t leaf_smem_bytes(int R, int c);
+size_t leaf_smem_bytes(int R, bool u_side);
+bool leaf_fits(int R8);   // leaf kernels: R8 <= 64
 cudaError_t launch_apply_tc(const TCArgs& a, int grid, size_t smem, cudaStream_t stream);
-cudaError_t launch_leaf(const LeafArgs& a, bool u_side, int n_groups, cudaStream_t stream);
+cudaError_t launch_leaf(const LeafArgs& a, bool u_side, int n_leaves, cudaStream_t stream);
+// vec = g [nrhs][len_vec], perm = inverse tree permutation (natural -> tree, -1 if absent),
+// outp = panel in tree order [tree point][NR]
+cudaError_t launch_permute_in(const LeafArgs& a, cudaStream_t stream);
 
 }  // namespace mbf

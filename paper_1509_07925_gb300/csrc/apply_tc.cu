@@ -1,22 +1,26 @@
-// Tensor-core apply of a butterfly factorization for panels of many right-hand
-// sides (sm_103a: tcgen05 MMAs, TMEM accumulators, cp.async.bulk staging).
+// Tensor-core apply of a butterfly factorization for panels of 64 right-hand sides
+// (sm_103a: tcgen05 MMAs, TMEM accumulators, cp.async.bulk staging).
 //
 // Every group product of a G^l / (H^l)^* level, Y = T X with T complex (M_t x K_t) and X
-// complex (K_t x NR), becomes real MMAs on split-BF16 planes (T = T_hi + T_lo, X = X_hi +
-// X_lo, products hi*hi + hi*lo + lo*hi accumulated in FP32):
-//     Y_re = T_re X_re - T_im X_im,     Y_im = T_im X_re + T_re X_im.
-// T is the MMA's A operand (M = 128 rows per block), the panel X the B operand
-// (N = NR), both K-major without swizzle; K advances 16 per MMA.
+// complex (K_t x 64), is computed transposed, Y^T = X^T T^T, on split-BF16 operands
+// (T = T_hi + T_lo, X = X_hi + X_lo, products hi*hi + hi*lo + lo*hi, FP32 accumulation).
+// The MMA's A operand stacks the real and imaginary parts of X^T on M (rows n and
+// 64 + n: M = 128), its B operand is one plane of T (N = M_t), so two accumulators
+//     D1 = [X_re^T; X_im^T] T_re^T,     D2 = [X_re^T; X_im^T] T_im^T
+// give Y_re^T = D1[n] - D2[64 + n] and Y_im^T = D2[n] + D1[64 + n]: six MMAs per K = 16.
+// The vectors between stages are kept as split blocks (apply.hpp), so a group's X is
+// two bulk copies per input block.
 //
 // Warp roles in a CTA (one per SM, persistent, cooperative):
 //   warp 0     one lane streams each group's tile, chunk by chunk (K = 16 columns,
 //              4 planes), into a ring of shared-memory slots (full/empty mbarriers);
-//   warp 1     allocates TMEM; one lane issues the MMAs into one of two accumulator
-//              buffers and commits completions to the mbarriers;
-//   warps 4-7, 8-11   two epilogue sets, alternating groups: wait for the group's
-//              inputs (dependency counters), gather and split the RHS panel into the
-//              B buffer, wait for the MMAs, read the accumulators (tcgen05.ld) and
-//              store the group's outputs, then count them in for the consumers.
+//   warp 1     allocates TMEM; one lane issues the MMAs into an accumulator set and
+//              commits completions to the mbarriers;
+//   warp 2     lane 0 waits for a group's inputs (dependency counters) and copies its c
+//              blocks into a panel buffer; the warp drops consumed blocks from L2;
+//   warps 4-7, 8-11   epilogue sets, one per accumulator set: read the accumulators
+//              (tcgen05.ld), pair the halves through shared memory, split and store the
+//              group's output blocks, then count them in for the consumers.
 // The (V^L)^* and U^L leaf products run before and after it (leaf kernels below).
 // Every wait is bounded; on a timeout the status word is set and all roles drain.
 #include <cuda_runtime.h>
@@ -61,6 +65,23 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       "l"(src), "r"(bytes), "r"(sa(bar))
       : "memory");
 }
+// Same, with an L2 eviction-priority policy for the source lines.
+__device__ __forceinline__ void bulk_g2s_hint(void* dst, const void* src, uint32_t bytes, uint64_t* bar, uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          sa(dst)),
+      "l"(src), "r"(bytes), "r"(sa(bar)), "l"(pol)
+      : "memory");
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+// Drop a 128-byte line from L2 without writing it back (its contents become undefined).
+__device__ __forceinline__ void l2_discard(const void* p) {
+  asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
+}
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -93,27 +114,44 @@ __device__ __forceinline__ bool named_sync_or(int id, int n, bool v) {
   return r != 0;
 }
 
-// 32 consecutive TMEM columns of this thread's lane (one row of the accumulator).
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
+// 16 consecutive TMEM columns of this thread's lane (one row of the accumulator).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
-      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Two floats -> bf16x2 (round to nearest even), the first in the low half.
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo_half, float hi_half) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi_half), "f"(lo_half));
+  return r;
+}
+// Split 8 floats into hi = bf16(x) and lo = bf16(x - hi) (4 words each).
+__device__ __forceinline__ void split8(const float* y, uint4& hi, uint4& lo) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    h[i] = pack_bf16x2(y[2 * i], y[2 * i + 1]);
+    const float r0 = y[2 * i] - __uint_as_float(h[i] << 16), r1 = y[2 * i + 1] - __uint_as_float(h[i] & 0xffff0000u);
+    l[i] = pack_bf16x2(r0, r1);
+  }
+  hi = make_uint4(h[0], h[1], h[2], h[3]);
+  lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
-__device__ __forceinline__ int64_t pat_off(int pat, int g, int t, const TCStage& s, int R, int c) {
+// Block index (tree-node pair of the level) of segment t of group g under a pattern.
+__device__ __forceinline__ int64_t pat_blk(int pat, int g, int t, const TCStage& s, int c) {
   const int a = g / s.B, b = g - (g / s.B) * s.B;
-  if (pat == PAT_SPLIT) return (int64_t(c * a + t) * s.B + b) * R;
-  if (pat == PAT_CONTIG) return (int64_t(c) * g + t) * R;
-  return (int64_t(c * b + t) * s.ch + a) * R;  // PAT_CORNER
+  if (pat == PAT_SPLIT) return int64_t(c * a + t) * s.B + b;
+  if (pat == PAT_CONTIG) return int64_t(c) * g + t;
+  return int64_t(c * b + t) * s.ch + a;  // PAT_CORNER
 }
 __device__ __forceinline__ int pat_group(int pat, int64_t P, const TCStage& s, int c) {
   if (pat == PAT_CONTIG) return int(P / c);
@@ -141,21 +179,22 @@ __device__ __forceinline__ bool wait_bar(uint64_t* b, uint32_t ph, volatile int*
 }  // namespace tc
 
 constexpr int kTcThreads = 384;
+constexpr int kTcChunk = 16;   // accumulator columns per epilogue step
 
 __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_constant__ TCArgs a) {
   using namespace tc;
   extern __shared__ __align__(1024) uint8_t smem[];
-  const int NR = a.NR, nsa = a.nsa;
-  const uint32_t a_plane = uint32_t(a.mpad) * 32u;          // bytes of one A plane (mpad rows x 16 cols)
-  const uint32_t a_slot = 4u * a_plane;
-  const uint32_t b_buf = 4u * uint32_t(NR) * uint32_t(a.kpad_max) * 2u;
+  const int nsa = a.nsa, nxb = a.nxb, nsets = a.nsets;
+  const uint32_t a_slot = 4u * uint32_t(a.mt_max) * 32u;       // one K16 chunk of a tile (4 planes)
+  const uint32_t x_buf = 2u * uint32_t(a.kpad_max) * 256u;      // hi + lo halves of a panel
   uint8_t* aring = smem;
-  uint8_t* bbuf = smem + size_t(nsa) * a_slot;
-  uint64_t* afull = reinterpret_cast<uint64_t*>(bbuf + 2 * size_t(b_buf));
+  uint8_t* xbuf = aring + size_t(nsa) * a_slot;
+  float* xch = reinterpret_cast<float*>(xbuf + size_t(nxb) * x_buf);   // [set][2][kTcChunk][128]
+  uint64_t* afull = reinterpret_cast<uint64_t*>(xch + size_t(nsets) * 2 * kTcChunk * 128);
   uint64_t* aempty = afull + nsa;
-  uint64_t* bfull = aempty + nsa;
-  uint64_t* bempty = bfull + 2;
-  uint64_t* dfull = bempty + 2;
+  uint64_t* xfull = aempty + nsa;
+  uint64_t* xempty = xfull + 2;
+  uint64_t* dfull = xempty + 2;
   uint64_t* dempty = dfull + 2;
   uint64_t* done = dempty + 2;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
@@ -168,8 +207,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
       mbar_init(&aempty[i], 1);
     }
     for (int s = 0; s < 2; ++s) {
-      mbar_init(&bfull[s], 128);
-      mbar_init(&bempty[s], 1);
+      mbar_init(&xfull[s], 1);
+      mbar_init(&xempty[s], 1);
       mbar_init(&dfull[s], 1);
       mbar_init(&dempty[s], 128);
     }
@@ -187,18 +226,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
   const uint32_t taddr = *tslot;
   const TCPlan& plan = a.plan;
   const int S = plan.n_stages, c = plan.c;
-  // accumulator set s (2 x MB blocks of NR columns) starts at column s * set_cols
-  int mb_max = 1;
-  for (int e = 0; e < S; ++e) mb_max = max(mb_max, plan.st[e].MB);
-  const uint32_t set_cols = uint32_t(mb_max * 2 * NR);
+  const uint32_t set_cols = 2u * uint32_t(a.mt_max);   // D1 | D2 of one accumulator set
 
   if (warp == 0 && lane == 0) {
-    // ---------------------------------------------------------------- producer
+    // ---------------------------------------------------------------- A tiles
+    // (streamed once: first out of L2, so that the stage vectors stay there)
+    const uint64_t pol = policy_evict_first();
     uint32_t ca = 0;
     bool ok = true;
     for (int e = 0; e < S && ok; ++e) {
       const TCStage& st = plan.st[e];
       const int nk = st.K_pad / 16;
+      const uint32_t chunk = 4u * uint32_t(st.plane_bytes);
       for (int g = blockIdx.x; g < st.n_groups && ok; g += gridDim.x) {
         const uint8_t* src = a.arena + st.base + int64_t(g) * st.tile_bytes;
         for (int kk = 0; kk < nk; ++kk, ++ca) {
@@ -211,10 +250,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
             ok = false;
             break;
           }
-          mbar_expect_tx(&afull[slot], 4u * uint32_t(st.plane_bytes));
-          for (int p = 0; p < 4; ++p)
-            bulk_g2s(aring + size_t(slot) * a_slot + size_t(p) * a_plane,
-                     src + (int64_t(kk) * 4 + p) * st.plane_bytes, uint32_t(st.plane_bytes), &afull[slot]);
+          mbar_expect_tx(&afull[slot], chunk);
+          bulk_g2s_hint(aring + size_t(slot) * a_slot, src + int64_t(kk) * chunk, chunk, &afull[slot], pol);
         }
       }
     }
@@ -225,22 +262,95 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
       while (!mbar_try(&afull[slot], ph) && gtimer() - t1 < kTimeoutNs) {
       }
     }
+  } else if (warp == 2) {
+    // ---------------------------------------------------------------- X panels
+    // Lane 0 waits and issues the copies.  Once the MMAs of a group are done (its
+    // buffer is free again), the whole warp drops the group's input blocks from L2:
+    // each block is read by exactly one group, so they need no write-back.
+    const uint8_t* prev[2][8] = {};
+    int64_t prev_bytes[2] = {0, 0};
+    int j = 0;
+    bool ok = true;
+    for (int e = 0; e < S && ok; ++e) {
+      const TCStage& st = plan.st[e];
+      const uint8_t* src = e == 0 ? a.x_in : a.bufs + int64_t(e - 1) * a.buf_stride;
+      const unsigned* cnt_in = a.counters + int64_t(e) * st.n_groups;
+      const uint32_t half = uint32_t(st.R8_in) * 256u;      // hi or lo half of one block
+      const uint32_t xhalf = uint32_t(st.K_pad) * 256u;     // hi or lo half of the panel buffer
+      const int64_t blk = split_block_bytes(st.R8_in);
+      for (int g = blockIdx.x; g < st.n_groups && ok; g += gridDim.x, ++j) {
+        const int xs = j % nxb;
+        const uint32_t xu = uint32_t(j / nxb);
+        int fail = 0;
+        if (lane == 0) {
+          fail = !wait_bar(&xempty[xs], (xu & 1u) ^ 1u, abort);
+          // all c input blocks written by the previous stage
+          if (!fail && e > 0) {
+            const unsigned* cp = cnt_in + g;
+            const uint64_t t0 = gtimer();
+            while (ld_acquire(cp) < unsigned(c)) {
+              if (*abort || *reinterpret_cast<volatile int*>(a.status) != 0) {
+                fail = 1;
+                break;
+              }
+              if (gtimer() - t0 > kTimeoutNs) {
+                atomicCAS(a.status, 0, ST_DEP_TIMEOUT);
+                fail = 1;
+                break;
+              }
+              __nanosleep(32);
+            }
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+          }
+          if (fail) *abort = 1;
+        }
+        if (__shfl_sync(0xffffffffu, fail, 0)) {
+          ok = false;
+          break;
+        }
+        // the group that used this buffer before is done: drop its input blocks from L2
+        if (j >= nxb) {
+          const int64_t nl = prev_bytes[xs] >> 7;
+          for (int t = 0; t < c; ++t)
+            for (int64_t q = lane; q < nl; q += 32) l2_discard(prev[xs][t] + (q << 7));
+        }
+        uint8_t* xb = xbuf + size_t(xs) * x_buf;
+        if (lane == 0) mbar_expect_tx(&xfull[xs], 2u * uint32_t(c) * half);
+        for (int t = 0; t < c; ++t) {
+          const uint8_t* sb = src + int64_t(pat_blk(st.in_pat, g, t, st, c)) * blk;
+          prev[xs][t] = sb;
+          if (lane == 0)
+            for (int hl = 0; hl < 2; ++hl)
+              bulk_g2s(xb + size_t(hl) * xhalf + size_t(t) * half, sb + int64_t(hl) * half, half, &xfull[xs]);
+        }
+        prev_bytes[xs] = blk;
+        __syncwarp();
+      }
+    }
+    // wait (bounded) for the copies of the last groups
+    if (lane == 0)
+      for (int q = max(0, j - nxb); q < j; ++q) {
+        const uint64_t t1 = gtimer();
+        while (!mbar_try(&xfull[q % nxb], uint32_t(q / nxb) & 1u) && gtimer() - t1 < kTimeoutNs) {
+        }
+      }
   } else if (warp == 1 && lane == 0) {
     // ---------------------------------------------------------------- MMA issuer
     uint32_t ca = 0;
     int j = 0;
     bool ok = true;
-    const uint32_t abase = sa(aring), bbase0 = sa(bbuf);
+    const uint32_t abase = sa(aring), xbase0 = sa(xbuf);
     for (int e = 0; e < S && ok; ++e) {
       const TCStage& st = plan.st[e];
       const int nk = st.K_pad / 16;
-      const uint32_t bplane = uint32_t(NR) * uint32_t(st.K_pad) * 2u;
-      const uint32_t sbo_b = uint32_t(st.K_pad) * 16u;
-      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(NR >> 3) << 17) | (uint32_t(128 >> 4) << 24);
+      const uint32_t xhalf = uint32_t(st.K_pad) * 256u;
+      const uint32_t pb = uint32_t(st.plane_bytes);
+      // kind::f16, FP32 accumulate, BF16 A and B, both K-major, N = M_t, M = 128
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(st.M_t >> 3) << 17) | (uint32_t(128 >> 4) << 24);
       for (int g = blockIdx.x; g < st.n_groups && ok; g += gridDim.x, ++j) {
-        const int s = j & 1;
-        const uint32_t u = uint32_t(j >> 1);
-        if (!wait_bar(&bfull[s], u & 1u, abort) || !wait_bar(&dempty[s], (u & 1u) ^ 1u, abort)) {
+        const int xs = j % nxb, ds = j % nsets;
+        const uint32_t xu = uint32_t(j / nxb), du = uint32_t(j / nsets);
+        if (!wait_bar(&xfull[xs], xu & 1u, abort) || !wait_bar(&dempty[ds], (du & 1u) ^ 1u, abort)) {
           if (!*abort) {
             atomicCAS(a.status, 0, ST_FULL_TIMEOUT);
             *abort = 1;
@@ -249,8 +359,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t dcol = taddr + uint32_t(s) * set_cols;
-        const uint32_t bb = bbase0 + uint32_t(s) * b_buf;
+        const uint32_t d1 = taddr + uint32_t(ds) * set_cols, d2 = d1 + uint32_t(a.mt_max);
+        const uint32_t xb = xbase0 + uint32_t(xs) * x_buf;
         for (int kk = 0; kk < nk; ++kk, ++ca) {
           const uint32_t slot = ca % uint32_t(nsa), ph = (ca / uint32_t(nsa)) & 1u;
           if (!wait_bar(&afull[slot], ph, abort)) {
@@ -263,33 +373,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t as = abase + slot * a_slot;
-          for (int mb = 0; mb < st.MB; ++mb) {
-            // A planes: 0 Re hi, 1 Re lo, 2 Im hi, 3 Im lo; B planes: 0 Xre hi, 1 Xre lo, 2 Xim hi, 3 Xim lo
-            auto A = [&](int p) { return sdesc(as + uint32_t(p) * a_plane + uint32_t(mb) * 4096u, 128u, 256u); };
-            auto Bd = [&](int p) { return sdesc(bb + uint32_t(p) * bplane + uint32_t(kk) * 256u, 128u, sbo_b); };
-            const uint32_t dre = dcol + uint32_t((mb * 2 + 0) * NR), dim = dcol + uint32_t((mb * 2 + 1) * NR);
-            const uint32_t acc0 = kk > 0 ? 1u : 0u;
-            const uint32_t neg = idesc | (1u << 13);
-            // Re: T_re X_re - T_im X_im
-            mma_bf16(dre, A(0), Bd(0), idesc, acc0);
-            mma_bf16(dre, A(0), Bd(1), idesc, 1u);
-            mma_bf16(dre, A(1), Bd(0), idesc, 1u);
-            mma_bf16(dre, A(2), Bd(2), neg, 1u);
-            mma_bf16(dre, A(2), Bd(3), neg, 1u);
-            mma_bf16(dre, A(3), Bd(2), neg, 1u);
-            // Im: T_im X_re + T_re X_im
-            mma_bf16(dim, A(2), Bd(0), idesc, acc0);
-            mma_bf16(dim, A(2), Bd(1), idesc, 1u);
-            mma_bf16(dim, A(3), Bd(0), idesc, 1u);
-            mma_bf16(dim, A(0), Bd(2), idesc, 1u);
-            mma_bf16(dim, A(0), Bd(3), idesc, 1u);
-            mma_bf16(dim, A(1), Bd(2), idesc, 1u);
-          }
+          // A: panel half (hi / lo), K-major, next 8 K at +2048, next 8 rows at +128
+          const uint64_t xh = sdesc(xb + uint32_t(kk) * 4096u, 2048u, 128u);
+          const uint64_t xl = sdesc(xb + xhalf + uint32_t(kk) * 4096u, 2048u, 128u);
+          // B: tile planes 0 Re hi, 1 Re lo, 2 Im hi, 3 Im lo; next 8 K at +128, next 8 rows at +256
+          const uint64_t t0 = sdesc(as, 128u, 256u), t1 = sdesc(as + pb, 128u, 256u);
+          const uint64_t t2 = sdesc(as + 2u * pb, 128u, 256u), t3 = sdesc(as + 3u * pb, 128u, 256u);
+          const uint32_t acc0 = kk > 0 ? 1u : 0u;
+          mma_bf16(d1, xh, t0, idesc, acc0);
+          mma_bf16(d1, xh, t1, idesc, 1u);
+          mma_bf16(d1, xl, t0, idesc, 1u);
+          mma_bf16(d2, xh, t2, idesc, acc0);
+          mma_bf16(d2, xh, t3, idesc, 1u);
+          mma_bf16(d2, xl, t2, idesc, 1u);
           mma_commit(&aempty[slot]);
         }
         if (!ok) break;
-        mma_commit(&dfull[s]);
-        mma_commit(&bempty[s]);
+        mma_commit(&dfull[ds]);
+        mma_commit(&xempty[xs]);
       }
     }
     // every MMA this thread issued has completed before TMEM is freed
@@ -297,97 +398,33 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
     const uint64_t t1 = gtimer();
     while (!mbar_try(done, 0) && gtimer() - t1 < kTimeoutNs) {
     }
-  } else if (warp >= 4) {
+  } else if (warp >= 4 && (warp - 4) / 4 < nsets) {
     // ---------------------------------------------------------------- epilogue sets
-    const int set = (warp - 4) >> 2;            // 0: warps 4-7, 1: warps 8-11
-    const int et = (warp - 4 - 4 * set) * 32 + lane;   // 0..127
+    const int set = (warp - 4) >> 2;             // 0: warps 4-7, 1: warps 8-11
     const int quarter = warp & 3;                // TMEM lane quarter this warp may access
+    const int tl = quarter * 32 + lane;          // TMEM lane: n (real part) or 64 + n (imaginary)
+    const int h = tl >> 6, n = tl & 63;
+    const int et = (warp - 4 - 4 * set) * 32 + lane;   // 0..127
     const int bar_id = 1 + set;
     const uint32_t lane_base = uint32_t(32 * quarter) << 16;
+    float* xs0 = xch + size_t(set) * 2 * kTcChunk * 128;
+    uint32_t chunk_no = 0;
     int j = 0;
     bool ok = true;
     for (int e = 0; e < S && ok; ++e) {
       const TCStage& st = plan.st[e];
-      const float2* src = e == 0 ? a.x_in : a.bufs + int64_t(e - 1) * a.buf_stride;
-      float2* dst = a.bufs + int64_t(e) * a.buf_stride;
-      const bool notify = e + 1 < S;
+      const bool last = st.last != 0;
+      uint8_t* dst = a.bufs + int64_t(e) * a.buf_stride;
       const TCStage& nst = plan.st[e + 1 < S ? e + 1 : e];
-      unsigned* cnt_in = a.counters + int64_t(e) * st.n_groups;
       unsigned* cnt_out = a.counters + int64_t(e + 1) * nst.n_groups;
-      const uint32_t bplane = uint32_t(NR) * uint32_t(st.K_pad) * 2u;
-      const uint32_t sbo_b = uint32_t(st.K_pad) * 16u;
+      const int64_t blk = split_block_bytes(st.R8_out);
+      const uint32_t half = uint32_t(st.R8_out) * 256u;
       for (int g = blockIdx.x; g < st.n_groups && ok; g += gridDim.x, ++j) {
-        if ((j & 1) != set) continue;
-        const uint32_t u = uint32_t(j >> 1);
-        uint8_t* bb = bbuf + size_t(set) * b_buf;
-        // (1) the B buffer is free once the MMAs of this set's previous group are done
-        int fail = 0;
-        if (et == 0) {
-          if (!wait_bar(&bempty[set], (u & 1u) ^ 1u, abort)) fail = 1;
-          // (2) all c input segments written by the previous stage
-          if (!fail && e > 0) {
-            const unsigned* cp = cnt_in + g;
-            const uint64_t t0 = gtimer();
-            while (ld_acquire(cp) < unsigned(c)) {
-              if (*abort || *reinterpret_cast<volatile int*>(a.status) != 0) { fail = 1; break; }
-              if (gtimer() - t0 > kTimeoutNs) {
-                atomicCAS(a.status, 0, ST_DEP_TIMEOUT);
-                fail = 1;
-                break;
-              }
-              __nanosleep(32);
-            }
-          }
-          if (fail) *abort = 1;
-        }
-        if (named_sync_or(bar_id, 128, *abort != 0)) {
-          ok = false;
-          break;
-        }
-        // (3) gather the panel and split it into bf16 hi/lo planes (K-major core matrices)
-        {
-          const int nkb = st.K_pad / 8;
-          for (int item = et; item < nkb * NR; item += 128) {
-            const int kb = item / NR, n = item - (item / NR) * NR;
-            uint32_t w[4][4];
-#pragma unroll
-            for (int i = 0; i < 8; i += 2) {
-              float2 v[2];
-#pragma unroll
-              for (int h = 0; h < 2; ++h) {
-                const int k = kb * 8 + i + h;
-                if (k < st.K_t) {
-                  const int t = k / st.R_in, kk = k - t * st.R_in;
-                  const int64_t pos = pat_off(st.in_pat, g, t, st, st.R_in, c) + kk;
-                  v[h] = __ldcg(src + pos * NR + n);
-                } else {
-                  v[h] = make_float2(0.f, 0.f);
-                }
-              }
-              uint16_t hr[2], lr[2], hi[2], li[2];
-#pragma unroll
-              for (int h = 0; h < 2; ++h) {
-                hr[h] = bf16_bits(v[h].x);
-                lr[h] = bf16_bits(v[h].x - __bfloat162float(__ushort_as_bfloat16(hr[h])));
-                hi[h] = bf16_bits(v[h].y);
-                li[h] = bf16_bits(v[h].y - __bfloat162float(__ushort_as_bfloat16(hi[h])));
-              }
-              w[0][i / 2] = uint32_t(hr[0]) | (uint32_t(hr[1]) << 16);
-              w[1][i / 2] = uint32_t(lr[0]) | (uint32_t(lr[1]) << 16);
-              w[2][i / 2] = uint32_t(hi[0]) | (uint32_t(hi[1]) << 16);
-              w[3][i / 2] = uint32_t(li[0]) | (uint32_t(li[1]) << 16);
-            }
-            const uint32_t off = uint32_t(n >> 3) * sbo_b + uint32_t(kb) * 128u + uint32_t(n & 7) * 16u;
-#pragma unroll
-            for (int p = 0; p < 4; ++p)
-              *reinterpret_cast<uint4*>(bb + size_t(p) * bplane + off) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
-          }
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive(&bfull[set]);
-        // (4) wait for the MMAs of this group
+        if (j % nsets != set) continue;
+        const uint32_t du = uint32_t(j / nsets);
+        // wait for the MMAs of this group
         int got = 1;
-        if (et == 0 && !wait_bar(&dfull[set], u & 1u, abort)) {
+        if (et == 0 && !wait_bar(&dfull[set], du & 1u, abort)) {
           got = 0;
           if (!*abort) {
             atomicCAS(a.status, 0, ST_FULL_TIMEOUT);
@@ -399,35 +436,52 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // (5) accumulators -> outputs; row = one output entry (t, k) of the group
-        const uint32_t dcol = taddr + uint32_t(set) * set_cols;
-        for (int mb = 0; mb < st.MB; ++mb) {
-          const int row = mb * 128 + quarter * 32 + lane;
-          const bool live = row < st.M_t;
-          int64_t pos = 0;
-          if (live) {
-            const int t = row / st.R_out, kk = row - t * st.R_out;
-            pos = pat_off(st.out_pat, g, t, st, st.R_out, c) + kk;
-          }
-          for (int c0 = 0; c0 < NR; c0 += 32) {
-            float re[32], im[32];
-            tmem_ld32(dcol + lane_base + uint32_t((mb * 2 + 0) * NR + c0), re);
-            tmem_ld32(dcol + lane_base + uint32_t((mb * 2 + 1) * NR + c0), im);
-            if (live) {
-              float4* o = reinterpret_cast<float4*>(dst + pos * NR + c0);
+        const uint32_t d1 = taddr + uint32_t(set) * set_cols + lane_base, d2 = d1 + uint32_t(a.mt_max);
+        for (int c0 = 0; c0 < st.M_t; c0 += kTcChunk, ++chunk_no) {
+          float v1[kTcChunk], v2[kTcChunk];
+          tmem_ld16(d1 + uint32_t(c0), v1);
+          tmem_ld16(d2 + uint32_t(c0), v2);
+          tmem_wait_ld();
+          // pair lanes n and 64 + n: Y_re = D1[n] - D2[64 + n] (h = 0), Y_im = D2[n] + D1[64 + n] (h = 1)
+          float* xsb = xs0 + size_t(chunk_no & 1u) * kTcChunk * 128;
 #pragma unroll
-              for (int q = 0; q < 16; ++q) o[q] = make_float4(re[2 * q], im[2 * q], re[2 * q + 1], im[2 * q + 1]);
+          for (int q = 0; q < kTcChunk; ++q) xsb[q * 128 + tl] = v2[q];
+          named_sync(bar_id, 128);
+          float y[kTcChunk];
+#pragma unroll
+          for (int q = 0; q < kTcChunk; ++q) {
+            const float pv = xsb[q * 128 + (tl ^ 64)];
+            y[q] = h == 0 ? v1[q] - pv : v1[q] + pv;
+          }
+          // rows m = c0 .. c0 + 15 of the group's output: two runs of 8 within one block each
+#pragma unroll
+          for (int r8 = 0; r8 < kTcChunk / 8; ++r8) {
+            const int m0 = c0 + 8 * r8;
+            const int t = m0 / st.R8_out, k2 = m0 - t * st.R8_out;
+            const int64_t P = pat_blk(st.out_pat, g, t, st, c);
+            if (last) {
+              float* o = a.y_out + (P * st.R_out + k2) * (2 * kTcNR) + h * kTcNR + n;
+#pragma unroll
+              for (int i = 0; i < 8; ++i)
+                if (k2 + i < st.R_out) o[i * 2 * kTcNR] = y[8 * r8 + i];
+            } else {
+              uint4 hi, lo;
+              split8(y + 8 * r8, hi, lo);
+              uint8_t* o = dst + P * blk + (k2 >> 3) * 2048 + (8 * h + (n >> 3)) * 128 + (n & 7) * 16;
+              *reinterpret_cast<uint4*>(o) = hi;
+              *reinterpret_cast<uint4*>(o + half) = lo;
             }
           }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         mbar_arrive(&dempty[set]);
-        // (6) count the written segments in for the consumers of the next stage
-        if (notify) {
+        // count the written blocks in for the consumers of the next stage
+        if (!last) {
+          asm volatile("fence.proxy.async.global;" ::: "memory");
           __threadfence();
           named_sync(bar_id, 128);
           if (et < c) {
-            const int64_t P = pat_off(st.out_pat, g, et, st, st.R_out, c) / st.R_out;
+            const int64_t P = pat_blk(st.out_pat, g, et, st, c);
             atomicAdd(cnt_out + pat_group(nst.in_pat, P, nst, c), 1u);
           }
         }
@@ -442,109 +496,192 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
 }
 
 // ------------------------------------------------------------------ leaf kernels
-// (V^L_j)^* for a panel of NR RHS: one CTA per group of c Omega leaves.  The group's
-// leaf item (lines = points, len = R_L, split planes per chunk) and the panel's input
-// values are staged in shared memory; y[(c g + t) R + k][r] = sum over the points b of
-// leaf t of conj(V^L_t[b][k]) g[r][perm(b)].
+// One CTA per leaf; the leaf's points are staged kLeafChunk at a time.
 constexpr int kLeafThreads = 256;
-constexpr int kLeafRhs = 16;   // RHS per sub-panel
+constexpr int kLeafChunk = 32;
+constexpr int kLeafMaxR8 = 64;      // largest leaf rank (rounded up to 8) of the tensor path
 
-__device__ __forceinline__ void stage_item(const LeafArgs& a, const Item& it, float* re_s, float* im_s) {
-  // unpack the item's chunks into dense [line][len] real / imaginary arrays
-  const uint8_t* base = a.arena + size_t(it.off128) * 128;
-  for (int l0 = 0; l0 < it.nlines; l0 += it.lpc) {
-    const int nl = min(int(it.lpc), int(it.nlines) - l0);
-    const float* re = reinterpret_cast<const float*>(base);
-    const float* im = re + pad4(int64_t(nl) * it.len);
-    for (int q = threadIdx.x; q < nl * it.len; q += blockDim.x) {
-      re_s[l0 * it.len + q] = __ldg(re + q);
-      im_s[l0 * it.len + q] = __ldg(im + q);
+// Entry e of line `line` of a chunked item (split real / imaginary planes per chunk).
+__device__ __forceinline__ float2 item_entry(const uint8_t* base, const Item& it, int line, int e) {
+  const int ci = line / it.lpc, li = line - ci * it.lpc;
+  const int nl = min(int(it.lpc), int(it.nlines) - ci * int(it.lpc));
+  const float* re = reinterpret_cast<const float*>(base + int64_t(ci) * chunk_bytes(it.lpc, it.len));
+  const int64_t q = int64_t(li) * it.len + e;
+  return make_float2(__ldg(re + q), __ldg(re + pad4(int64_t(nl) * it.len) + q));
+}
+
+// Panel in tree order: gt[inv(i)][n] = g[rhs0 + n][i] for the natural indices i of the
+// Omega points in the tree (inv(i) < 0: not in the tree), zero for rhs0 + n >= nrhs.  A
+// CTA moves 64 consecutive natural indices: rows of g are read and rows of gt written
+// whole, the transpose goes through shared memory.
+constexpr int kPermTile = 64;
+__global__ void __launch_bounds__(kLeafThreads) permute_in_kernel(const __grid_constant__ LeafArgs a) {
+  __shared__ float2 tile[kTcNR][kPermTile + 1];
+  const int i0 = blockIdx.x * kPermTile, tid = threadIdx.x;
+  for (int q = tid; q < kTcNR * kPermTile; q += kLeafThreads) {
+    const int n = q / kPermTile, ii = q - n * kPermTile, rhs = a.rhs0 + n, i = i0 + ii;
+    tile[n][ii] = (rhs < a.nrhs && i < a.len_vec) ? __ldg(a.vec + int64_t(rhs) * a.len_vec + i) : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  for (int q = tid; q < kTcNR * kPermTile; q += kLeafThreads) {
+    const int ii = q / kTcNR, n = q - ii * kTcNR, i = i0 + ii;
+    if (i < a.len_vec) {
+      const int tp = a.perm[i];
+      if (tp >= 0) a.outp[int64_t(tp) * kTcNR + n] = tile[n][ii];
     }
-    base += chunk_bytes(nl, it.len);
   }
 }
 
+// (V^L_j)^* for a panel of 64 RHS, leaf j = c g + t:
+//   y_j[k][n] = sum over the points b of leaf j of conj(V^L_j[b][k]) gt[b][n],
+// gt = the panel in tree order (permute_in_kernel), stored as split block j (rows
+// k >= R are zero).  The group's item holds conj(V) with line = point (tree order from
+// the group's first point), entry = k.  Thread (n, kq) accumulates column n for the
+// rows k = 4 (m KT + kq) + 0..3.
 __global__ void __launch_bounds__(kLeafThreads) leaf_v_kernel(const __grid_constant__ LeafArgs a) {
-  extern __shared__ __align__(16) float lsm[];
-  const int g = blockIdx.x, c = a.c, R = a.R;
+  constexpr int NR = kTcNR, KT = kLeafThreads / NR, NRP = NR + 1;
+  constexpr int MM = (kLeafMaxR8 + 4 * KT - 1) / (4 * KT);
+  extern __shared__ __align__(16) float2 lsm[];
+  const int leaf = blockIdx.x, c = a.c, R = a.R, R8 = a.R8;
+  const int g = leaf / c;
   const Item it = a.items[a.item_base + int64_t(g) * a.item_stride];
-  const int p0 = a.off[c * g], npts = a.off[c * g + c] - p0;   // == it.nlines
-  float* re_s = lsm;
-  float* im_s = re_s + kMaxGroupPoints * R;
-  float2* xs = reinterpret_cast<float2*>(im_s + kMaxGroupPoints * R);   // [point][kLeafRhs]
-  int* bnd = reinterpret_cast<int*>(xs + kMaxGroupPoints * kLeafRhs);
-  if (threadIdx.x <= c) bnd[threadIdx.x] = a.off[c * g + threadIdx.x] - p0;
-  stage_item(a, it, re_s, im_s);
-  for (int r0 = 0; r0 < a.NR; r0 += kLeafRhs) {
+  const uint8_t* ibase = a.arena + size_t(it.off128) * 128;
+  const int pg = a.off[c * g], p0 = a.off[leaf], np = a.off[leaf + 1] - p0;
+  float2* vs = lsm;                        // [kLeafChunk][R8], zero for k >= R
+  float2* xs = vs + kLeafChunk * R8;       // [kLeafChunk][NR + 1]
+  const int tid = threadIdx.x, n = tid % NR, kq = tid / NR;
+  float2 acc[MM][4];
+#pragma unroll
+  for (int m = 0; m < MM; ++m)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[m][j] = make_float2(0.f, 0.f);
+  for (int b0 = 0; b0 < np; b0 += kLeafChunk) {
+    const int nb = min(kLeafChunk, np - b0);
     __syncthreads();
-    for (int q = threadIdx.x; q < npts * kLeafRhs; q += blockDim.x) {
-      const int b = q / kLeafRhs, r = q - b * kLeafRhs;
-      const int rhs = a.rhs0 + r0 + r;
-      xs[q] = rhs < a.nrhs ? __ldg(a.vec + int64_t(rhs) * a.len_vec + a.perm[p0 + b]) : make_float2(0.f, 0.f);
+    for (int q = tid; q < nb * R8; q += kLeafThreads) {
+      const int b = q / R8, k = q - b * R8;
+      vs[q] = k < R ? item_entry(ibase, it, p0 - pg + b0 + b, k) : make_float2(0.f, 0.f);
+    }
+    for (int q = tid; q < nb * NR; q += kLeafThreads) {   // rows of the tree-ordered panel
+      const int b = q / NR, nn = q - b * NR;
+      xs[b * NRP + nn] = __ldcg(a.vec + int64_t(p0 + b0 + b) * NR + nn);
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < c * R * kLeafRhs; q += blockDim.x) {
-      const int r = q % kLeafRhs, k = (q / kLeafRhs) % R, t = q / (kLeafRhs * R);
-      float2 s = make_float2(0.f, 0.f);
-      for (int b = bnd[t]; b < bnd[t + 1]; ++b) {
-        const float ar = re_s[b * R + k], ai = im_s[b * R + k];   // stored conj(V)
-        const float2 x = xs[b * kLeafRhs + r];
-        s.x = fmaf(ar, x.x, fmaf(-ai, x.y, s.x));
-        s.y = fmaf(ar, x.y, fmaf(ai, x.x, s.y));
+    for (int b = 0; b < nb; ++b) {
+      const float2 x = xs[b * NRP + n];
+#pragma unroll
+      for (int m = 0; m < MM; ++m) {
+        const int k0 = 4 * (m * KT + kq);
+        if (k0 < R8) {
+          const float4 v01 = *reinterpret_cast<const float4*>(vs + b * R8 + k0);
+          const float4 v23 = *reinterpret_cast<const float4*>(vs + b * R8 + k0 + 2);
+          const float vr[4] = {v01.x, v01.z, v23.x, v23.z}, vi[4] = {v01.y, v01.w, v23.y, v23.w};
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            acc[m][j].x = fmaf(vr[j], x.x, fmaf(-vi[j], x.y, acc[m][j].x));
+            acc[m][j].y = fmaf(vr[j], x.y, fmaf(vi[j], x.x, acc[m][j].y));
+          }
+        }
       }
-      a.outp[(int64_t(c * g + t) * R + k) * a.NR + r0 + r] = s;
+    }
+  }
+  // split block `leaf`: byte (hl, k, ri, n) as in apply.hpp; 4 consecutive k = 8 bytes
+  const int64_t half = int64_t(R8) * 256;
+  uint8_t* ob = a.outs + int64_t(leaf) * split_block_bytes(R8) + (n >> 3) * 128 + (n & 7) * 16;
+#pragma unroll
+  for (int m = 0; m < MM; ++m) {
+    const int k0 = 4 * (m * KT + kq);
+    if (k0 < R8) {
+      float re[4], im[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        re[j] = acc[m][j].x;
+        im[j] = acc[m][j].y;
+      }
+      uint32_t hr[2], lr[2], hi[2], li[2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        hr[i] = tc::pack_bf16x2(re[2 * i], re[2 * i + 1]);
+        lr[i] = tc::pack_bf16x2(re[2 * i] - __uint_as_float(hr[i] << 16), re[2 * i + 1] - __uint_as_float(hr[i] & 0xffff0000u));
+        hi[i] = tc::pack_bf16x2(im[2 * i], im[2 * i + 1]);
+        li[i] = tc::pack_bf16x2(im[2 * i] - __uint_as_float(hi[i] << 16), im[2 * i + 1] - __uint_as_float(hi[i] & 0xffff0000u));
+      }
+      uint8_t* o = ob + (k0 >> 3) * 2048 + (k0 & 7) * 2;
+      *reinterpret_cast<uint2*>(o) = make_uint2(hr[0], hr[1]);                 // Re hi
+      *reinterpret_cast<uint2*>(o + 1024) = make_uint2(hi[0], hi[1]);          // Im hi
+      *reinterpret_cast<uint2*>(o + half) = make_uint2(lr[0], lr[1]);          // Re lo
+      *reinterpret_cast<uint2*>(o + half + 1024) = make_uint2(li[0], li[1]);   // Im lo
     }
   }
 }
 
-// U^L for a panel: u[r][perm(a)] = sum_k U^L_t[a][k] w[(c g + t) R + k][r] for the points a
-// of leaf t of group g (item stored by columns: line = k, entry = point).
+// U^L for a panel, leaf j = c g + t: u[rhs0 + n][perm(b)] = sum_k U^L_j[b][k] w[j R + k][n]
+// for the points b of leaf j.  The group's item is stored by columns (line = k, entry =
+// point of the group); the leaf's coefficient rows are R contiguous rows of 64 real
+// then 64 imaginary parts.  Thread (n, bq) computes column n for the points
+// b = bq + m BT of each chunk.
 __global__ void __launch_bounds__(kLeafThreads) leaf_u_kernel(const __grid_constant__ LeafArgs a) {
-  extern __shared__ __align__(16) float lsm[];
-  const int g = blockIdx.x, c = a.c, R = a.R;
+  constexpr int NR = kTcNR, BT = kLeafThreads / NR, MB = kLeafChunk / BT;
+  extern __shared__ __align__(16) float2 lsm[];
+  const int leaf = blockIdx.x, c = a.c, R = a.R, RP = a.R + 1;
+  const int g = leaf / c;
+  const int pg = a.off[c * g], p0 = a.off[leaf], np = a.off[leaf + 1] - p0;
+  if (np == 0) return;
   const Item it = a.items[a.item_base + int64_t(g) * a.item_stride];
-  const int p0 = a.off[c * g], npts = a.off[c * g + c] - p0;
-  float* re_s = lsm;                                         // [k][point]
-  float* im_s = re_s + kMaxGroupPoints * R;
-  float2* ws = reinterpret_cast<float2*>(im_s + kMaxGroupPoints * R);   // [c R][kLeafRhs]
-  int* bnd = reinterpret_cast<int*>(ws + c * R * kLeafRhs);
-  if (threadIdx.x <= c) bnd[threadIdx.x] = a.off[c * g + threadIdx.x] - p0;
-  stage_item(a, it, re_s, im_s);
-  const int len = it.len;   // = npts (at least 1)
-  for (int r0 = 0; r0 < a.NR; r0 += kLeafRhs) {
+  const uint8_t* ibase = a.arena + size_t(it.off128) * 128;
+  float2* ws = lsm;                 // [R][NR]
+  float2* us = ws + R * NR;         // [kLeafChunk][R + 1]
+  const int tid = threadIdx.x, n = tid % NR, bq = tid / NR, rhs = a.rhs0 + n;
+  const float* wsrc = a.wl + int64_t(leaf) * R * 2 * NR;
+  for (int q = tid; q < R * NR; q += kLeafThreads) {
+    const int k = q / NR, nn = q - k * NR;
+    ws[q] = make_float2(__ldcg(wsrc + k * 2 * NR + nn), __ldcg(wsrc + k * 2 * NR + NR + nn));
+  }
+  for (int b0 = 0; b0 < np; b0 += kLeafChunk) {
+    const int nb = min(kLeafChunk, np - b0);
     __syncthreads();
-    for (int q = threadIdx.x; q < c * R * kLeafRhs; q += blockDim.x) {
-      const int r = q % kLeafRhs, m = q / kLeafRhs;
-      ws[q] = __ldcg(a.vec + (int64_t(c * g) * R + m) * a.NR + r0 + r);
+    for (int q = tid; q < nb * R; q += kLeafThreads) {
+      const int k = q / nb, b = q - k * nb;
+      us[b * RP + k] = item_entry(ibase, it, k, p0 - pg + b0 + b);
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < npts * kLeafRhs; q += blockDim.x) {
-      const int r = q % kLeafRhs, pt = q / kLeafRhs;
-      int t = 0;
-      while (t + 1 < c && pt >= bnd[t + 1]) ++t;
-      float2 s = make_float2(0.f, 0.f);
-      for (int k = 0; k < R; ++k) {
-        const float ar = re_s[k * len + pt], ai = im_s[k * len + pt];
-        const float2 w = ws[(t * R + k) * kLeafRhs + r];
-        s.x = fmaf(ar, w.x, fmaf(-ai, w.y, s.x));
-        s.y = fmaf(ar, w.y, fmaf(ai, w.x, s.y));
+    float2 acc[MB];
+#pragma unroll
+    for (int m = 0; m < MB; ++m) acc[m] = make_float2(0.f, 0.f);
+    for (int k = 0; k < R; ++k) {
+      const float2 w = ws[k * NR + n];
+#pragma unroll
+      for (int m = 0; m < MB; ++m) {
+        const float2 v = us[(bq + m * BT) * RP + k];   // rows past nb hold stale values, never stored
+        acc[m].x = fmaf(v.x, w.x, fmaf(-v.y, w.y, acc[m].x));
+        acc[m].y = fmaf(v.x, w.y, fmaf(v.y, w.x, acc[m].y));
       }
-      const int rhs = a.rhs0 + r0 + r;
-      if (rhs < a.nrhs) a.outp[int64_t(rhs) * a.len_out + a.perm[p0 + pt]] = s;
+    }
+    if (rhs < a.nrhs) {
+      float2* orow = a.outp + int64_t(rhs) * a.len_out;
+#pragma unroll
+      for (int m = 0; m < MB; ++m) {
+        const int b = bq + m * BT;
+        if (b < nb) orow[a.perm[p0 + b0 + b]] = acc[m];
+      }
     }
   }
 }
 
 // ------------------------------------------------------------------ host side
 
-size_t tc_smem_bytes(int nsa, int mpad, int NR, int kpad_max) {
-  return size_t(nsa) * 4 * size_t(mpad) * 32 + 2 * 4 * size_t(NR) * size_t(kpad_max) * 2 + (2 * size_t(nsa) + 16) * 8 + 64;
+size_t tc_smem_bytes(int nsa, int nxb, int nsets, int mt_max, int kpad_max) {
+  return size_t(nsa) * 4 * size_t(mt_max) * 32 + size_t(nxb) * 2 * size_t(kpad_max) * 256 +
+         size_t(nsets) * 2 * kTcChunk * 128 * sizeof(float) + (2 * size_t(nsa) + 16) * 8 + 64;
 }
 
-size_t leaf_smem_bytes(int R, int c) {
-  return size_t(2) * kMaxGroupPoints * R * sizeof(float) +
-         sizeof(float2) * size_t(std::max(kMaxGroupPoints, c * R)) * kLeafRhs + 64 * sizeof(int);
+size_t leaf_smem_bytes(int R, bool u_side) {
+  const int R8 = (R + 7) & ~7;
+  return sizeof(float2) * (u_side ? size_t(R) * kTcNR + size_t(kLeafChunk) * (R + 1)
+                                  : size_t(kLeafChunk) * R8 + size_t(kLeafChunk) * (kTcNR + 1));
 }
+
+bool leaf_fits(int R8) { return R8 <= kLeafMaxR8; }
 
 cudaError_t launch_apply_tc(const TCArgs& a, int grid, size_t smem, cudaStream_t stream) {
   cudaError_t err = cudaMemsetAsync(a.counters, 0, tc_counter_bytes(a.plan), stream);
@@ -570,12 +707,17 @@ size_t tc_counter_bytes(const TCPlan& plan) {
   return (n * sizeof(unsigned) + 255) & ~size_t(255);
 }
 
-cudaError_t launch_leaf(const LeafArgs& a, bool u_side, int n_groups, cudaStream_t stream) {
-  const size_t smem = leaf_smem_bytes(a.R, a.c);
-  auto kern = u_side ? leaf_u_kernel : leaf_v_kernel;
+cudaError_t launch_permute_in(const LeafArgs& a, cudaStream_t stream) {
+  permute_in_kernel<<<unsigned((a.len_vec + kPermTile - 1) / kPermTile), kLeafThreads, 0, stream>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_leaf(const LeafArgs& a, bool u_side, int n_leaves, cudaStream_t stream) {
+  const size_t smem = leaf_smem_bytes(a.R, u_side);
+  void (*kern)(LeafArgs) = u_side ? leaf_u_kernel : leaf_v_kernel;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (err != cudaSuccess) return err;
-  kern<<<n_groups, kLeafThreads, smem, stream>>>(a);
+  kern<<<n_leaves, kLeafThreads, smem, stream>>>(a);
   return cudaGetLastError();
 }
 

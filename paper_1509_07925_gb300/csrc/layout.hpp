@@ -76,12 +76,13 @@ struct Plan {
 // plane M8 = roundup(M_t, 8) rows by 16 columns in 8x8 core matrices (128 B), the two
 // core matrices of a row group adjacent (K-major, no swizzle).
 struct TCStage {
-  int32_t n_groups, M_t, K_t, M8, K_pad, MB;   // MB = ceil(M_t / 128) row blocks
+  int32_t n_groups;
+  int32_t M_t, K_t, K_pad, pad_;  // tile rows c R8_out (<= 256), columns c R8_in (K_pad: to 16)
   int32_t in_pat, out_pat, R_in, R_out, B, ch;
-  int64_t base;          // arena offset of group 0
-  int64_t tile_bytes;    // bytes per group tile (K_pad / 16 chunks)
-  int32_t plane_bytes;   // M8 * 32
-  int32_t pad_;
+  int32_t R8_in, R8_out;          // ranks rounded up to 8: one vector block holds R8 entries
+  int32_t plane_bytes, last;      // one K16 chunk of one A plane (M_t x 16 bf16); last main stage
+  int64_t base;                   // arena offset of group 0
+  int64_t tile_bytes;             // (K_pad / 16) chunks x 4 planes x plane_bytes
 };
 
 struct TCPlan {
@@ -89,7 +90,7 @@ struct TCPlan {
   TCStage st[kMaxStages];
 };
 
-constexpr int kTcMaxRows = 256;   // M_t limit (two 128-row MMA blocks)
+constexpr int kTcMaxRows = 256;   // M_t limit (the MMA's N)
 constexpr int kTcMaxK = 256;      // K_t limit
 
 MBF_HD int64_t pad4(int64_t x) { return (x + 3) & ~int64_t(3); }

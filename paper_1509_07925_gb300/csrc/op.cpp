@@ -210,42 +210,46 @@ float bf16_to_float(uint16_t h) {
 
 // Split-bf16 tiles of every G^l / (H^l)^* group product (the main stages of the SIMT
 // plan; the last G stage writes the level-L coefficient vector instead of applying U^L).
-// Tile element (m, k) of a group = output entry m, input entry k, exactly as the SIMT
-// main items; value x (FP64) is stored as hi = bf16(x), lo = bf16(x - hi) for the real and
-// imaginary parts.
-void pack_tc(const mbf_factors_t& f, const Plan& sp, TCPlan& tp, std::vector<uint8_t>& arena, int& mpad,
+// Ranks are rounded up to R8 (a multiple of 8) with zero rows and columns, so that every
+// tree-node pair owns a whole number of 8-row core matrices.  Tile element (m, k) of a
+// group = output entry m = (t, k2), input entry k = (tp, kk), with m = t R8_out + k2 and
+// k = tp R8_in + kk; value x (FP64) is stored as hi = bf16(x), lo = bf16(x - hi) for the
+// real and imaginary parts, each plane K-major in 8 x 8 core matrices.
+void pack_tc(const mbf_factors_t& f, const Plan& sp, TCPlan& tp, std::vector<uint8_t>& arena, int& mt_max,
              int& kpad_max) {
   const int c = 1 << f.dim, L = f.L, h = L / 2;
   auto cplx = [](const double* a, int64_t i) { return cd(a[2 * i], a[2 * i + 1]); };
+  auto r8 = [](int r) { return (r + 7) & ~7; };
   tp = TCPlan{};
   tp.c = c;
   tp.d = f.dim;
   tp.L = L;
-  mpad = 128;
+  mt_max = 16;
   kpad_max = 16;
   int n = 0;
   for (int e = 1; e < sp.n_stages; ++e) {
     const Stage& st = sp.st[e];
     TCStage& ts = tp.st[n++];
     ts.n_groups = st.n_groups;
-    ts.M_t = c * st.R_out;
-    ts.K_t = c * st.R_in;
-    if (ts.M_t > kTcMaxRows || ts.K_t > kTcMaxK) fail(MBF_ERR_INVALID, "tile too large for the tensor path");
-    ts.M8 = (ts.M_t + 7) & ~7;
-    ts.K_pad = (ts.K_t + 15) & ~15;
-    ts.MB = (ts.M_t + 127) / 128;
-    ts.in_pat = st.in_pat;
-    ts.out_pat = st.out_pat == PAT_LEAF ? PAT_SPLIT : st.out_pat;   // B = 1: writes leaf c g + t
     ts.R_in = st.R_in;
     ts.R_out = st.R_out;
+    ts.R8_in = r8(st.R_in);
+    ts.R8_out = r8(st.R_out);
+    ts.M_t = c * ts.R8_out;
+    ts.K_t = c * ts.R8_in;
+    if (ts.M_t > kTcMaxRows || ts.K_t > kTcMaxK) fail(MBF_ERR_INVALID, "tile too large for the tensor path");
+    ts.K_pad = (ts.K_t + 15) & ~15;
+    ts.in_pat = st.in_pat;
+    ts.last = e == sp.n_stages - 1;
+    ts.out_pat = st.out_pat == PAT_LEAF ? PAT_SPLIT : st.out_pat;   // B = 1: writes block c g + t
     ts.B = st.B;
     ts.ch = st.ch;
-    ts.plane_bytes = ts.M8 * 32;
+    ts.plane_bytes = ts.M_t * 32;
     ts.tile_bytes = int64_t(ts.K_pad / 16) * 4 * ts.plane_bytes;
     size_t base = (arena.size() + 127) & ~size_t(127);
     ts.base = int64_t(base);
     arena.resize(base + size_t(ts.tile_bytes) * size_t(ts.n_groups), 0);
-    mpad = std::max(mpad, ts.MB * 128);
+    mt_max = std::max(mt_max, ts.M_t);
     kpad_max = std::max(kpad_max, ts.K_pad);
     const int l = st.level, R1 = st.side == 1 ? f.RV[l] : f.RU[l], R2 = st.side == 1 ? f.RV[l + 1] : f.RU[l + 1];
     const double* M = st.side == 1 ? f.H[l - h] : f.G[l - h];
@@ -254,12 +258,14 @@ void pack_tc(const mbf_factors_t& f, const Plan& sp, TCPlan& tp, std::vector<uin
       const int64_t i = g / st.B, jp = g % st.B;
       for (int m = 0; m < ts.M_t; ++m)
         for (int k = 0; k < ts.K_t; ++k) {
+          const int mo = m / ts.R8_out, mi = m % ts.R8_out, ko = k / ts.R8_in, ki = k % ts.R8_in;
+          if (mi >= ts.R_out || ki >= ts.R_in) continue;   // zero padding
           cd v;
           if (st.side == 1) {   // T[(tp,k)][(t,k2)] = conj(H^l_{c j + t, ip}[k2][(tp,k)])
-            const int tp_ = m / R1, kk = m % R1, t = k / R2, k2 = k % R2;
+            const int tp_ = mo, kk = mi, t = ko, k2 = ki;
             v = std::conj(cplx(M, ((((g * c + t) * R2 + k2) * c + tp_) * R1) + kk));
           } else {              // T[(t,k2)][(tp,k)] = G^l_{c i + t, jp}[k2][(tp,k)] (x S^h at l = h)
-            const int t = m / R2, k2 = m % R2, tp_ = k / R1, kk = k % R1;
+            const int t = mo, k2 = mi, tp_ = ko, kk = ki;
             v = cplx(M, ((((g * c + t) * R2 + k2) * c + tp_) * R1) + kk);
             if (l == h) v *= f.S[(i * st.ch + (c * jp + tp_)) * R1 + kk];
           }
@@ -450,6 +456,8 @@ void op_free(mbf_op_s* op) {
   cudaFree(op->d_tc_arena);
   cudaFree(op->d_tc_bufs);
   cudaFree(op->d_tc_counters);
+  cudaFree(op->d_tc_gt);
+  cudaFree(op->d_w_inv);
   cudaSetDevice(prev);
   delete op;
 }
@@ -500,7 +508,7 @@ mbf_op_s* op_create(const mbf_factors_t& f) {
     // the SIMT path only and says why
     try {
       std::vector<uint8_t> tc_arena;
-      pack_tc(f, op->plan, op->tcplan, tc_arena, op->tc_mpad, op->tc_kpad_max);
+      pack_tc(f, op->plan, op->tcplan, tc_arena, op->tc_mt_max, op->tc_kpad_max);
       const Stage& first = op->plan.st[0];
       const Stage& last = op->plan.st[op->plan.n_stages - 1];
       if (op->plan.n_stages < 2 || first.n_items != 1 || last.n_items != 2 || last.B != 1 ||
@@ -508,12 +516,22 @@ mbf_op_s* op_create(const mbf_factors_t& f) {
         fail(MBF_ERR_INVALID, "plan shape not supported by the tensor path");
       int optin = 0;
       cuda_check(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, op->device), "attr");
-      for (int R : {op->RU[size_t(op->L)], op->RV[size_t(op->L)]})
-        if (leaf_smem_bytes(R, op->c) > size_t(optin)) fail(MBF_ERR_INVALID, "leaf rank too large for the tensor path");
-      int mb_max = 1;
-      for (int e = 0; e < op->tcplan.n_stages; ++e) mb_max = std::max(mb_max, op->tcplan.st[e].MB);
-      if (4 * mb_max * 32 > 512 || tc_smem_bytes(3, op->tc_mpad, 32, op->tc_kpad_max) > size_t(optin))
-        fail(MBF_ERR_INVALID, "tiles too large for the tensor path");
+      if (!leaf_fits(op->tcplan.st[0].R8_in) || leaf_smem_bytes(op->RU[size_t(op->L)], true) > size_t(optin))
+        fail(MBF_ERR_INVALID, "leaf rank too large for the tensor path");
+      // accumulator sets (2 M_t TMEM columns each), panel buffers, A ring slots
+      op->tc_nsets = 4 * op->tc_mt_max <= 512 ? 2 : 1;
+      op->tc_nxb = 2;
+      auto smem = [&](int nsa) { return tc_smem_bytes(nsa, op->tc_nxb, op->tc_nsets, op->tc_mt_max, op->tc_kpad_max); };
+      if (smem(2) > size_t(optin)) op->tc_nxb = 1;
+      if (smem(2) > size_t(optin)) fail(MBF_ERR_INVALID, "tiles too large for the tensor path");
+      op->tc_nsa = 2;
+      while (op->tc_nsa < 8 && smem(op->tc_nsa + 1) <= size_t(optin)) ++op->tc_nsa;
+      // more than half the SM's shared memory: one CTA per SM, so that each CTA's
+      // 512-column TMEM allocation never waits on another CTA of the same launch
+      op->tc_smem = std::max(smem(op->tc_nsa), size_t(optin) / 2 + 1024);
+      std::vector<int32_t> winv(size_t(std::max<int64_t>(f.n_in, 1)), -1);
+      for (int64_t p = 0; p < f.n_w; ++p) winv[size_t(f.w_perm[p])] = int32_t(p);
+      op->d_w_inv = dev_upload(winv, "inverse Omega permutation");
       op->tc_bytes = int64_t(tc_arena.size());
       op->d_tc_arena = dev_upload(tc_arena, "tensor-core arena");
     } catch (const Error& err) {
@@ -526,75 +544,72 @@ mbf_op_s* op_create(const mbf_factors_t& f) {
   return op;
 }
 
-// Tensor-core apply for panels of up to kTcMaxNR RHS: leaf kernel ((V^L)^*), the
-// persistent tcgen05 kernel over the G / H levels, leaf kernel (U^L), per panel.
+// Tensor-core apply, per panel of 64 RHS: permute the panel into Omega-tree order, the
+// (V^L)^* leaf kernel, the persistent tcgen05 kernel over the G / H levels, the U^L leaf
+// kernel.
 void apply_tc(mbf_op_s* op, const float2* g, float2* u, int64_t nrhs, cudaStream_t st) {
   if (!op->tc_unavailable.empty()) fail(MBF_ERR_INVALID, "tensor path unavailable: " + op->tc_unavailable);
   const TCPlan& tp = op->tcplan;
   const int S = tp.n_stages;
-  const int64_t vec = op->positions * kTcMaxNR;
+  // one vector: every block of a level at the largest R8, split or complex64 (8 bytes an entry)
+  int r8max = 8;
+  for (int e = 0; e < S; ++e) r8max = std::max({r8max, tp.st[e].R8_in, tp.st[e].R8_out});
+  const int64_t vec_bytes = Tree::ipow(op->c, op->L) * split_block_bytes(r8max);
   if (!op->d_tc_bufs) {
-    if (cudaMalloc(&op->d_tc_bufs, size_t(S + 1) * size_t(vec) * sizeof(float2)) != cudaSuccess)
+    if (cudaMalloc(&op->d_tc_bufs, size_t(S + 1) * size_t(vec_bytes)) != cudaSuccess)
       fail(MBF_ERR_OOM, "cudaMalloc tensor-path workspace");
     if (cudaMalloc(&op->d_tc_counters, tc_counter_bytes(tp)) != cudaSuccess)
       fail(MBF_ERR_OOM, "cudaMalloc tensor-path counters");
+    if (cudaMalloc(&op->d_tc_gt, size_t(std::max<int64_t>(op->n_w, 1)) * kTcNR * sizeof(float2)) != cudaSuccess)
+      fail(MBF_ERR_OOM, "cudaMalloc tensor-path input panel");
   }
-  int dev = 0, sms = 0, optin = 0;
+  int dev = 0, sms = 0;
   cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
   cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "attr");
-  cuda_check(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "attr");
-  int mb_max = 1;
-  for (int e = 0; e < S; ++e) mb_max = std::max(mb_max, tp.st[e].MB);
   const Stage& leaf_st = op->plan.st[0];
   const Stage& last_st = op->plan.st[op->plan.n_stages - 1];
-  const int RL_w = op->RV[size_t(op->L)], RL_x = op->RU[size_t(op->L)];
-  // panel width: a multiple of 32 (the epilogue reads the accumulators 32 columns at a
-  // time), within the shared-memory and TMEM budgets (4 accumulator column blocks of NR
-  // per 128-row block, two accumulator sets)
-  int NR = int(std::min<int64_t>(kTcMaxNR, (nrhs + 31) / 32 * 32));
-  while (NR > 32 && (4 * mb_max * NR > 512 || tc_smem_bytes(3, op->tc_mpad, NR, op->tc_kpad_max) > size_t(optin)))
-    NR -= 32;
-  if (4 * mb_max * NR > 512 || tc_smem_bytes(3, op->tc_mpad, NR, op->tc_kpad_max) > size_t(optin))
-    fail(MBF_ERR_INVALID, "tensor path does not fit shared memory for this operator");
-  for (int64_t r0 = 0; r0 < nrhs; r0 += NR) {
-    int nsa = 3;
-    while (nsa < 8 && tc_smem_bytes(nsa + 1, op->tc_mpad, NR, op->tc_kpad_max) <= size_t(optin)) ++nsa;
-    // more than half the SM's shared memory: one CTA per SM, so that each CTA's
-    // 512-column TMEM allocation never waits on another CTA of the same launch
-    const size_t smem = std::max(tc_smem_bytes(nsa, op->tc_mpad, NR, op->tc_kpad_max), size_t(optin) / 2 + 1024);
-    float2* yl = op->d_tc_bufs;              // level-L input vector of the main stages
-    float2* bufs = op->d_tc_bufs + vec;      // main stage e writes bufs + e * vec
-    // (V^L)^*: g -> yl
+  uint8_t* yl = op->d_tc_bufs;                       // level-L input of the main stages
+  uint8_t* bufs = yl + vec_bytes;                    // main stage e < S - 1 writes bufs + e * vec_bytes
+  float* ylast = reinterpret_cast<float*>(yl + int64_t(S) * vec_bytes);   // last main stage
+  for (int64_t r0 = 0; r0 < nrhs; r0 += kTcNR) {
+    // g -> panel in tree order
+    LeafArgs pa{};
+    pa.perm = op->d_w_inv;
+    pa.vec = g;
+    pa.outp = op->d_tc_gt;
+    pa.len_vec = op->n_in;
+    pa.nrhs = int32_t(nrhs);
+    pa.rhs0 = int32_t(r0);
+    cuda_check(launch_permute_in(pa, st), "panel permute launch");
+    // (V^L)^*: panel -> yl
     LeafArgs la{};
     la.arena = op->d_arena;
     la.items = op->d_items;
     la.item_base = leaf_st.item_base;
-    la.perm = op->d_w_perm;
-    la.off = op->d_w_off;
-    la.vec = g;
-    la.outp = yl;
-    la.len_vec = op->n_in;
-    la.nrhs = int32_t(nrhs);
-    la.rhs0 = int32_t(r0);
-    la.NR = NR;
-    la.c = op->c;
-    la.R = RL_w;
     la.item_stride = leaf_st.n_items;
-    cuda_check(launch_leaf(la, false, leaf_st.n_groups, st), "leaf (V^L)^* launch");
+    la.off = op->d_w_off;
+    la.vec = op->d_tc_gt;
+    la.outs = yl;
+    la.c = op->c;
+    la.R = op->RV[size_t(op->L)];
+    la.R8 = tp.st[0].R8_in;
+    cuda_check(launch_leaf(la, false, leaf_st.n_groups * op->c, st), "leaf (V^L)^* launch");
     // G / H levels on tensor cores
     TCArgs ta{};
     ta.arena = op->d_tc_arena;
     ta.x_in = yl;
     ta.bufs = bufs;
-    ta.buf_stride = int64_t(NR) * op->positions;
+    ta.y_out = ylast;
+    ta.buf_stride = vec_bytes;
     ta.counters = op->d_tc_counters;
     ta.status = op->d_status;
-    ta.NR = NR;
-    ta.nsa = nsa;
-    ta.mpad = op->tc_mpad;
+    ta.nsa = op->tc_nsa;
+    ta.nxb = op->tc_nxb;
+    ta.nsets = op->tc_nsets;
+    ta.mt_max = op->tc_mt_max;
     ta.kpad_max = op->tc_kpad_max;
     ta.plan = tp;
-    cuda_check(launch_apply_tc(ta, sms, smem, st), "tensor-core launch");
+    cuda_check(launch_apply_tc(ta, sms, op->tc_smem, st), "tensor-core launch");
     // U^L: last main stage output -> u
     LeafArgs lu{};
     lu.arena = op->d_arena;
@@ -603,15 +618,14 @@ void apply_tc(mbf_op_s* op, const float2* g, float2* u, int64_t nrhs, cudaStream
     lu.item_stride = last_st.n_items;
     lu.perm = op->d_x_perm;
     lu.off = op->d_x_off;
-    lu.vec = bufs + int64_t(S - 1) * NR * op->positions;
+    lu.wl = ylast;
     lu.outp = u;
     lu.len_out = op->n_out;
     lu.nrhs = int32_t(nrhs);
     lu.rhs0 = int32_t(r0);
-    lu.NR = NR;
     lu.c = op->c;
-    lu.R = RL_x;
-    cuda_check(launch_leaf(lu, true, last_st.n_groups, st), "leaf U^L launch");
+    lu.R = op->RU[size_t(op->L)];
+    cuda_check(launch_leaf(lu, true, last_st.n_groups * op->c, st), "leaf U^L launch");
   }
 }
 

@@ -34,9 +34,12 @@ struct mbf_op_s {
   mbf::TCPlan tcplan{};
   uint8_t* d_tc_arena = nullptr;
   int64_t tc_bytes = 0;
-  int tc_mpad = 128, tc_kpad_max = 16, tc_grid = 0;
-  float2* d_tc_bufs = nullptr;        // [S_main + 1] vectors of positions x kTcMaxNR
+  int tc_mt_max = 16, tc_kpad_max = 16, tc_nsa = 2, tc_nxb = 2, tc_nsets = 2;
+  size_t tc_smem = 0;
+  uint8_t* d_tc_bufs = nullptr;       // S_main + 1 vectors of c^L blocks x R8 x 64 entries (8 bytes each)
   unsigned* d_tc_counters = nullptr;
+  float2* d_tc_gt = nullptr;          // input panel in Omega-tree order [n_w][64]
+  int32_t* d_w_inv = nullptr;         // natural Omega index -> tree position (-1: not in the tree)
   std::string tc_unavailable;         // why the tensor path cannot run for this operator ("" if it can)
   // staging for mbf_apply_host
   float2 *d_stage_in = nullptr, *d_stage_out = nullptr;
