@@ -1,10 +1,12 @@
 """Benchmark of the butterfly-factorization apply on GB300.
 
 Default workload: 2-D FIO K = exp(2 pi i (x.xi + c(x)|xi|)), polar tree on Omega,
-n = 256 (N = 65,536), depth L = 6, rank r = 24, one right-hand side.  One *step*
-is one full apply u = K_f g (all stages: (V^L)^*, (H^l)^*, M^h, G^l, U^L) of one
-batch of synthetic input already resident in HBM.  Factors (about 420 MB of
-complex64) exceed the 129 MB L2, so no flush is needed between steps.
+n = 256 (N = 65,536), depth L = 6, rank r = 24.  One *step* is one full apply
+u = K_f g (all stages: (V^L)^*, (H^l)^*, M^h, G^l, U^L) of one batch of synthetic
+input already resident in HBM.  The headline leg applies 64 RHS on the tensor cores
+(split-BF16x3); a second leg applies 1 RHS with the FP32 SIMT kernel.  Factors (about
+420 MB of complex64; 450 MB of tensor tiles) exceed the 129 MB L2, so no flush is
+needed between steps.
 
 Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle's FP64
 factor apply on a bounded sample of the same workload instead.
@@ -119,7 +121,7 @@ class ClockSampler:
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("apply_simt.cu", "layout.hpp", "apply.hpp"):
+    for f in ("apply_simt.cu", "apply_tc.cu", "layout.hpp", "apply.hpp", "op.cpp"):
         with open(os.path.join(ROOT, "paper_1509_07925_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -173,7 +175,7 @@ def run_reference(args, rank, world):
     from paper_1509_07925_gb300 import buildlib
     buildlib.build()
     wl = WORKLOADS[args.workload]
-    nrhs = args.nrhs or wl.nrhs
+    nrhs = args.nrhs or 64
     hf = build_factors(bd, wl)
     rates = []
     for k in range(args.warmup + args.steps):
@@ -191,6 +193,31 @@ def run_reference(args, rank, world):
                              "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def timed_applies(torch, op, g, u, nrhs, prec, steps, stream):
+    """Device time per apply over `steps` back-to-back applies (CUDA events on the stream)."""
+    sp = stream.cuda_stream
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        op.apply(g.data_ptr(), u.data_ptr(), nrhs, prec, sp)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) / steps
+
+
+def kernel_times(torch, op, g, u, nrhs, prec, steps, stream):
+    """Per-kernel device time per apply: a second pass with the library's kernel timing
+    on (CUDA events around each launch, on the apply's stream)."""
+    op.set_profiling(True)
+    for _ in range(steps):
+        op.apply(g.data_ptr(), u.data_ptr(), nrhs, prec, stream.cuda_stream)
+    torch.cuda.synchronize()
+    prof = op.profile()
+    op.set_profiling(False)
+    return {k: {"launches_per_apply": n / steps, "ms_per_apply": ms / steps}
+            for k, (n, ms) in prof.items() if n}
 
 
 def main():
@@ -211,87 +238,118 @@ def main():
         torch.distributed.barrier()
     buildlib.build()
     wl = WORKLOADS[args.workload]
-    nrhs = args.nrhs or wl.nrhs
     N = wl.N
     hf = build_factors(bd, wl)
     op = bd.Operator(hf)
     info = op.info()
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
-    g = torch.from_numpy(complex_normal(N, nrhs, seed=wl.seed_g).astype(np.complex64)).cuda()
-    u = torch.empty((nrhs, N), dtype=torch.complex64, device="cuda")
+    peak, peak_kind = measured_peaks()
+
+    # legs: the headline (64 RHS on tensor cores, or --nrhs / --precision) and the
+    # single-RHS FP32 SIMT apply it is compared with
+    nrhs = args.nrhs or 64
     if args.precision == "auto":
         args.precision = "bf16x3" if nrhs >= 8 else "fp32_simt"
     prec = {"fp32_simt": bd.MBF_PREC_FP32_SIMT, "bf16x3": bd.MBF_PREC_BF16X3}[args.precision]
-    for _ in range(max(3, args.warmup)):
-        op.apply(g.data_ptr(), u.data_ptr(), nrhs, prec, sp)
-    op.check(sp)
-    torch.cuda.synchronize()
-
+    legs = [("headline", nrhs, prec, args.precision)]
+    if not (nrhs == 1 and args.precision == "fp32_simt"):
+        legs.append(("simt_1rhs", 1, bd.MBF_PREC_FP32_SIMT, "fp32_simt"))
+    res = {}
     clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.3)
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        op.apply(g.data_ptr(), u.data_ptr(), nrhs, prec, sp)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if world > 1:
-        torch.distributed.barrier()
-    clk = clocks.stop()
-    op.check(sp)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    clk = None
+    for name, R, pr, prname in legs:
+        g = torch.from_numpy(complex_normal(N, R, seed=wl.seed_g).astype(np.complex64)).cuda()
+        u = torch.empty((R, N), dtype=torch.complex64, device="cuda")
+        for _ in range(max(3, args.warmup)):
+            op.apply(g.data_ptr(), u.data_ptr(), R, pr, sp)
+        op.check(sp)
+        torch.cuda.synchronize()
+        if name == "headline":
+            clocks.start()
+            time.sleep(0.3)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        ms = timed_applies(torch, op, g, u, R, pr, args.steps, stream)
+        if world > 1:
+            torch.distributed.barrier()
+            t = torch.tensor([ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        if name == "headline":
+            clk = clocks.stop()
+        op.check(sp)
+        kt = kernel_times(torch, op, g, u, R, pr, args.steps, stream)
+        op.check(sp)
+        res[name] = {"nrhs": R, "precision": prname, "ms": ms, "value": world * N * R / (ms * 1e-3),
+                     "kernels": kt}
+        del g, u
+
+    # roofline of the dominant kernel of the headline leg
+    head = res["headline"]
+    R = head["nrhs"]
+    if head["precision"] == "bf16x3":
+        kname = "bf_apply_tc"
+        nnz_tc = sum(info.nnz_stage[s] for s in range(1, info.n_stages)) - info.nnz_leaf_u
+        nL = info.c ** info.L
+        vec = nL * (info.RV[info.L] + info.RU[info.L])        # level-L vectors in and out
+        alg_bytes = 8 * nnz_tc + 8 * R * vec
+        alg_note = ("8 B x nonzeros of the G/H factors (S folded) + 8 B x 64 RHS x (level-L input "
+                    "+ level-L output coefficients), per launch (one 64-RHS panel)")
+    else:
+        kname = "bf_apply_simt"
+        alg_bytes = info.bytes_algorithmic + 16 * N * R
+        alg_note = "8 B x nonzeros of all factors + 8 B in + 8 B out per point and RHS"
+    k_ms = head["kernels"][kname]["ms_per_apply"] / head["kernels"][kname]["launches_per_apply"]
+    achieved = alg_bytes / (k_ms * 1e-3) / 1e9
+    traffic = recorded_traffic(wl.name, R)
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
-    g_host = torch.from_numpy(complex_normal(N, nrhs, seed=wl.seed_g).astype(np.complex64)).pin_memory()
-    u_host = torch.empty((nrhs, N), dtype=torch.complex64).pin_memory()
+    g_host = torch.from_numpy(complex_normal(N, R, seed=wl.seed_g).astype(np.complex64)).pin_memory()
+    u_host = torch.empty((R, N), dtype=torch.complex64).pin_memory()
     import ctypes as C
     lib = bd.lib()
+    hprec = {"fp32_simt": bd.MBF_PREC_FP32_SIMT, "bf16x3": bd.MBF_PREC_BF16X3}[head["precision"]]
     for _ in range(2):
         bd._check(lib.mbf_apply_host(op.handle, C.c_void_p(g_host.data_ptr()),
-                                     C.c_void_p(u_host.data_ptr()), nrhs, prec, C.c_void_p(sp)))
+                                     C.c_void_p(u_host.data_ptr()), R, hprec, C.c_void_p(sp)))
     t0 = time.perf_counter()
     n_e2e = max(3, args.steps // 2)
     for _ in range(n_e2e):
         bd._check(lib.mbf_apply_host(op.handle, C.c_void_p(g_host.data_ptr()),
-                                     C.c_void_p(u_host.data_ptr()), nrhs, prec, C.c_void_p(sp)))
+                                     C.c_void_p(u_host.data_ptr()), R, hprec, C.c_void_p(sp)))
     e2e_s = (time.perf_counter() - t0) / n_e2e
 
-    value = world * N * nrhs / (ms * 1e-3)
-    peak, peak_kind = measured_peaks()
-    alg_bytes = info.bytes_algorithmic + 16 * N * nrhs
-    achieved = alg_bytes / (ms * 1e-3) / 1e9
-    traffic = recorded_traffic(wl.name, nrhs)
+    launches = sum(k["launches_per_apply"] for k in head["kernels"].values())
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 (complex64)", "data": "synthetic",
+        "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (complex64; tensor path: split-bf16x3 operands, f32 accumulate)"
+        if head["precision"] == "bf16x3" else "f32 (complex64)", "data": "synthetic",
         "config": {"workload": wl.name, "kernel": wl.kernel, "tree": wl.transform, "n": wl.n, "N": N,
-                   "L": wl.L, "r": wl.r, "nrhs": nrhs, "precision": args.precision,
+                   "L": wl.L, "r": wl.r, "nrhs": R, "precision": head["precision"],
                    "parallelism": f"replicas{world}",
-                   "l2": f"inputs larger than L2: packed factors {info.bytes_packed / 1e6:.0f} MB > 129 MB",
+                   "l2": f"inputs larger than L2: packed factors {info.bytes_packed / 1e6:.0f} MB "
+                         f"(tensor tiles {info.bytes_tensor / 1e6:.0f} MB) > 129 MB",
                    "factor_bytes_algorithmic": info.bytes_algorithmic,
                    "factor_bytes_packed": info.bytes_packed},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+        "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": f"{peak_kind} hbm_gbs (burst copy)",
-                     "algorithmic_bytes_per_launch": alg_bytes},
-        "e2e": {"value": world * N * nrhs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * N * nrhs,
-                "d2h_bytes_per_step": 8 * N * nrhs},
-        "gpu_launches": args.steps,
+                     "algorithmic_bytes_per_launch": alg_bytes, "algorithmic_bytes": alg_note,
+                     "kernel_ms_per_launch": k_ms},
+        "legs": res,
+        "e2e": {"value": world * N * R / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * N * R,
+                "d2h_bytes_per_step": 8 * N * R},
+        "gpu_launches": int(round(launches * args.steps)),
         "clocks": clk,
     }
+    if "simt_1rhs" in res:
+        line["speedup_vs_simt_1rhs"] = head["value"] / res["simt_1rhs"]["value"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            v, sample, cores = oracle_apply_rate(hf, wl, nrhs)
+            v, sample, cores = oracle_apply_rate(hf, wl, R)
             line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                     "sample": sample}
         except Exception as e:  # the baseline must not hide the GPU number

@@ -163,6 +163,13 @@ typedef struct mbf_op_info {
   int64_t bytes_packed;         /* device bytes of the packed tiles incl. padding         */
   int64_t bytes_stage[32];      /* packed bytes streamed by each forward stage            */
   int32_t grid, threads, smem;  /* persistent launch shape of the SIMT apply              */
+  int64_t nnz_stage[32];        /* nonzero factor entries applied by each forward stage    */
+  int64_t nnz_leaf_u;           /* of which U^L (part of the last stage)                  */
+  int32_t tensor_ok;            /* 1 if the tensor-core path is available                 */
+  int32_t tensor_stages;        /* G / H levels applied by the tensor-core kernel         */
+  int64_t bytes_tensor;         /* device bytes of its split-bf16 tiles                   */
+  int32_t tensor_smem, tensor_slots;  /* its shared memory per CTA and A-ring depth      */
+  char tensor_unavailable[128]; /* why not, if tensor_ok == 0                             */
 } mbf_op_info_t;
 mbf_status mbf_op_info(mbf_op_t op, mbf_op_info_t* info);
 
@@ -201,6 +208,22 @@ mbf_status mbf_apply_static(mbf_op_t op, const void* g, void* u, int64_t nrhs, v
 /* Synchronize `stream` and return MBF_ERR_TIMEOUT if a device wait of a previous
  * apply on this operator ran out of time (and clear the flag), else MBF_OK. */
 mbf_status mbf_op_check(mbf_op_t op, void* stream);
+
+/* Kernel timing, a measurement aid (no counterpart in the paper; off by default).
+ * While enabled, every kernel an apply on this operator launches is bracketed by two
+ * CUDA events recorded on the apply's stream.  mbf_op_profile() waits for those events
+ * and returns, per kernel kind, the launches and their total device time since
+ * profiling was last enabled, then clears them.  Enabling adds two event records per
+ * launch to the stream; it does not change what the kernels compute. */
+#define MBF_PROFILE_KINDS 8
+typedef struct mbf_profile {
+  int32_t n_kinds;
+  char name[MBF_PROFILE_KINDS][32];
+  int64_t launches[MBF_PROFILE_KINDS];
+  double ms[MBF_PROFILE_KINDS];
+} mbf_profile_t;
+mbf_status mbf_op_set_profiling(mbf_op_t op, int32_t enable);
+mbf_status mbf_op_profile(mbf_op_t op, mbf_profile_t* out);
 
 /* Thread-local text of the last error ("" if none). */
 const char* mbf_last_error(void);

@@ -58,7 +58,18 @@ class OpInfo(C.Structure):
                 ("RV", C.c_int32 * 32), ("nnz_algorithmic", C.c_int64),
                 ("bytes_algorithmic", C.c_int64), ("bytes_packed", C.c_int64),
                 ("bytes_stage", C.c_int64 * 32), ("grid", C.c_int32), ("threads", C.c_int32),
-                ("smem", C.c_int32)]
+                ("smem", C.c_int32), ("nnz_stage", C.c_int64 * 32), ("nnz_leaf_u", C.c_int64),
+                ("tensor_ok", C.c_int32), ("tensor_stages", C.c_int32), ("bytes_tensor", C.c_int64),
+                ("tensor_smem", C.c_int32), ("tensor_slots", C.c_int32),
+                ("tensor_unavailable", C.c_char * 128)]
+
+
+PROFILE_KINDS = 8
+
+
+class Profile(C.Structure):
+    _fields_ = [("n_kinds", C.c_int32), ("name", (C.c_char * 32) * PROFILE_KINDS),
+                ("launches", C.c_int64 * PROFILE_KINDS), ("ms", C.c_double * PROFILE_KINDS)]
 
 
 ENTRY_FN = C.CFUNCTYPE(None, C.POINTER(C.c_double), C.c_int64, C.POINTER(C.c_double), C.c_int64,
@@ -82,6 +93,8 @@ SIGNATURES = {
                                  C.c_void_p]),
     "mbf_op_check": (C.c_int, [C.c_void_p, C.c_void_p]),
     "mbf_apply_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
+    "mbf_op_set_profiling": (C.c_int, [C.c_void_p, C.c_int32]),
+    "mbf_op_profile": (C.c_int, [C.c_void_p, C.POINTER(Profile)]),
     "mbf_last_error": (C.c_char_p, []),
     "mbf_version": (C.c_char_p, []),
     "mbf_kernel_dft": (None, [C.POINTER(C.c_double), C.c_int64, C.POINTER(C.c_double), C.c_int64,
@@ -259,6 +272,15 @@ class Operator:
         _check(lib().mbf_apply_host(self._h, g.ctypes.data_as(C.c_void_p),
                                     u.ctypes.data_as(C.c_void_p), nrhs, precision, C.c_void_p(stream)))
         return u
+
+    def set_profiling(self, enable: bool = True):
+        _check(lib().mbf_op_set_profiling(self._h, 1 if enable else 0))
+
+    def profile(self) -> dict:
+        """{kernel: (launches, total ms)} since profiling was enabled or last read."""
+        p = Profile()
+        _check(lib().mbf_op_profile(self._h, C.byref(p)))
+        return {p.name[k].value.decode(): (int(p.launches[k]), float(p.ms[k])) for k in range(p.n_kinds)}
 
     def check(self, stream: int = 0):
         _check(lib().mbf_op_check(self._h, C.c_void_p(stream)))

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -47,6 +48,8 @@ struct Packer {
 
   explicit Packer(const mbf_factors_t& fa) : f(fa) {}
 
+  int64_t stage_nnz = 0, leaf_x_nnz = 0;   // nonzero entries packed (this stage; U^L items)
+
   // Append one item: `nlines` lines of `len` entries, value(line, e) -> complex.
   template <class F>
   Item add_item(int nlines, int len, uint8_t kind, uint8_t t, F value) {
@@ -72,6 +75,10 @@ struct Packer {
           const cd v = value(l0 + l, e);
           re[l * len + e] = float(v.real());
           im[l * len + e] = float(v.imag());
+          if (v != cd(0.0, 0.0)) {
+            ++stage_nnz;
+            if (kind == ITEM_LEAF_X) ++leaf_x_nnz;
+          }
         }
       p += chunk_bytes(nl, len);
     }
@@ -129,6 +136,8 @@ struct Packer {
         items.back().base = int32_t(p0);
       }
       st.bytes = int64_t(arena.size() - a0);
+      op.nnz_stage.push_back(stage_nnz);
+      stage_nnz = 0;
     }
     // ---- H-stages l = L-1 .. h: (H^l)^*
     for (int l = L - 1; l >= h; --l) {
@@ -150,6 +159,8 @@ struct Packer {
         }));
       }
       st.bytes = int64_t(arena.size() - a0);
+      op.nnz_stage.push_back(stage_nnz);
+      stage_nnz = 0;
     }
     // ---- G-stages l = h .. L-1: G^l, the first with M^h folded in, the last fused with U^L
     for (int l = h; l < L; ++l) {
@@ -188,6 +199,8 @@ struct Packer {
         }
       }
       st.bytes = int64_t(arena.size() - a0);
+      op.nnz_stage.push_back(stage_nnz);
+      stage_nnz = 0;
     }
     plan.n_stages = ns;
     (void)nL;
@@ -455,6 +468,10 @@ void op_free(mbf_op_s* op) {
   cudaFree(op->d_stage_out);
   cudaFree(op->d_tc_arena);
   cudaFree(op->d_tc_bufs);
+  for (auto& r : op->prof_pending) {
+    cudaEventDestroy(r.e0);
+    cudaEventDestroy(r.e1);
+  }
   cudaFree(op->d_tc_counters);
   cudaFree(op->d_tc_gt);
   cudaFree(op->d_w_inv);
@@ -478,6 +495,7 @@ mbf_op_s* op_create(const mbf_factors_t& f) {
     op->nnz = f.nnz;
     Packer pk(f);
     pk.run(*op);
+    op->nnz_leaf_x = pk.leaf_x_nnz;
     op->bytes_packed = int64_t(pk.arena.size());
     int64_t rmax = 1;
     for (int l = op->h; l <= op->L; ++l) rmax = std::max<int64_t>({rmax, op->RU[size_t(l)], op->RV[size_t(l)]});
@@ -544,6 +562,39 @@ mbf_op_s* op_create(const mbf_factors_t& f) {
   return op;
 }
 
+// ---------------------------------------------------------------- kernel timing
+enum ProfKind { PK_SIMT = 0, PK_PERMUTE, PK_LEAF_V, PK_TC, PK_LEAF_U, PK_COUNT };
+const char* const kProfNames[PK_COUNT] = {"bf_apply_simt", "permute_in", "leaf_v", "bf_apply_tc", "leaf_u"};
+
+// Records an event before a launch when profiling is on (nullptr otherwise).
+cudaEvent_t prof_begin(mbf_op_s* op, cudaStream_t st) {
+  if (!op->prof_on) return nullptr;
+  cudaEvent_t e = nullptr;
+  cuda_check(cudaEventCreate(&e), "cudaEventCreate");
+  cuda_check(cudaEventRecord(e, st), "cudaEventRecord");
+  return e;
+}
+void prof_end(mbf_op_s* op, int kind, cudaEvent_t e0, cudaStream_t st) {
+  if (!e0) return;
+  cudaEvent_t e1 = nullptr;
+  cuda_check(cudaEventCreate(&e1), "cudaEventCreate");
+  cuda_check(cudaEventRecord(e1, st), "cudaEventRecord");
+  op->prof_pending.push_back({kind, e0, e1});
+}
+void prof_collect(mbf_op_s* op) {
+  for (auto& r : op->prof_pending) {
+    float ms = 0.f;
+    const cudaError_t err = cudaEventSynchronize(r.e1);
+    if (err == cudaSuccess && cudaEventElapsedTime(&ms, r.e0, r.e1) == cudaSuccess) {
+      op->prof_ms[r.kind] += ms;
+      op->prof_launches[r.kind] += 1;
+    }
+    cudaEventDestroy(r.e0);
+    cudaEventDestroy(r.e1);
+  }
+  op->prof_pending.clear();
+}
+
 // Tensor-core apply, per panel of 64 RHS: permute the panel into Omega-tree order, the
 // (V^L)^* leaf kernel, the persistent tcgen05 kernel over the G / H levels, the U^L leaf
 // kernel.
@@ -580,7 +631,9 @@ void apply_tc(mbf_op_s* op, const float2* g, float2* u, int64_t nrhs, cudaStream
     pa.len_vec = op->n_in;
     pa.nrhs = int32_t(nrhs);
     pa.rhs0 = int32_t(r0);
+    cudaEvent_t e0 = prof_begin(op, st);
     cuda_check(launch_permute_in(pa, st), "panel permute launch");
+    prof_end(op, PK_PERMUTE, e0, st);
     // (V^L)^*: panel -> yl
     LeafArgs la{};
     la.arena = op->d_arena;
@@ -593,7 +646,9 @@ void apply_tc(mbf_op_s* op, const float2* g, float2* u, int64_t nrhs, cudaStream
     la.c = op->c;
     la.R = op->RV[size_t(op->L)];
     la.R8 = tp.st[0].R8_in;
+    e0 = prof_begin(op, st);
     cuda_check(launch_leaf(la, false, leaf_st.n_groups * op->c, st), "leaf (V^L)^* launch");
+    prof_end(op, PK_LEAF_V, e0, st);
     // G / H levels on tensor cores
     TCArgs ta{};
     ta.arena = op->d_tc_arena;
@@ -609,7 +664,9 @@ void apply_tc(mbf_op_s* op, const float2* g, float2* u, int64_t nrhs, cudaStream
     ta.mt_max = op->tc_mt_max;
     ta.kpad_max = op->tc_kpad_max;
     ta.plan = tp;
+    e0 = prof_begin(op, st);
     cuda_check(launch_apply_tc(ta, sms, op->tc_smem, st), "tensor-core launch");
+    prof_end(op, PK_TC, e0, st);
     // U^L: last main stage output -> u
     LeafArgs lu{};
     lu.arena = op->d_arena;
@@ -625,7 +682,9 @@ void apply_tc(mbf_op_s* op, const float2* g, float2* u, int64_t nrhs, cudaStream
     lu.rhs0 = int32_t(r0);
     lu.c = op->c;
     lu.R = op->RU[size_t(op->L)];
+    e0 = prof_begin(op, st);
     cuda_check(launch_leaf(lu, true, last_st.n_groups * op->c, st), "leaf U^L launch");
+    prof_end(op, PK_LEAF_U, e0, st);
   }
 }
 
@@ -669,7 +728,9 @@ void apply_impl(mbf_op_s* op, const void* in, void* out, int64_t nrhs, int32_t p
   a.plan = op->plan;
   if (adj && op->n_w < op->n_in)
     cuda_check(cudaMemsetAsync(out, 0, size_t(nrhs) * size_t(op->n_in) * sizeof(float2), st), "cudaMemsetAsync");
+  cudaEvent_t e0 = prof_begin(op, st);
   cuda_check(launch_apply_simt(a, nrb, adj, op->grid, op->smem[nrb], st), "apply launch");
+  prof_end(op, PK_SIMT, e0, st);
 }
 
 template <class F>
@@ -775,6 +836,42 @@ mbf_status mbf_op_info(mbf_op_t op, mbf_op_info_t* info) {
     info->grid = op->grid;
     info->threads = simt_threads(1);
     info->smem = int(op->smem[1]);
+    for (size_t e = 0; e < op->nnz_stage.size() && e < 32; ++e) info->nnz_stage[e] = op->nnz_stage[e];
+    info->nnz_leaf_u = op->nnz_leaf_x;
+    info->tensor_ok = op->tc_unavailable.empty() ? 1 : 0;
+    info->tensor_stages = op->tcplan.n_stages;
+    info->bytes_tensor = op->tc_bytes;
+    info->tensor_smem = int(op->tc_smem);
+    info->tensor_slots = op->tc_nsa;
+    std::snprintf(info->tensor_unavailable, sizeof(info->tensor_unavailable), "%s", op->tc_unavailable.c_str());
+  });
+}
+
+mbf_status mbf_op_set_profiling(mbf_op_t op, int32_t enable) {
+  return guard([&] {
+    if (!op) fail(MBF_ERR_INVALID, "NULL operator");
+    prof_collect(op);
+    op->prof_on = enable != 0;
+    for (int k = 0; k < 8; ++k) {
+      op->prof_launches[k] = 0;
+      op->prof_ms[k] = 0.0;
+    }
+  });
+}
+
+mbf_status mbf_op_profile(mbf_op_t op, mbf_profile_t* out) {
+  return guard([&] {
+    if (!op || !out) fail(MBF_ERR_INVALID, "NULL argument");
+    prof_collect(op);
+    std::memset(out, 0, sizeof(*out));
+    out->n_kinds = PK_COUNT;
+    for (int k = 0; k < PK_COUNT; ++k) {
+      std::snprintf(out->name[k], sizeof(out->name[k]), "%s", kProfNames[k]);
+      out->launches[k] = op->prof_launches[k];
+      out->ms[k] = op->prof_ms[k];
+      op->prof_launches[k] = 0;
+      op->prof_ms[k] = 0.0;
+    }
   });
 }
 
@@ -824,8 +921,9 @@ mbf_status mbf_op_check(mbf_op_t op, void* stream) {
     cuda_check(cudaMemcpy(&st, op->d_status, sizeof(int), cudaMemcpyDeviceToHost), "read status");
     if (st != ST_OK) {
       cuda_check(cudaMemset(op->d_status, 0, sizeof(int)), "clear status");
-      static const char* names[] = {"ok", "grid barrier", "full mbarrier", "empty mbarrier", "bad item"};
-      fail(MBF_ERR_TIMEOUT, std::string("device wait gave up: ") + (st >= 0 && st <= 4 ? names[st] : "unknown"));
+      static const char* names[] = {"ok", "grid barrier", "full mbarrier", "empty mbarrier", "bad item",
+                                    "dependency counter"};
+      fail(MBF_ERR_TIMEOUT, std::string("device wait gave up: ") + (st >= 0 && st <= 5 ? names[st] : "unknown"));
     }
   });
 }

@@ -41,6 +41,14 @@ struct mbf_op_s {
   float2* d_tc_gt = nullptr;          // input panel in Omega-tree order [n_w][64]
   int32_t* d_w_inv = nullptr;         // natural Omega index -> tree position (-1: not in the tree)
   std::string tc_unavailable;         // why the tensor path cannot run for this operator ("" if it can)
+  std::vector<int64_t> nnz_stage;     // nonzero factor entries per forward stage
+  int64_t nnz_leaf_x = 0;             // of which U^L
+  // kernel timing (mbf_op_set_profiling): events bracketing each launch, by kind
+  bool prof_on = false;
+  struct ProfRec { int kind; cudaEvent_t e0, e1; };
+  std::vector<ProfRec> prof_pending;
+  int64_t prof_launches[8] = {};
+  double prof_ms[8] = {};
   // staging for mbf_apply_host
   float2 *d_stage_in = nullptr, *d_stage_out = nullptr;
   size_t stage_in_bytes = 0, stage_out_bytes = 0;
