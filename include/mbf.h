@@ -225,6 +225,76 @@ typedef struct mbf_profile {
 mbf_status mbf_op_set_profiling(mbf_op_t op, int32_t enable);
 mbf_status mbf_op_profile(mbf_op_t op, mbf_profile_t* out);
 
+/* ------------------------------------------------------------------ autotuner
+ * The paper has no counterpart (its applies are single-threaded CPU loops).  Measures,
+ * on `stream` with device buffers it allocates and frees itself, (a) the FP32 SIMT apply
+ * for 1, 2, 4, 8, 16, 32 and 64 RHS, (b) the tensor-core apply of one 64-RHS panel for
+ * every A-tile ring depth that fits shared memory, then keeps the fastest ring depth and
+ * sets the RHS count from which MBF_PREC_AUTO takes the tensor cores to the smallest
+ * measured count at which one panel is faster than the SIMT apply.  Blocking; the
+ * operator must be idle.  The choices stay with the operator until it is destroyed. */
+typedef struct mbf_tune_result {
+  int32_t n_simt;
+  int32_t simt_rhs[8];
+  double simt_ms[8];            /* device time of one SIMT apply of simt_rhs[i] RHS  */
+  int32_t n_slots;
+  int32_t slots[8];
+  double tc_ms[8];              /* one 64-RHS panel with slots[i] A-ring slots       */
+  int32_t tc_slots_chosen;      /* 0 if the tensor path is unavailable               */
+  int32_t tc_min_rhs;           /* AUTO uses the tensor cores from this many RHS     */
+} mbf_tune_result_t;
+mbf_status mbf_op_tune(mbf_op_t op, void* stream, mbf_tune_result_t* out);
+
+/* ------------------------------------------------------------------ serving
+ * The paper has no counterpart.  A server owns a worker thread, a few CUDA streams
+ * (slots) and a staging budget on one device; operators stay resident and are shared.
+ *   mbf_submit   queues u = K_f g for device buffers g [nrhs][n_in], u [nrhs][n_out]
+ *                (complex64; caller-owned, live until the ticket is DONE or ERROR).  It
+ *                never blocks: a request that does not fit the staging budget
+ *                (2 nrhs max(n_in, n_out) 8 bytes reserved until it completes) or the
+ *                queue returns MBF_ERR_BUSY.
+ *   worker       continuous batching: whenever a slot is free it takes the oldest queued
+ *                request whose operator is idle, coalesces the queued requests on the
+ *                same operator (FIFO, up to max_batch_rhs RHS) into one apply through
+ *                staging buffers, and launches the batch on the slot's stream -- as one
+ *                captured CUDA graph when use_graphs is set.  Batches of different
+ *                operators overlap on the device; while others are running or waiting a
+ *                batch's persistent kernels get a 1 / max_inflight share of the SMs.
+ *                The precision is MBF_PREC_AUTO for the coalesced RHS count.
+ *   mbf_poll     state and timestamps of a ticket; a ticket is forgotten after the poll
+ *                that reports DONE or ERROR (later polls: MBF_ERR_NOT_FOUND).
+ * An operator used by a server must not be applied by the caller at the same time. */
+typedef struct mbf_server_opts {
+  int64_t staging_budget_bytes; /* device bytes for staging (0: 1 GiB)                 */
+  int32_t max_inflight;         /* slots = batches on the device at once (0: 4, <= 16)  */
+  int32_t max_batch_rhs;        /* RHS coalesced into one apply (0: 64)                */
+  int32_t max_queue;            /* queued requests (0: 4096)                           */
+  int32_t use_graphs;           /* 1: each batch is one CUDA graph launch              */
+} mbf_server_opts_t;
+typedef int64_t mbf_ticket_t;
+enum { MBF_REQ_QUEUED = 0, MBF_REQ_RUNNING = 1, MBF_REQ_DONE = 2, MBF_REQ_ERROR = 3 };
+typedef struct mbf_request_status {
+  int32_t state;                /* MBF_REQ_*                                            */
+  int32_t error;                /* mbf_status of a failed request                       */
+  int32_t batch_requests;       /* requests in the batch that carried this one         */
+  int32_t batch_rhs;            /* RHS of that batch                                   */
+  double t_submit, t_start, t_done;   /* seconds since the server was created          */
+} mbf_request_status_t;
+typedef struct mbf_server_stats {
+  int64_t submitted, completed, failed, rejected_busy;
+  int64_t batches, coalesced_requests, graph_launches, graph_instantiations;
+  int32_t max_batch_requests, max_concurrent_batches;
+} mbf_server_stats_t;
+mbf_status mbf_server_create(const mbf_server_opts_t* opts, mbf_server_t* out);
+mbf_status mbf_submit(mbf_server_t s, mbf_op_t op, const void* g, void* u, int64_t nrhs,
+                      mbf_ticket_t* ticket);
+mbf_status mbf_poll(mbf_server_t s, mbf_ticket_t ticket, mbf_request_status_t* status);
+/* Wait until nothing is queued or running (at most timeout_s; MBF_ERR_TIMEOUT after). */
+mbf_status mbf_server_drain(mbf_server_t s, double timeout_s);
+mbf_status mbf_server_stats(mbf_server_t s, mbf_server_stats_t* out);
+/* Finishes queued and running requests, then frees the server. */
+mbf_status mbf_server_destroy(mbf_server_t s);
+
 /* Thread-local text of the last error ("" if none). */
 const char* mbf_last_error(void);
 /* Library version string. */

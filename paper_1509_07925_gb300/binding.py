@@ -67,6 +67,33 @@ class OpInfo(C.Structure):
 PROFILE_KINDS = 8
 
 
+class TuneResult(C.Structure):
+    _fields_ = [("n_simt", C.c_int32), ("simt_rhs", C.c_int32 * 8), ("simt_ms", C.c_double * 8),
+                ("n_slots", C.c_int32), ("slots", C.c_int32 * 8), ("tc_ms", C.c_double * 8),
+                ("tc_slots_chosen", C.c_int32), ("tc_min_rhs", C.c_int32)]
+
+
+class ServerOpts(C.Structure):
+    _fields_ = [("staging_budget_bytes", C.c_int64), ("max_inflight", C.c_int32),
+                ("max_batch_rhs", C.c_int32), ("max_queue", C.c_int32), ("use_graphs", C.c_int32)]
+
+
+class RequestStatus(C.Structure):
+    _fields_ = [("state", C.c_int32), ("error", C.c_int32), ("batch_requests", C.c_int32),
+                ("batch_rhs", C.c_int32), ("t_submit", C.c_double), ("t_start", C.c_double),
+                ("t_done", C.c_double)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
+                ("rejected_busy", C.c_int64), ("batches", C.c_int64), ("coalesced_requests", C.c_int64),
+                ("graph_launches", C.c_int64), ("graph_instantiations", C.c_int64),
+                ("max_batch_requests", C.c_int32), ("max_concurrent_batches", C.c_int32)]
+
+
+MBF_REQ_QUEUED, MBF_REQ_RUNNING, MBF_REQ_DONE, MBF_REQ_ERROR = 0, 1, 2, 3
+
+
 class Profile(C.Structure):
     _fields_ = [("n_kinds", C.c_int32), ("name", (C.c_char * 32) * PROFILE_KINDS),
                 ("launches", C.c_int64 * PROFILE_KINDS), ("ms", C.c_double * PROFILE_KINDS)]
@@ -94,6 +121,14 @@ SIGNATURES = {
     "mbf_op_check": (C.c_int, [C.c_void_p, C.c_void_p]),
     "mbf_apply_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "mbf_op_set_profiling": (C.c_int, [C.c_void_p, C.c_int32]),
+    "mbf_op_tune": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(TuneResult)]),
+    "mbf_server_create": (C.c_int, [C.POINTER(ServerOpts), C.POINTER(C.c_void_p)]),
+    "mbf_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                             C.POINTER(C.c_int64)]),
+    "mbf_poll": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(RequestStatus)]),
+    "mbf_server_drain": (C.c_int, [C.c_void_p, C.c_double]),
+    "mbf_server_stats": (C.c_int, [C.c_void_p, C.POINTER(ServerStats)]),
+    "mbf_server_destroy": (C.c_int, [C.c_void_p]),
     "mbf_op_profile": (C.c_int, [C.c_void_p, C.POINTER(Profile)]),
     "mbf_last_error": (C.c_char_p, []),
     "mbf_version": (C.c_char_p, []),
@@ -282,12 +317,59 @@ class Operator:
         _check(lib().mbf_op_profile(self._h, C.byref(p)))
         return {p.name[k].value.decode(): (int(p.launches[k]), float(p.ms[k])) for k in range(p.n_kinds)}
 
+    def tune(self, stream: int = 0) -> TuneResult:
+        """Run the autotuner (blocking); returns its measurements and choices."""
+        r = TuneResult()
+        _check(lib().mbf_op_tune(self._h, C.c_void_p(stream), C.byref(r)))
+        return r
+
     def check(self, stream: int = 0):
         _check(lib().mbf_op_check(self._h, C.c_void_p(stream)))
 
     def close(self):
         if self._h:
             lib().mbf_op_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Serving loop (mbf_server_t): continuous batching of applies on resident operators."""
+
+    def __init__(self, staging_budget_bytes: int = 0, max_inflight: int = 0, max_batch_rhs: int = 0,
+                 max_queue: int = 0, use_graphs: bool = True):
+        o = ServerOpts(staging_budget_bytes, max_inflight, max_batch_rhs, max_queue, 1 if use_graphs else 0)
+        self._h = C.c_void_p()
+        _check(lib().mbf_server_create(C.byref(o), C.byref(self._h)))
+
+    def submit(self, op: "Operator", g_ptr: int, u_ptr: int, nrhs: int) -> int:
+        """Queue u = K_f g (device buffers, caller-owned until DONE).  Raises MbfError with
+        code MBF_ERR_BUSY when the queue or the staging budget is full."""
+        t = C.c_int64()
+        _check(lib().mbf_submit(self._h, op.handle, C.c_void_p(g_ptr), C.c_void_p(u_ptr), nrhs, C.byref(t)))
+        return t.value
+
+    def poll(self, ticket: int) -> RequestStatus:
+        st = RequestStatus()
+        _check(lib().mbf_poll(self._h, ticket, C.byref(st)))
+        return st
+
+    def drain(self, timeout_s: float = 60.0):
+        _check(lib().mbf_server_drain(self._h, timeout_s))
+
+    def stats(self) -> ServerStats:
+        st = ServerStats()
+        _check(lib().mbf_server_stats(self._h, C.byref(st)))
+        return st
+
+    def close(self):
+        if self._h:
+            _check(lib().mbf_server_destroy(self._h))
             self._h = C.c_void_p()
 
     def __del__(self):

@@ -522,6 +522,7 @@ mbf_op_s* op_create(const mbf_factors_t& f) {
       fail(MBF_ERR_OOM, "cudaMalloc barrier");
     cuda_check(cudaMemset(op->d_status, 0, 256), "cudaMemset status");
     for (int nrb : {1, 2, 4}) cuda_check(simt_config(nrb, &op->grid, &op->ns[nrb], &op->smem[nrb]), "simt_config");
+    cuda_check(cudaDeviceGetAttribute(&op->sms, cudaDevAttrMultiProcessorCount, op->device), "attr");
     // tensor-core tiles (the multi-RHS path); an operator whose tiles do not fit keeps
     // the SIMT path only and says why
     try {
@@ -598,25 +599,14 @@ void prof_collect(mbf_op_s* op) {
 // Tensor-core apply, per panel of 64 RHS: permute the panel into Omega-tree order, the
 // (V^L)^* leaf kernel, the persistent tcgen05 kernel over the G / H levels, the U^L leaf
 // kernel.
-void apply_tc(mbf_op_s* op, const float2* g, float2* u, int64_t nrhs, cudaStream_t st) {
+void apply_tc(mbf_op_s* op, const float2* g, float2* u, int64_t nrhs, cudaStream_t st, int grid) {
   if (!op->tc_unavailable.empty()) fail(MBF_ERR_INVALID, "tensor path unavailable: " + op->tc_unavailable);
   const TCPlan& tp = op->tcplan;
   const int S = tp.n_stages;
-  // one vector: every block of a level at the largest R8, split or complex64 (8 bytes an entry)
-  int r8max = 8;
-  for (int e = 0; e < S; ++e) r8max = std::max({r8max, tp.st[e].R8_in, tp.st[e].R8_out});
-  const int64_t vec_bytes = Tree::ipow(op->c, op->L) * split_block_bytes(r8max);
-  if (!op->d_tc_bufs) {
-    if (cudaMalloc(&op->d_tc_bufs, size_t(S + 1) * size_t(vec_bytes)) != cudaSuccess)
-      fail(MBF_ERR_OOM, "cudaMalloc tensor-path workspace");
-    if (cudaMalloc(&op->d_tc_counters, tc_counter_bytes(tp)) != cudaSuccess)
-      fail(MBF_ERR_OOM, "cudaMalloc tensor-path counters");
-    if (cudaMalloc(&op->d_tc_gt, size_t(std::max<int64_t>(op->n_w, 1)) * kTcNR * sizeof(float2)) != cudaSuccess)
-      fail(MBF_ERR_OOM, "cudaMalloc tensor-path input panel");
-  }
-  int dev = 0, sms = 0;
-  cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
-  cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "attr");
+  const int64_t vec_bytes = tc_vec_bytes(op);
+  tc_prepare(op);
+  int sms = op->sms;
+  if (grid > 0) sms = std::min(sms, grid);
   const Stage& leaf_st = op->plan.st[0];
   const Stage& last_st = op->plan.st[op->plan.n_stages - 1];
   uint8_t* yl = op->d_tc_bufs;                       // level-L input of the main stages
@@ -689,7 +679,7 @@ void apply_tc(mbf_op_s* op, const float2* g, float2* u, int64_t nrhs, cudaStream
 }
 
 void apply_impl(mbf_op_s* op, const void* in, void* out, int64_t nrhs, int32_t precision, void* stream,
-                bool adj) {
+                bool adj, int grid = 0) {
   if (!op) fail(MBF_ERR_INVALID, "operator is NULL");
   if (nrhs < 0) fail(MBF_ERR_INVALID, "nrhs < 0");
   if (nrhs == 0) return;
@@ -698,11 +688,9 @@ void apply_impl(mbf_op_s* op, const void* in, void* out, int64_t nrhs, int32_t p
     fail(MBF_ERR_INVALID, "precision not available");
   if (nrhs > (int64_t(1) << 24)) fail(MBF_ERR_INVALID, "nrhs too large");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const bool tensor = precision == MBF_PREC_BF16X3 ||
-                      (precision == MBF_PREC_AUTO && nrhs >= 8 && !adj && op->tc_unavailable.empty());
-  if (tensor) {
+  if (uses_tensor(op, nrhs, precision, adj)) {
     if (adj) fail(MBF_ERR_INVALID, "the tensor-core path applies the forward operator only");
-    apply_tc(op, static_cast<const float2*>(in), static_cast<float2*>(out), nrhs, st);
+    apply_tc(op, static_cast<const float2*>(in), static_cast<float2*>(out), nrhs, st, grid);
     return;
   }
   const int nrb = nrhs >= 4 ? 4 : (nrhs >= 2 ? 2 : 1);
@@ -729,7 +717,8 @@ void apply_impl(mbf_op_s* op, const void* in, void* out, int64_t nrhs, int32_t p
   if (adj && op->n_w < op->n_in)
     cuda_check(cudaMemsetAsync(out, 0, size_t(nrhs) * size_t(op->n_in) * sizeof(float2), st), "cudaMemsetAsync");
   cudaEvent_t e0 = prof_begin(op, st);
-  cuda_check(launch_apply_simt(a, nrb, adj, op->grid, op->smem[nrb], st), "apply launch");
+  const int g = grid > 0 ? std::min(grid, op->grid) : op->grid;
+  cuda_check(launch_apply_simt(a, nrb, adj, g, op->smem[nrb], st), "apply launch");
   prof_end(op, PK_SIMT, e0, st);
 }
 
@@ -754,6 +743,40 @@ mbf_status guard(F&& fn) {
 }  // namespace
 
 void set_last_error(const std::string& m) { g_last_error = m; }
+
+// Which path an apply takes: split-BF16x3 on request; AUTO uses the tensor cores for
+// forward applies from tc_min_rhs right-hand sides (8, or what the tuner measured).
+bool uses_tensor(const mbf_op_s* op, int64_t nrhs, int32_t precision, bool adj) {
+  return precision == MBF_PREC_BF16X3 ||
+         (precision == MBF_PREC_AUTO && nrhs >= op->tc_min_rhs && !adj && op->tc_unavailable.empty());
+}
+
+// Bytes of one tensor-path vector: every block of a level at the largest R8, split or
+// complex64 (8 bytes an entry, 64 RHS).
+int64_t tc_vec_bytes(const mbf_op_s* op) {
+  int r8max = 8;
+  for (int e = 0; e < op->tcplan.n_stages; ++e)
+    r8max = std::max({r8max, op->tcplan.st[e].R8_in, op->tcplan.st[e].R8_out});
+  return Tree::ipow(op->c, op->L) * split_block_bytes(r8max);
+}
+
+// Allocate the tensor-path workspace (first use), so that later applies allocate nothing.
+void tc_prepare(mbf_op_s* op) {
+  if (op->d_tc_bufs || !op->tc_unavailable.empty()) return;
+  const int S = op->tcplan.n_stages;
+  const int64_t vec_bytes = tc_vec_bytes(op);
+  if (cudaMalloc(&op->d_tc_bufs, size_t(S + 1) * size_t(vec_bytes)) != cudaSuccess)
+    fail(MBF_ERR_OOM, "cudaMalloc tensor-path workspace");
+  if (cudaMalloc(&op->d_tc_counters, tc_counter_bytes(op->tcplan)) != cudaSuccess)
+    fail(MBF_ERR_OOM, "cudaMalloc tensor-path counters");
+  if (cudaMalloc(&op->d_tc_gt, size_t(std::max<int64_t>(op->n_w, 1)) * kTcNR * sizeof(float2)) != cudaSuccess)
+    fail(MBF_ERR_OOM, "cudaMalloc tensor-path input panel");
+}
+
+void apply_dev(mbf_op_s* op, const void* in, void* out, int64_t nrhs, int32_t precision, cudaStream_t st,
+               bool adj, int grid) {
+  apply_impl(op, in, out, nrhs, precision, st, adj, grid);
+}
 
 }  // namespace mbf
 

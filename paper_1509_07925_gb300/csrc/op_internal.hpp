@@ -41,6 +41,8 @@ struct mbf_op_s {
   float2* d_tc_gt = nullptr;          // input panel in Omega-tree order [n_w][64]
   int32_t* d_w_inv = nullptr;         // natural Omega index -> tree position (-1: not in the tree)
   std::string tc_unavailable;         // why the tensor path cannot run for this operator ("" if it can)
+  int sms = 0;                        // SMs of the device (the persistent grids)
+  int64_t tc_min_rhs = 8;             // AUTO: tensor cores from this many RHS (tuner may change it)
   std::vector<int64_t> nnz_stage;     // nonzero factor entries per forward stage
   int64_t nnz_leaf_x = 0;             // of which U^L
   // kernel timing (mbf_op_set_profiling): events bracketing each launch, by kind
@@ -54,3 +56,14 @@ struct mbf_op_s {
   size_t stage_in_bytes = 0, stage_out_bytes = 0;
 };
 
+
+namespace mbf {
+void set_last_error(const std::string& m);
+// Internal entry points shared with the server and the tuner.  All throw mbf::Error.
+bool uses_tensor(const mbf_op_s* op, int64_t nrhs, int32_t precision, bool adj);
+void tc_prepare(mbf_op_s* op);
+int64_t tc_vec_bytes(const mbf_op_s* op);
+// Apply on the device; grid > 0 caps the persistent kernels' CTA count (an SM share).
+void apply_dev(mbf_op_s* op, const void* in, void* out, int64_t nrhs, int32_t precision, cudaStream_t st,
+               bool adj, int grid);
+}  // namespace mbf

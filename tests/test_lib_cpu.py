@@ -153,3 +153,23 @@ def test_no_gpu_means_no_apply(bd, case):
     with pytest.raises(bd.MbfError) as ei:
         bd.Operator(hf)
     assert ei.value.code in (bd.MBF_ERR_CUDA, bd.MBF_ERR_OOM), str(ei.value)
+
+
+def test_server_needs_a_gpu(bd):
+    """The serving loop owns CUDA streams: without a GPU it is not created (no host
+    fallback), and the C ABI rejects NULL arguments without touching the device."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present")
+    except ImportError:
+        pass
+    with pytest.raises(bd.MbfError) as ei:
+        bd.Server()
+    assert ei.value.code == bd.MBF_ERR_CUDA, str(ei.value)
+    import ctypes
+    t = ctypes.c_int64()
+    assert bd.lib().mbf_submit(None, None, None, None, 1, ctypes.byref(t)) == bd.MBF_ERR_INVALID
+    st = bd.RequestStatus()
+    assert bd.lib().mbf_poll(None, 1, ctypes.byref(st)) == bd.MBF_ERR_INVALID
+    assert bd.lib().mbf_op_tune(None, None, None) == bd.MBF_ERR_INVALID
