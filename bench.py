@@ -28,7 +28,7 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-from mbf_synth import WORKLOADS, complex_normal  # noqa: E402
+from mbf_synth import SERVE_MIX, WORKLOADS, complex_normal, request_stream  # noqa: E402
 
 METRIC = "MBF apply points·RHS/s & %HBM/TC roofline; serve p50/p99 at rel err ≤1e-4"
 UNIT = "points*RHS/s"
@@ -45,6 +45,8 @@ def parse():
     p.add_argument("--precision", default="auto", choices=["auto", "fp32_simt", "bf16x3"],
                    help="auto: FP32 SIMT below 8 RHS, split-BF16x3 tensor cores from 8 RHS")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-serve", action="store_true", help="skip the served-mix experiment")
+    p.add_argument("--serve-requests", type=int, default=512)
     return p.parse_args()
 
 
@@ -119,15 +121,21 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def kernel_source_hash():
+KERNEL_SOURCES = {"bf_apply_simt": ("apply_simt.cu", "layout.hpp"),
+                  "bf_apply_tc": ("apply_tc.cu", "layout.hpp", "apply.hpp")}
+
+
+def kernel_source_hash(kernel):
+    """Hash of the sources a kernel is compiled from (its DRAM traffic record is only
+    used while they are unchanged)."""
     h = hashlib.sha256()
-    for f in ("apply_simt.cu", "apply_tc.cu", "layout.hpp", "apply.hpp", "op.cpp"):
+    for f in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_1509_07925_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload, nrhs):
+def recorded_traffic(workload, nrhs, kernel):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on the
     current kernel source; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
@@ -136,7 +144,7 @@ def recorded_traffic(workload, nrhs):
     with open(path) as f:
         d = json.load(f)
     ent = d.get(f"{workload}/nrhs{nrhs}")
-    if not ent or ent.get("kernel_hash") != kernel_source_hash():
+    if not ent or ent.get("kernel_hash") != kernel_source_hash(kernel):
         return None
     return ent.get("dram_bytes_per_launch")
 
@@ -218,6 +226,87 @@ def kernel_times(torch, op, g, u, nrhs, prec, steps, stream):
     op.set_profiling(False)
     return {k: {"launches_per_apply": n / steps, "ms_per_apply": ms / steps}
             for k, (n, ms) in prof.items() if n}
+
+
+def serve_experiment(torch, bd, ops, n_requests, loads=(0.5, 0.8, 1.1)):
+    """The served mix: n_requests seeded requests (operator uniform over `ops`, RHS
+    uniform 1..32), first as a closed-loop flood (all submitted at once) to find the
+    saturation rate, then as Poisson arrivals at fractions of it.  Latency = device
+    completion - submission, from the server's own clock.  A few results are checked
+    against the same request applied alone."""
+    names = [nm for nm, _ in ops]
+    base = request_stream(n_requests, names, rate_hz=1.0, max_rhs=32, seed=2)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(2)
+    byname = dict(ops)
+    bufs = []
+    for _, nm, R in base:
+        op, N = byname[nm]
+        g = torch.randn((R, N), dtype=torch.complex64, device="cuda", generator=gen)
+        u = torch.empty((R, N), dtype=torch.complex64, device="cuda")
+        bufs.append((g, u))
+    torch.cuda.synchronize()
+    work = sum(byname[nm][1] * R for _, nm, R in base)     # points x RHS of all requests
+
+    def run(arrivals):
+        srv = bd.Server(staging_budget_bytes=4 << 30, max_inflight=4, max_batch_rhs=64)
+        pending, lat, t_first, t_last = {}, [], None, 0.0
+        k = 0
+        t0 = time.perf_counter()
+        while k < len(base) or pending:
+            now = time.perf_counter() - t0
+            while k < len(base) and arrivals[k] <= now:
+                _, nm, R = base[k]
+                g, u = bufs[k]
+                try:
+                    tk = srv.submit(byname[nm][0], g.data_ptr(), u.data_ptr(), R)
+                except bd.MbfError as e:
+                    if e.code != bd.MBF_ERR_BUSY:
+                        raise
+                    break                                   # retry at the next sweep
+                pending[tk] = k
+                k += 1
+            for tk in list(pending):
+                st = srv.poll(tk)
+                if st.state == bd.MBF_REQ_DONE:
+                    lat.append(st.t_done - st.t_submit)
+                    t_first = st.t_submit if t_first is None else min(t_first, st.t_submit)
+                    t_last = max(t_last, st.t_done)
+                    del pending[tk]
+                elif st.state == bd.MBF_REQ_ERROR:
+                    raise RuntimeError(f"served request failed: status {st.error}")
+        stats = srv.stats()
+        srv.close()
+        wall = t_last - t_first
+        lat_ms = np.array(lat) * 1e3
+        return {"p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+                "value": work / wall, "requests_per_s": len(base) / wall, "wall_s": wall,
+                "batches": int(stats.batches), "coalesced_requests": int(stats.coalesced_requests),
+                "max_batch_requests": int(stats.max_batch_requests),
+                "max_concurrent_batches": int(stats.max_concurrent_batches),
+                "graph_launches": int(stats.graph_launches), "rejected_busy": int(stats.rejected_busy)}
+
+    run([0.0] * len(base))                                 # warm-up (graphs, workspaces)
+    flood = run([0.0] * len(base))
+    sat = flood["requests_per_s"]
+    out = {"requests": len(base), "operators": names, "rhs": "uniform 1..32", "flood": flood, "loads": []}
+    for f in loads:
+        arr = [t / (f * sat) for t, _, _ in base]           # unit-rate Poisson times, rescaled
+        r = run(arr)
+        r["offered"] = f
+        out["loads"].append(r)
+    # spot check: a few served results equal the same request applied alone
+    worst = 0.0
+    for k in range(0, len(base), max(1, len(base) // 8)):
+        _, nm, R = base[k]
+        g, u = bufs[k]
+        ref = torch.empty_like(u)
+        byname[nm][0].apply(g.data_ptr(), ref.data_ptr(), R, bd.MBF_PREC_AUTO,
+                            torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        worst = max(worst, float(torch.linalg.norm(u - ref) / torch.linalg.norm(ref)))
+    out["served_vs_alone_max_rel"] = worst
+    return out
 
 
 def main():
@@ -303,7 +392,7 @@ def main():
         alg_note = "8 B x nonzeros of all factors + 8 B in + 8 B out per point and RHS"
     k_ms = head["kernels"][kname]["ms_per_apply"] / head["kernels"][kname]["launches_per_apply"]
     achieved = alg_bytes / (k_ms * 1e-3) / 1e9
-    traffic = recorded_traffic(wl.name, R)
+    traffic = recorded_traffic(wl.name, R, kname)
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     g_host = torch.from_numpy(complex_normal(N, R, seed=wl.seed_g).astype(np.complex64)).pin_memory()
@@ -347,6 +436,19 @@ def main():
     }
     if "simt_1rhs" in res:
         line["speedup_vs_simt_1rhs"] = head["value"] / res["simt_1rhs"]["value"]
+    if not args.no_serve and world == 1:
+        serve_ops, keep = [], []
+        for nm in SERVE_MIX:
+            if nm == wl.name:
+                serve_ops.append((nm, (op, N)))
+            else:
+                w2 = WORKLOADS[nm]
+                o2 = bd.Operator(build_factors(bd, w2))
+                keep.append(o2)
+                serve_ops.append((nm, (o2, w2.N)))
+        line["serve"] = serve_experiment(torch, bd, serve_ops, args.serve_requests)
+        for o2 in keep:
+            o2.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             v, sample, cores = oracle_apply_rate(hf, wl, R)

@@ -91,7 +91,15 @@ WORKLOADS = {
     "fio2_polar_n32_L4_r12": Workload("fio2_polar_n32_L4_r12", "fio_iso", 2, 32, 4, 12, 1, "polar"),
     "fio2_polar_n64_L4_r24": Workload("fio2_polar_n64_L4_r24", "fio_iso", 2, 64, 4, 24, 1, "polar"),
     "dft3_n8_L2_r16": Workload("dft3_n8_L2_r16", "dft", 3, 8, 2, 16, 1),
+    # Further operators of the served mix (2x2- and 4x4-point leaves).
+    "dft2_n128_L6_r16": Workload("dft2_n128_L6_r16", "dft", 2, 128, 6, 16, 1),
+    "fio2_polar_n128_L6_r24": Workload("fio2_polar_n128_L6_r24", "fio_iso", 2, 128, 6, 24, 1, "polar"),
+    "dft2_n256_L6_r16": Workload("dft2_n256_L6_r16", "dft", 2, 256, 6, 16, 1),
 }
+
+# The served mix: six resident operators, requests drawn uniformly over them.
+SERVE_MIX = ["dft2_n64_L4_r16", "fio2_polar_n64_L4_r24", "dft2_n128_L6_r16", "fio2_polar_n128_L6_r24",
+             "dft2_n256_L6_r16", "fio2_polar_n256_L6_r24"]
 
 
 def request_stream(n_requests: int, operators: list[str], rate_hz: float, max_rhs: int = 32,
