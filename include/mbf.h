@@ -135,6 +135,7 @@ typedef struct mbf_factors {
 typedef struct mbf_factors_s* mbf_factors_h;  /* host FP64 factors owned by the library */
 typedef struct mbf_op_s* mbf_op_t;            /* device-resident packed operator        */
 typedef struct mbf_server_s* mbf_server_t;    /* serving loop                           */
+typedef struct mbf_msbf_s* mbf_msbf_t;        /* multiscale factorization (§4)          */
 
 /* Build the FP64 factors on the host (§2.3-2.4, Case (ii)); threads per opts.
  * The builder keeps O(N log N) memory by recomputing each middle-level block for the
@@ -224,6 +225,48 @@ typedef struct mbf_profile {
 } mbf_profile_t;
 mbf_status mbf_op_set_profiling(mbf_op_t op, int32_t enable);
 mbf_status mbf_op_profile(mbf_op_t op, mbf_profile_t* out);
+
+/* ------------------------------------------------------------------ multiscale (§4)
+ * The multiscale butterfly factorization of a 2-D kernel with a singularity at xi = 0:
+ *     K ~ K_C R_C + sum_t BF_t R_t                                          (eq. f1)
+ * over the coronas Omega_t = {n/2^(t+2) < max_k |xi_k| <= n/2^(t+1)} (eq.
+ * domaindecomp) for the t with n/2^(t+2) >= n_center/2, and the centre Omega_C (the
+ * rest, with n_center = 16: the paper's 16 x 16 centre, 17 x 17 points by the
+ * inequalities).  BF_t is a butterfly factorization on quadtrees of depth
+ * L_t = 2 floor((log2 n - t) / 2) over X and over the square [-n/2^(t+1), n/2^(t+1))^2
+ * (upper faces closed) that holds Omega_t; K_C is kept dense in HBM (complex64).
+ *   mbf_build_msbf     builds every part on the host (FP64, as mbf_build_factors; prob
+ *                      gives dim = 2, n and r; its L and tree are ignored) and K_C through
+ *                      the entry callback, then uploads them.
+ *   mbf_msbf_create    assembles one from resident operators (same n_out / n_in; their
+ *                      Omega trees must hold disjoint point sets) and the centre kernel
+ *                      center_kernel [n_c][n_out] (complex FP64 interleaved, centre-point
+ *                      major) on the natural Omega indices center_index [n_c].  With
+ *                      take_ownership the parts are destroyed with it.
+ *   mbf_msbf_apply     u = K_C g_C + sum_t BF_t g, device [nrhs][n] buffers, stream-ordered:
+ *                      the centre product writes u, each part adds into it.
+ *   mbf_msbf_apply_adjoint  g = K^* u (FP32 SIMT parts; MBF_PREC_BF16X3 is rejected). */
+typedef struct mbf_msbf_info {
+  int32_t n_parts;
+  int32_t part_t[16], part_L[16];
+  int64_t part_points[16], part_nnz[16];
+  int64_t n_out, n_in, n_center_points;
+  int64_t nnz_algorithmic;      /* sum of the parts' nonzeros + n_out * n_center_points  */
+  int64_t bytes_algorithmic;
+} mbf_msbf_info_t;
+mbf_status mbf_build_msbf(const mbf_problem_t* prob, mbf_entry_fn fn, void* ctx,
+                          const mbf_build_opts_t* opts, int32_t n_center, mbf_msbf_t* out);
+mbf_status mbf_msbf_create(const mbf_op_t* parts, int32_t n_parts, const double* center_kernel,
+                           const int64_t* center_index, int64_t n_center_points,
+                           int32_t take_ownership, mbf_msbf_t* out);
+mbf_status mbf_msbf_apply(mbf_msbf_t m, const void* g, void* u, int64_t nrhs, int32_t precision,
+                          void* stream);
+mbf_status mbf_msbf_apply_adjoint(mbf_msbf_t m, const void* u, void* g, int64_t nrhs,
+                                  int32_t precision, void* stream);
+mbf_status mbf_msbf_info(mbf_msbf_t m, mbf_msbf_info_t* info);
+/* The i-th part (borrowed handle, e.g. for mbf_op_info or mbf_op_tune). */
+mbf_status mbf_msbf_part(mbf_msbf_t m, int32_t i, mbf_op_t* op);
+mbf_status mbf_msbf_destroy(mbf_msbf_t m);
 
 /* ------------------------------------------------------------------ autotuner
  * The paper has no counterpart (its applies are single-threaded CPU loops).  Measures,

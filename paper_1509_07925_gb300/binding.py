@@ -94,6 +94,13 @@ class ServerStats(C.Structure):
 MBF_REQ_QUEUED, MBF_REQ_RUNNING, MBF_REQ_DONE, MBF_REQ_ERROR = 0, 1, 2, 3
 
 
+class MsbfInfo(C.Structure):
+    _fields_ = [("n_parts", C.c_int32), ("part_t", C.c_int32 * 16), ("part_L", C.c_int32 * 16),
+                ("part_points", C.c_int64 * 16), ("part_nnz", C.c_int64 * 16), ("n_out", C.c_int64),
+                ("n_in", C.c_int64), ("n_center_points", C.c_int64), ("nnz_algorithmic", C.c_int64),
+                ("bytes_algorithmic", C.c_int64)]
+
+
 class Profile(C.Structure):
     _fields_ = [("n_kinds", C.c_int32), ("name", (C.c_char * 32) * PROFILE_KINDS),
                 ("launches", C.c_int64 * PROFILE_KINDS), ("ms", C.c_double * PROFILE_KINDS)]
@@ -122,6 +129,15 @@ SIGNATURES = {
     "mbf_apply_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "mbf_op_set_profiling": (C.c_int, [C.c_void_p, C.c_int32]),
     "mbf_op_tune": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(TuneResult)]),
+    "mbf_build_msbf": (C.c_int, [C.POINTER(Problem), C.c_void_p, C.c_void_p, C.POINTER(BuildOpts), C.c_int32,
+                                 C.POINTER(C.c_void_p)]),
+    "mbf_msbf_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_void_p, C.c_void_p, C.c_int64,
+                                  C.c_int32, C.POINTER(C.c_void_p)]),
+    "mbf_msbf_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p]),
+    "mbf_msbf_apply_adjoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p]),
+    "mbf_msbf_info": (C.c_int, [C.c_void_p, C.POINTER(MsbfInfo)]),
+    "mbf_msbf_part": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p)]),
+    "mbf_msbf_destroy": (C.c_int, [C.c_void_p]),
     "mbf_server_create": (C.c_int, [C.POINTER(ServerOpts), C.POINTER(C.c_void_p)]),
     "mbf_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                              C.POINTER(C.c_int64)]),
@@ -370,6 +386,77 @@ class Server:
     def close(self):
         if self._h:
             _check(lib().mbf_server_destroy(self._h))
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MsBF:
+    """Multiscale butterfly factorization (mbf_msbf_t, §4): per-corona operators plus the
+    dense centre, applied as the sum of eq. (f1)."""
+
+    def __init__(self):
+        self._h = C.c_void_p()
+        self._parts = []
+
+    @classmethod
+    def build(cls, n, r, kernel="fio_iso", n_center=16, seed=7, threads=0, sample_factor=3, max_rounds=3,
+              tol=1e-14):
+        """Host FP64 construction of every part and the centre (mbf_build_msbf)."""
+        self = cls()
+        prob = Problem(dim=2, n=n, L=2, r=r, tree=MBF_TREE_UNIFORM)
+        opts = BuildOpts(seed=seed, sample_factor=sample_factor, max_rounds=max_rounds, tol=tol, threads=threads)
+        fn = builtin_kernel(kernel) if isinstance(kernel, str) else kernel
+        _check(lib().mbf_build_msbf(C.byref(prob), fn, None, C.byref(opts), n_center, C.byref(self._h)))
+        return self
+
+    @classmethod
+    def create(cls, parts, center_kernel, center_index):
+        """From resident operators (kept alive by this object) and the centre kernel
+        [n_c][n_out] (complex) on the natural Omega indices center_index."""
+        self = cls()
+        self._parts = list(parts)
+        arr = (C.c_void_p * max(1, len(parts)))(*[p.handle.value for p in parts])
+        kc = np.ascontiguousarray(center_kernel, dtype=np.complex128)
+        ci = np.ascontiguousarray(center_index, dtype=np.int64)
+        _check(lib().mbf_msbf_create(arr, len(parts), kc.ctypes.data_as(C.c_void_p),
+                                     ci.ctypes.data_as(C.c_void_p), ci.size, 0, C.byref(self._h)))
+        return self
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> MsbfInfo:
+        inf = MsbfInfo()
+        _check(lib().mbf_msbf_info(self._h, C.byref(inf)))
+        return inf
+
+    def apply(self, g_ptr: int, u_ptr: int, nrhs: int, precision=MBF_PREC_AUTO, stream: int = 0):
+        _check(lib().mbf_msbf_apply(self._h, C.c_void_p(g_ptr), C.c_void_p(u_ptr), nrhs, precision,
+                                    C.c_void_p(stream)))
+
+    def apply_adjoint(self, u_ptr: int, g_ptr: int, nrhs: int, precision=MBF_PREC_AUTO, stream: int = 0):
+        _check(lib().mbf_msbf_apply_adjoint(self._h, C.c_void_p(u_ptr), C.c_void_p(g_ptr), nrhs, precision,
+                                            C.c_void_p(stream)))
+
+    def part_handle(self, i: int):
+        h = C.c_void_p()
+        _check(lib().mbf_msbf_part(self._h, i, C.byref(h)))
+        return h
+
+    def check(self, stream: int = 0):
+        """mbf_op_check on every part (a device wait that ran out of time raises)."""
+        for i in range(self.info().n_parts):
+            _check(lib().mbf_op_check(self.part_handle(i), C.c_void_p(stream)))
+
+    def close(self):
+        if self._h:
+            _check(lib().mbf_msbf_destroy(self._h))
             self._h = C.c_void_p()
 
     def __del__(self):

@@ -24,7 +24,8 @@ struct ApplyArgs {
   unsigned int* counters;  // [stage][group]: input segments written so far (zeroed per launch)
   unsigned int* barrier;   // grid barrier between passes (zeroed per launch)
   int* status;             // 0 = ok; nonzero = a device wait ran out of time (sticky)
-  int32_t nrhs, n_pass, n_slots, pad_;
+  int32_t nrhs, n_pass, n_slots;
+  int32_t accumulate;      // 1: out += result (the caller initialised out), 0: out = result
   Plan plan;
 };
 
@@ -74,6 +75,7 @@ struct LeafArgs {
   int64_t len_vec, len_out;
   int32_t nrhs, rhs0, c, R;
   int32_t R8, item_stride;
+  int32_t accumulate, pad_;   // U^L: 1 adds into u
 };
 
 size_t simt_smem_bytes(int nrb, int ns);

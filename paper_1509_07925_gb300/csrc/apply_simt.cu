@@ -761,7 +761,16 @@ __global__ void __launch_bounds__(Cfg<NRB>::W * 32, 1) bf_apply_simt(const __gri
               if (pt < npts)
 #pragma unroll
                 for (int r = 0; r < NRB; ++r)
-                  if (rhs0 + r < a.nrhs) a.out[int64_t(rhs0 + r) * a.out_len + idx[u]] = res[pt * NRB + r];
+                  if (rhs0 + r < a.nrhs) {
+                    float2* o = a.out + int64_t(rhs0 + r) * a.out_len + idx[u];
+                    float2 v = res[pt * NRB + r];
+                    if (a.accumulate) {
+                      const float2 w = *o;
+                      v.x += w.x;
+                      v.y += w.y;
+                    }
+                    *o = v;
+                  }
             }
           }
           __syncwarp();

@@ -662,7 +662,16 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_u_kernel(const __grid_const
 #pragma unroll
       for (int m = 0; m < MB; ++m) {
         const int b = bq + m * BT;
-        if (b < nb) orow[a.perm[p0 + b0 + b]] = acc[m];
+        if (b < nb) {
+          float2* o = orow + a.perm[p0 + b0 + b];
+          float2 v = acc[m];
+          if (a.accumulate) {
+            const float2 w = *o;
+            v.x += w.x;
+            v.y += w.y;
+          }
+          *o = v;
+        }
       }
     }
   }

@@ -599,7 +599,7 @@ void prof_collect(mbf_op_s* op) {
 // Tensor-core apply, per panel of 64 RHS: permute the panel into Omega-tree order, the
 // (V^L)^* leaf kernel, the persistent tcgen05 kernel over the G / H levels, the U^L leaf
 // kernel.
-void apply_tc(mbf_op_s* op, const float2* g, float2* u, int64_t nrhs, cudaStream_t st, int grid) {
+void apply_tc(mbf_op_s* op, const float2* g, float2* u, int64_t nrhs, cudaStream_t st, int grid, bool accumulate) {
   if (!op->tc_unavailable.empty()) fail(MBF_ERR_INVALID, "tensor path unavailable: " + op->tc_unavailable);
   const TCPlan& tp = op->tcplan;
   const int S = tp.n_stages;
@@ -672,6 +672,7 @@ void apply_tc(mbf_op_s* op, const float2* g, float2* u, int64_t nrhs, cudaStream
     lu.rhs0 = int32_t(r0);
     lu.c = op->c;
     lu.R = op->RU[size_t(op->L)];
+    lu.accumulate = accumulate ? 1 : 0;
     e0 = prof_begin(op, st);
     cuda_check(launch_leaf(lu, true, last_st.n_groups * op->c, st), "leaf U^L launch");
     prof_end(op, PK_LEAF_U, e0, st);
@@ -679,7 +680,7 @@ void apply_tc(mbf_op_s* op, const float2* g, float2* u, int64_t nrhs, cudaStream
 }
 
 void apply_impl(mbf_op_s* op, const void* in, void* out, int64_t nrhs, int32_t precision, void* stream,
-                bool adj, int grid = 0) {
+                bool adj, int grid = 0, bool accumulate = false) {
   if (!op) fail(MBF_ERR_INVALID, "operator is NULL");
   if (nrhs < 0) fail(MBF_ERR_INVALID, "nrhs < 0");
   if (nrhs == 0) return;
@@ -690,7 +691,7 @@ void apply_impl(mbf_op_s* op, const void* in, void* out, int64_t nrhs, int32_t p
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (uses_tensor(op, nrhs, precision, adj)) {
     if (adj) fail(MBF_ERR_INVALID, "the tensor-core path applies the forward operator only");
-    apply_tc(op, static_cast<const float2*>(in), static_cast<float2*>(out), nrhs, st, grid);
+    apply_tc(op, static_cast<const float2*>(in), static_cast<float2*>(out), nrhs, st, grid, accumulate);
     return;
   }
   const int nrb = nrhs >= 4 ? 4 : (nrhs >= 2 ? 2 : 1);
@@ -714,7 +715,8 @@ void apply_impl(mbf_op_s* op, const void* in, void* out, int64_t nrhs, int32_t p
   a.n_pass = int32_t((nrhs + nrb - 1) / nrb);
   a.n_slots = op->ns[nrb];
   a.plan = op->plan;
-  if (adj && op->n_w < op->n_in)
+  a.accumulate = accumulate ? 1 : 0;
+  if (adj && op->n_w < op->n_in && !accumulate)
     cuda_check(cudaMemsetAsync(out, 0, size_t(nrhs) * size_t(op->n_in) * sizeof(float2), st), "cudaMemsetAsync");
   cudaEvent_t e0 = prof_begin(op, st);
   const int g = grid > 0 ? std::min(grid, op->grid) : op->grid;
@@ -774,8 +776,8 @@ void tc_prepare(mbf_op_s* op) {
 }
 
 void apply_dev(mbf_op_s* op, const void* in, void* out, int64_t nrhs, int32_t precision, cudaStream_t st,
-               bool adj, int grid) {
-  apply_impl(op, in, out, nrhs, precision, st, adj, grid);
+               bool adj, int grid, bool accumulate) {
+  apply_impl(op, in, out, nrhs, precision, st, adj, grid, accumulate);
 }
 
 }  // namespace mbf

@@ -63,7 +63,8 @@ void set_last_error(const std::string& m);
 bool uses_tensor(const mbf_op_s* op, int64_t nrhs, int32_t precision, bool adj);
 void tc_prepare(mbf_op_s* op);
 int64_t tc_vec_bytes(const mbf_op_s* op);
-// Apply on the device; grid > 0 caps the persistent kernels' CTA count (an SM share).
+// Apply on the device; grid > 0 caps the persistent kernels' CTA count (an SM share);
+// accumulate adds the result into out (which the caller initialised).
 void apply_dev(mbf_op_s* op, const void* in, void* out, int64_t nrhs, int32_t precision, cudaStream_t st,
-               bool adj, int grid);
+               bool adj, int grid, bool accumulate = false);
 }  // namespace mbf

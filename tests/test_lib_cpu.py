@@ -173,3 +173,19 @@ def test_server_needs_a_gpu(bd):
     st = bd.RequestStatus()
     assert bd.lib().mbf_poll(None, 1, ctypes.byref(st)) == bd.MBF_ERR_INVALID
     assert bd.lib().mbf_op_tune(None, None, None) == bd.MBF_ERR_INVALID
+
+
+def test_multiscale_needs_a_gpu(bd):
+    """mbf_build_msbf uploads its parts: without a GPU it fails loudly before building."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present")
+    except ImportError:
+        pass
+    with pytest.raises(bd.MbfError) as ei:
+        bd.MsBF.build(16, 4, n_center=4)
+    assert ei.value.code == bd.MBF_ERR_CUDA, str(ei.value)
+    import ctypes
+    h = ctypes.c_void_p()
+    assert bd.lib().mbf_msbf_create(None, 0, None, None, 0, 0, ctypes.byref(h)) == bd.MBF_ERR_INVALID
