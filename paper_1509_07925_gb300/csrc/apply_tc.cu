@@ -496,10 +496,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
 }
 
 // ------------------------------------------------------------------ leaf kernels
-// One CTA per leaf; the leaf's points are staged kLeafChunk at a time.
+// One CTA per group (its c leaves); the group's points are staged kLeafPts at a time.
 constexpr int kLeafThreads = 256;
-constexpr int kLeafChunk = 32;
+constexpr int kLeafPts = 64;        // points staged per round
 constexpr int kLeafMaxR8 = 64;      // largest leaf rank (rounded up to 8) of the tensor path
+constexpr int kLeafMaxC = 8;        // children per node (3-D)
 
 // Entry e of line `line` of a chunked item (split real / imaginary planes per chunk).
 __device__ __forceinline__ float2 item_entry(const uint8_t* base, const Item& it, int line, int e) {
@@ -510,64 +511,95 @@ __device__ __forceinline__ float2 item_entry(const uint8_t* base, const Item& it
   return make_float2(__ldg(re + q), __ldg(re + pad4(int64_t(nl) * it.len) + q));
 }
 
-// Panel in tree order: gt[inv(i)][n] = g[rhs0 + n][i] for the natural indices i of the
-// Omega points in the tree (inv(i) < 0: not in the tree), zero for rhs0 + n >= nrhs.  A
-// CTA moves 64 consecutive natural indices: rows of g are read and rows of gt written
-// whole, the transpose goes through shared memory.
-constexpr int kPermTile = 64;
-__global__ void __launch_bounds__(kLeafThreads) permute_in_kernel(const __grid_constant__ LeafArgs a) {
-  __shared__ float2 tile[kTcNR][kPermTile + 1];
-  const int i0 = blockIdx.x * kPermTile, tid = threadIdx.x;
-  for (int q = tid; q < kTcNR * kPermTile; q += kLeafThreads) {
-    const int n = q / kPermTile, ii = q - n * kPermTile, rhs = a.rhs0 + n, i = i0 + ii;
-    tile[n][ii] = (rhs < a.nrhs && i < a.len_vec) ? __ldg(a.vec + int64_t(rhs) * a.len_vec + i) : make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-  for (int q = tid; q < kTcNR * kPermTile; q += kLeafThreads) {
-    const int ii = q / kTcNR, n = q - ii * kTcNR, i = i0 + ii;
-    if (i < a.len_vec) {
-      const int tp = a.perm[i];
-      if (tp >= 0) a.outp[int64_t(tp) * kTcNR + n] = tile[n][ii];
+// Split block `leaf` from the accumulators of thread (n, kq) (rows k = 4 (m KT + kq) + j):
+// byte (hl, k, ri, n) as in apply.hpp; 4 consecutive k = 8 bytes per plane.
+template <int MM, int KT>
+__device__ __forceinline__ void store_split_rows(uint8_t* outs, int64_t leaf, int R8, int n, int kq,
+                                                 float2 (&acc)[MM][4]) {
+  const int64_t half = int64_t(R8) * 256;
+  uint8_t* ob = outs + leaf * split_block_bytes(R8) + (n >> 3) * 128 + (n & 7) * 16;
+#pragma unroll
+  for (int m = 0; m < MM; ++m) {
+    const int k0 = 4 * (m * KT + kq);
+    if (k0 < R8) {
+      uint32_t hr[2], lr[2], hi[2], li[2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const float r0 = acc[m][2 * i].x, r1 = acc[m][2 * i + 1].x;
+        const float i0 = acc[m][2 * i].y, i1 = acc[m][2 * i + 1].y;
+        hr[i] = tc::pack_bf16x2(r0, r1);
+        lr[i] = tc::pack_bf16x2(r0 - __uint_as_float(hr[i] << 16), r1 - __uint_as_float(hr[i] & 0xffff0000u));
+        hi[i] = tc::pack_bf16x2(i0, i1);
+        li[i] = tc::pack_bf16x2(i0 - __uint_as_float(hi[i] << 16), i1 - __uint_as_float(hi[i] & 0xffff0000u));
+      }
+      uint8_t* o = ob + (k0 >> 3) * 2048 + (k0 & 7) * 2;
+      *reinterpret_cast<uint2*>(o) = make_uint2(hr[0], hr[1]);                 // Re hi
+      *reinterpret_cast<uint2*>(o + 1024) = make_uint2(hi[0], hi[1]);          // Im hi
+      *reinterpret_cast<uint2*>(o + half) = make_uint2(lr[0], lr[1]);          // Re lo
+      *reinterpret_cast<uint2*>(o + half + 1024) = make_uint2(li[0], li[1]);   // Im lo
     }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[m][j] = make_float2(0.f, 0.f);
   }
 }
 
-// (V^L_j)^* for a panel of 64 RHS, leaf j = c g + t:
-//   y_j[k][n] = sum over the points b of leaf j of conj(V^L_j[b][k]) gt[b][n],
-// gt = the panel in tree order (permute_in_kernel), stored as split block j (rows
-// k >= R are zero).  The group's item holds conj(V) with line = point (tree order from
-// the group's first point), entry = k.  Thread (n, kq) accumulates column n for the
-// rows k = 4 (m KT + kq) + 0..3.
+// (V^L)^* for a panel of 64 RHS, one CTA per group g (leaves j = c g + t):
+//   y_j[k][n] = sum over the points b of leaf j of conj(V^L_j[b][k]) g[rhs0 + n][w_perm(b)],
+// stored as split block j (rows k >= R are zero).  g is read in natural order through
+// the tree permutation w_perm (the input permutation folded into the loads; a thread
+// gathers one point for 16 RHS rows).  The group's item holds conj(V) with line = point
+// (tree order from the group's first point), entry = k.  Thread (n, kq) accumulates
+// column n for the rows k = 4 (m KT + kq) + 0..3 and emits a leaf's block when the
+// points pass the leaf's end (empty leaves give zero blocks).
+// MM = ceil(R8 / 16): row blocks of 4 per thread.
+template <int MM>
 __global__ void __launch_bounds__(kLeafThreads) leaf_v_kernel(const __grid_constant__ LeafArgs a) {
   constexpr int NR = kTcNR, KT = kLeafThreads / NR, NRP = NR + 1;
-  constexpr int MM = (kLeafMaxR8 + 4 * KT - 1) / (4 * KT);
+  constexpr int GQ = kLeafThreads / kLeafPts, GR = NR / GQ;   // gather: rows per thread
   extern __shared__ __align__(16) float2 lsm[];
-  const int leaf = blockIdx.x, c = a.c, R = a.R, R8 = a.R8;
-  const int g = leaf / c;
+  __shared__ int lend[kLeafMaxC + 1];
+  const int g = blockIdx.x, c = a.c, R = a.R, R8 = a.R8;
+  const int tid = threadIdx.x, n = tid % NR, kq = tid / NR;
+  if (tid <= c) lend[tid] = a.off[c * g + tid];
   const Item it = a.items[a.item_base + int64_t(g) * a.item_stride];
   const uint8_t* ibase = a.arena + size_t(it.off128) * 128;
-  const int pg = a.off[c * g], p0 = a.off[leaf], np = a.off[leaf + 1] - p0;
-  float2* vs = lsm;                        // [kLeafChunk][R8], zero for k >= R
-  float2* xs = vs + kLeafChunk * R8;       // [kLeafChunk][NR + 1]
-  const int tid = threadIdx.x, n = tid % NR, kq = tid / NR;
+  const int pg = a.off[c * g], np = a.off[c * g + c] - pg;
+  float2* vs = lsm;                        // [kLeafPts][R8], zero for k >= R
+  float2* xs = vs + kLeafPts * R8;         // [kLeafPts][NR + 1]
   float2 acc[MM][4];
 #pragma unroll
   for (int m = 0; m < MM; ++m)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[m][j] = make_float2(0.f, 0.f);
-  for (int b0 = 0; b0 < np; b0 += kLeafChunk) {
-    const int nb = min(kLeafChunk, np - b0);
-    __syncthreads();
+  int t = 0;                               // leaf being accumulated
+  for (int b0 = 0; b0 < np; b0 += kLeafPts) {
+    const int nb = min(kLeafPts, np - b0);
+    __syncthreads();                       // previous round's reads done (and lend written)
     for (int q = tid; q < nb * R8; q += kLeafThreads) {
       const int b = q / R8, k = q - b * R8;
-      vs[q] = k < R ? item_entry(ibase, it, p0 - pg + b0 + b, k) : make_float2(0.f, 0.f);
+      vs[q] = k < R ? item_entry(ibase, it, b0 + b, k) : make_float2(0.f, 0.f);
     }
-    for (int q = tid; q < nb * NR; q += kLeafThreads) {   // rows of the tree-ordered panel
-      const int b = q / NR, nn = q - b * NR;
-      xs[b * NRP + nn] = __ldcg(a.vec + int64_t(p0 + b0 + b) * NR + nn);
+    {
+      const int b = tid % kLeafPts, n0 = tid / kLeafPts;
+      if (b < nb) {
+        const int nat = __ldg(a.perm + pg + b0 + b);
+        float2 v[GR];
+#pragma unroll
+        for (int i = 0; i < GR; ++i) {
+          const int rhs = a.rhs0 + n0 + i * GQ;
+          v[i] = rhs < a.nrhs ? __ldg(a.vec + int64_t(rhs) * a.len_vec + nat) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int i = 0; i < GR; ++i) xs[b * NRP + n0 + i * GQ] = v[i];
+      }
     }
     __syncthreads();
     for (int b = 0; b < nb; ++b) {
+      const int p = pg + b0 + b;
+      while (p >= lend[t + 1]) {           // leaves that end before point p (uniform branch)
+        store_split_rows<MM, KT>(a.outs, int64_t(c) * g + t, R8, n, kq, acc);
+        ++t;
+      }
       const float2 x = xs[b * NRP + n];
 #pragma unroll
       for (int m = 0; m < MM; ++m) {
@@ -585,86 +617,75 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_v_kernel(const __grid_const
       }
     }
   }
-  // split block `leaf`: byte (hl, k, ri, n) as in apply.hpp; 4 consecutive k = 8 bytes
-  const int64_t half = int64_t(R8) * 256;
-  uint8_t* ob = a.outs + int64_t(leaf) * split_block_bytes(R8) + (n >> 3) * 128 + (n & 7) * 16;
-#pragma unroll
-  for (int m = 0; m < MM; ++m) {
-    const int k0 = 4 * (m * KT + kq);
-    if (k0 < R8) {
-      float re[4], im[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        re[j] = acc[m][j].x;
-        im[j] = acc[m][j].y;
-      }
-      uint32_t hr[2], lr[2], hi[2], li[2];
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        hr[i] = tc::pack_bf16x2(re[2 * i], re[2 * i + 1]);
-        lr[i] = tc::pack_bf16x2(re[2 * i] - __uint_as_float(hr[i] << 16), re[2 * i + 1] - __uint_as_float(hr[i] & 0xffff0000u));
-        hi[i] = tc::pack_bf16x2(im[2 * i], im[2 * i + 1]);
-        li[i] = tc::pack_bf16x2(im[2 * i] - __uint_as_float(hi[i] << 16), im[2 * i + 1] - __uint_as_float(hi[i] & 0xffff0000u));
-      }
-      uint8_t* o = ob + (k0 >> 3) * 2048 + (k0 & 7) * 2;
-      *reinterpret_cast<uint2*>(o) = make_uint2(hr[0], hr[1]);                 // Re hi
-      *reinterpret_cast<uint2*>(o + 1024) = make_uint2(hi[0], hi[1]);          // Im hi
-      *reinterpret_cast<uint2*>(o + half) = make_uint2(lr[0], lr[1]);          // Re lo
-      *reinterpret_cast<uint2*>(o + half + 1024) = make_uint2(li[0], li[1]);   // Im lo
-    }
-  }
+  if (np == 0) __syncthreads();            // lend visible
+  for (; t < c; ++t) store_split_rows<MM, KT>(a.outs, int64_t(c) * g + t, R8, n, kq, acc);
 }
 
-// U^L for a panel, leaf j = c g + t: u[rhs0 + n][perm(b)] = sum_k U^L_j[b][k] w[j R + k][n]
-// for the points b of leaf j.  The group's item is stored by columns (line = k, entry =
-// point of the group); the leaf's coefficient rows are R contiguous rows of 64 real
-// then 64 imaginary parts.  Thread (n, bq) computes column n for the points
-// b = bq + m BT of each chunk.
+// U^L for a panel, one CTA per group g (leaves i = c g + t):
+//   u[rhs0 + n][x_perm(b)] (+)= sum_k U^L_i[b][k] w[i R + k][n]
+// for the points b of leaf i.  The group's item is stored by columns (line = k, entry =
+// point of the group); the coefficient rows of the group's c leaves are c R contiguous
+// rows of 64 real then 64 imaginary parts, staged whole in shared memory.  Thread
+// (b, nq) computes point b of the round for the 16 RHS n = 16 nq + 0..15, so that a
+// warp stores 32 consecutive points of one RHS row.
 __global__ void __launch_bounds__(kLeafThreads) leaf_u_kernel(const __grid_constant__ LeafArgs a) {
-  constexpr int NR = kTcNR, BT = kLeafThreads / NR, MB = kLeafChunk / BT;
+  constexpr int NR = kTcNR, NQ = kLeafThreads / kLeafPts, MN = NR / NQ;
   extern __shared__ __align__(16) float2 lsm[];
-  const int leaf = blockIdx.x, c = a.c, R = a.R, RP = a.R + 1;
-  const int g = leaf / c;
-  const int pg = a.off[c * g], p0 = a.off[leaf], np = a.off[leaf + 1] - p0;
+  __shared__ int lend[kLeafMaxC + 1];
+  const int g = blockIdx.x, c = a.c, R = a.R;
+  const int tid = threadIdx.x;
+  const int pg = a.off[c * g], np = a.off[c * g + c] - pg;
   if (np == 0) return;
+  if (tid <= c) lend[tid] = a.off[c * g + tid] - pg;
   const Item it = a.items[a.item_base + int64_t(g) * a.item_stride];
   const uint8_t* ibase = a.arena + size_t(it.off128) * 128;
-  float2* ws = lsm;                 // [R][NR]
-  float2* us = ws + R * NR;         // [kLeafChunk][R + 1]
-  const int tid = threadIdx.x, n = tid % NR, bq = tid / NR, rhs = a.rhs0 + n;
-  const float* wsrc = a.wl + int64_t(leaf) * R * 2 * NR;
-  for (int q = tid; q < R * NR; q += kLeafThreads) {
-    const int k = q / NR, nn = q - k * NR;
-    ws[q] = make_float2(__ldcg(wsrc + k * 2 * NR + nn), __ldcg(wsrc + k * 2 * NR + NR + nn));
+  float* ws = reinterpret_cast<float*>(lsm);                       // [c R][2 NR]
+  float2* us = reinterpret_cast<float2*>(ws + size_t(c) * R * 2 * NR);   // [R][kLeafPts]
+  {
+    const float4* src = reinterpret_cast<const float4*>(a.wl + int64_t(c) * g * R * 2 * NR);
+    float4* dst = reinterpret_cast<float4*>(ws);
+    for (int q = tid; q < c * R * (2 * NR / 4); q += kLeafThreads) dst[q] = __ldcg(src + q);
   }
-  for (int b0 = 0; b0 < np; b0 += kLeafChunk) {
-    const int nb = min(kLeafChunk, np - b0);
+  const int bb = tid % kLeafPts, nq = tid / kLeafPts;
+  for (int b0 = 0; b0 < np; b0 += kLeafPts) {
+    const int nb = min(kLeafPts, np - b0);
     __syncthreads();
-    for (int q = tid; q < nb * R; q += kLeafThreads) {
+    for (int q = tid; q < R * nb; q += kLeafThreads) {
       const int k = q / nb, b = q - k * nb;
-      us[b * RP + k] = item_entry(ibase, it, k, p0 - pg + b0 + b);
+      us[k * kLeafPts + b] = item_entry(ibase, it, k, b0 + b);
     }
     __syncthreads();
-    float2 acc[MB];
+    if (bb < nb) {
+      const int p = b0 + bb;
+      int t = 0;
+      while (t + 1 < c && p >= lend[t + 1]) ++t;
+      const float* wr = ws + size_t(t) * R * 2 * NR + MN * nq;
+      float2 acc[MN];
 #pragma unroll
-    for (int m = 0; m < MB; ++m) acc[m] = make_float2(0.f, 0.f);
-    for (int k = 0; k < R; ++k) {
-      const float2 w = ws[k * NR + n];
+      for (int j = 0; j < MN; ++j) acc[j] = make_float2(0.f, 0.f);
+      for (int k = 0; k < R; ++k) {
+        const float2 uv = us[k * kLeafPts + bb];
+        const float* wk = wr + k * 2 * NR;
 #pragma unroll
-      for (int m = 0; m < MB; ++m) {
-        const float2 v = us[(bq + m * BT) * RP + k];   // rows past nb hold stale values, never stored
-        acc[m].x = fmaf(v.x, w.x, fmaf(-v.y, w.y, acc[m].x));
-        acc[m].y = fmaf(v.x, w.y, fmaf(v.y, w.x, acc[m].y));
+        for (int j4 = 0; j4 < MN / 4; ++j4) {
+          const float4 wre = *reinterpret_cast<const float4*>(wk + 4 * j4);
+          const float4 wim = *reinterpret_cast<const float4*>(wk + NR + 4 * j4);
+          const float re[4] = {wre.x, wre.y, wre.z, wre.w}, im[4] = {wim.x, wim.y, wim.z, wim.w};
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            float2& o = acc[4 * j4 + j];
+            o.x = fmaf(uv.x, re[j], fmaf(-uv.y, im[j], o.x));
+            o.y = fmaf(uv.x, im[j], fmaf(uv.y, re[j], o.y));
+          }
+        }
       }
-    }
-    if (rhs < a.nrhs) {
-      float2* orow = a.outp + int64_t(rhs) * a.len_out;
+      const int nat = __ldg(a.perm + pg + p);
 #pragma unroll
-      for (int m = 0; m < MB; ++m) {
-        const int b = bq + m * BT;
-        if (b < nb) {
-          float2* o = orow + a.perm[p0 + b0 + b];
-          float2 v = acc[m];
+      for (int j = 0; j < MN; ++j) {
+        const int rhs = a.rhs0 + MN * nq + j;
+        if (rhs < a.nrhs) {
+          float2* o = a.outp + int64_t(rhs) * a.len_out + nat;
+          float2 v = acc[j];
           if (a.accumulate) {
             const float2 w = *o;
             v.x += w.x;
@@ -684,13 +705,13 @@ size_t tc_smem_bytes(int nsa, int nxb, int nsets, int mt_max, int kpad_max) {
          size_t(nsets) * 2 * kTcChunk * 128 * sizeof(float) + (2 * size_t(nsa) + 16) * 8 + 64;
 }
 
-size_t leaf_smem_bytes(int R, bool u_side) {
+size_t leaf_smem_bytes(int R, int c, bool u_side) {
   const int R8 = (R + 7) & ~7;
-  return sizeof(float2) * (u_side ? size_t(R) * kTcNR + size_t(kLeafChunk) * (R + 1)
-                                  : size_t(kLeafChunk) * R8 + size_t(kLeafChunk) * (kTcNR + 1));
+  return u_side ? size_t(c) * R * 2 * kTcNR * sizeof(float) + size_t(R) * kLeafPts * sizeof(float2)
+                : sizeof(float2) * (size_t(kLeafPts) * R8 + size_t(kLeafPts) * (kTcNR + 1));
 }
 
-bool leaf_fits(int R8) { return R8 <= kLeafMaxR8; }
+bool leaf_fits(int R8, int c) { return R8 <= kLeafMaxR8 && c <= kLeafMaxC; }
 
 cudaError_t launch_apply_tc(const TCArgs& a, int grid, size_t smem, cudaStream_t stream) {
   cudaError_t err = cudaMemsetAsync(a.counters, 0, tc_counter_bytes(a.plan), stream);
@@ -716,17 +737,17 @@ size_t tc_counter_bytes(const TCPlan& plan) {
   return (n * sizeof(unsigned) + 255) & ~size_t(255);
 }
 
-cudaError_t launch_permute_in(const LeafArgs& a, cudaStream_t stream) {
-  permute_in_kernel<<<unsigned((a.len_vec + kPermTile - 1) / kPermTile), kLeafThreads, 0, stream>>>(a);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_leaf(const LeafArgs& a, bool u_side, int n_leaves, cudaStream_t stream) {
-  const size_t smem = leaf_smem_bytes(a.R, u_side);
-  void (*kern)(LeafArgs) = u_side ? leaf_u_kernel : leaf_v_kernel;
+cudaError_t launch_leaf(const LeafArgs& a, bool u_side, int n_groups, cudaStream_t stream) {
+  const size_t smem = leaf_smem_bytes(a.R, a.c, u_side);
+  void (*kern)(LeafArgs) = leaf_u_kernel;
+  if (!u_side) {
+    constexpr int KT = kLeafThreads / kTcNR;
+    const int mm = (a.R8 + 4 * KT - 1) / (4 * KT);
+    kern = mm <= 1 ? leaf_v_kernel<1> : mm <= 2 ? leaf_v_kernel<2> : leaf_v_kernel<kLeafMaxR8 / (4 * KT)>;
+  }
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (err != cudaSuccess) return err;
-  kern<<<n_leaves, kLeafThreads, smem, stream>>>(a);
+  kern<<<n_groups, kLeafThreads, smem, stream>>>(a);
   return cudaGetLastError();
 }
 
