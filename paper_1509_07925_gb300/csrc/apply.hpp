@@ -66,11 +66,11 @@ struct LeafArgs {
   const uint8_t* arena;    // packed arena of the SIMT path (leaf items)
   const Item* items;
   int64_t item_base;       // item of group 0; group g's item is item_base + g * item_stride
-  const int32_t* perm;     // (V^L)^*: tree -> natural Omega index; U^L: tree -> natural x index
+  const int32_t* perm;     // U^L: tree -> natural x index; permute: natural -> tree Omega index
   const int32_t* off;      // leaf offsets (tree order)
-  const float2* vec;       // (V^L)^*: g [nrhs][len_vec], natural order
+  const float2* vec;       // (V^L)^*: panel in tree order [point][64]; permute: g [nrhs][len_vec]
   const float* wl;         // U^L: level-L coefficients, row block * R + k, [re 64 | im 64] floats
-  float2* outp;            // U^L: u [nrhs][len_out]
+  float2* outp;            // U^L: u [nrhs][len_out]; permute: panel in tree order
   uint8_t* outs;           // (V^L)^*: split blocks of the level-L vector (block c g + t)
   int64_t len_vec, len_out;
   int32_t nrhs, rhs0, c, R;
@@ -94,5 +94,8 @@ bool leaf_fits(int R8, int c);   // leaf kernels: R8 <= 64, c <= 8
 cudaError_t launch_apply_tc(const TCArgs& a, int grid, size_t smem, cudaStream_t stream);
 // One CTA per group of c leaves.
 cudaError_t launch_leaf(const LeafArgs& a, bool u_side, int n_groups, cudaStream_t stream);
+// vec = g [nrhs][len_vec], perm = inverse tree permutation (natural -> tree, -1 if absent),
+// outp = panel in tree order [tree point][64]
+cudaError_t launch_permute_in(const LeafArgs& a, cudaStream_t stream);
 
 }  // namespace mbf

@@ -7,17 +7,19 @@
 // The MMA's A operand stacks the real and imaginary parts of X^T on M (rows n and
 // 64 + n: M = 128), its B operand is one plane of T (N = M_t), so two accumulators
 //     D1 = [X_re^T; X_im^T] T_re^T,     D2 = [X_re^T; X_im^T] T_im^T
-// give Y_re^T = D1[n] - D2[64 + n] and Y_im^T = D2[n] + D1[64 + n]: six MMAs per K = 16.
+// give Y_re^T = D1[n] - D2[64 + n] and Y_im^T = D2[n] + D1[64 + n].  With the tile's Re
+// and Im planes adjacent, D1 | D2 is one MMA of N = 2 M_t: three MMAs per K = 16.
 // The vectors between stages are kept as split blocks (apply.hpp), so a group's X is
-// two bulk copies per input block.
+// two contiguous runs per input block.
 //
 // Warp roles in a CTA (one per SM, persistent, cooperative):
 //   warp 0     one lane streams each group's tile, chunk by chunk (K = 16 columns,
 //              4 planes), into a ring of shared-memory slots (full/empty mbarriers);
 //   warp 1     allocates TMEM; one lane issues the MMAs into an accumulator set and
 //              commits completions to the mbarriers;
-//   warp 2     lane 0 waits for a group's inputs (dependency counters) and copies its c
-//              blocks into a panel buffer; the warp drops consumed blocks from L2;
+//   warps 2-3  thread 0 waits for a group's inputs (dependency counters); the 64
+//              threads copy its c blocks into a panel buffer with cp.async and drop
+//              the consumed blocks from L2;
 //   warps 4-7, 8-11   epilogue sets, one per accumulator set: read the accumulators
 //              (tcgen05.ld), pair the halves through shared memory, split and store the
 //              group's output blocks, then count them in for the consumers.
@@ -77,6 +79,13 @@ __device__ __forceinline__ uint64_t policy_evict_first() {
   uint64_t pol;
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
   return pol;
+}
+// 16-byte global -> shared copy through L2 (cp.async, the load/store path).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
 }
 // Drop a 128-byte line from L2 without writing it back (its contents become undefined).
 __device__ __forceinline__ void l2_discard(const void* p) {
@@ -207,7 +216,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
       mbar_init(&aempty[i], 1);
     }
     for (int s = 0; s < 2; ++s) {
-      mbar_init(&xfull[s], 1);
+      mbar_init(&xfull[s], 64);
       mbar_init(&xempty[s], 1);
       mbar_init(&dfull[s], 1);
       mbar_init(&dempty[s], 128);
@@ -262,13 +271,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
       while (!mbar_try(&afull[slot], ph) && gtimer() - t1 < kTimeoutNs) {
       }
     }
-  } else if (warp == 2) {
+  } else if (warp == 2 || warp == 3) {
     // ---------------------------------------------------------------- X panels
-    // Lane 0 waits and issues the copies.  Once the MMAs of a group are done (its
-    // buffer is free again), the whole warp drops the group's input blocks from L2:
-    // each block is read by exactly one group, so they need no write-back.
-    const uint8_t* prev[2][8] = {};
-    int64_t prev_bytes[2] = {0, 0};
+    // The 64 threads of warps 2-3 copy a group's c input blocks with 16-byte cp.async
+    // (the load/store path, so that the panels do not queue behind the tile stream's
+    // bulk copies), wait for their own copies, make them visible to the tensor cores
+    // and arrive on xfull.  Thread 0 first waits for the buffer and the inputs.  Each
+    // block is read by exactly one group, so once it sits in shared memory its lines
+    // are dropped from L2 without a write-back.
+    const int xt = tid - 64;
     int j = 0;
     bool ok = true;
     for (int e = 0; e < S && ok; ++e) {
@@ -278,11 +289,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
       const uint32_t half = uint32_t(st.R8_in) * 256u;      // hi or lo half of one block
       const uint32_t xhalf = uint32_t(st.K_pad) * 256u;     // hi or lo half of the panel buffer
       const int64_t blk = split_block_bytes(st.R8_in);
+      const int pieces = int(half >> 4);                      // 16-byte pieces of one half
       for (int g = blockIdx.x; g < st.n_groups && ok; g += gridDim.x, ++j) {
         const int xs = j % nxb;
         const uint32_t xu = uint32_t(j / nxb);
         int fail = 0;
-        if (lane == 0) {
+        if (xt == 0) {
           fail = !wait_bar(&xempty[xs], (xu & 1u) ^ 1u, abort);
           // all c input blocks written by the previous stage
           if (!fail && e > 0) {
@@ -300,40 +312,33 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
               }
               __nanosleep(32);
             }
-            asm volatile("fence.proxy.async.global;" ::: "memory");
           }
           if (fail) *abort = 1;
         }
-        if (__shfl_sync(0xffffffffu, fail, 0)) {
+        if (named_sync_or(3, 64, fail != 0)) {
           ok = false;
           break;
         }
-        // the group that used this buffer before is done: drop its input blocks from L2
-        if (j >= nxb) {
-          const int64_t nl = prev_bytes[xs] >> 7;
-          for (int t = 0; t < c; ++t)
-            for (int64_t q = lane; q < nl; q += 32) l2_discard(prev[xs][t] + (q << 7));
-        }
-        uint8_t* xb = xbuf + size_t(xs) * x_buf;
-        if (lane == 0) mbar_expect_tx(&xfull[xs], 2u * uint32_t(c) * half);
+        const uint32_t xb = sa(xbuf + size_t(xs) * x_buf);
         for (int t = 0; t < c; ++t) {
           const uint8_t* sb = src + int64_t(pat_blk(st.in_pat, g, t, st, c)) * blk;
-          prev[xs][t] = sb;
-          if (lane == 0)
-            for (int hl = 0; hl < 2; ++hl)
-              bulk_g2s(xb + size_t(hl) * xhalf + size_t(t) * half, sb + int64_t(hl) * half, half, &xfull[xs]);
+#pragma unroll 4
+          for (int q = xt; q < 2 * pieces; q += 64) {
+            const int hl = q >= pieces, pq = q - hl * pieces;
+            cp_async16(xb + uint32_t(hl) * xhalf + uint32_t(t) * half + uint32_t(pq) * 16u,
+                       sb + int64_t(hl) * half + int64_t(pq) * 16);
+          }
         }
-        prev_bytes[xs] = blk;
-        __syncwarp();
+        cp_async_wait_all();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(&xfull[xs]);
+        named_sync(3, 64);          // every thread's copies of the blocks have landed
+        for (int t = 0; t < c; ++t) {
+          const uint8_t* sb = src + int64_t(pat_blk(st.in_pat, g, t, st, c)) * blk;
+          for (int64_t q = xt; q < (blk >> 7); q += 64) l2_discard(sb + (q << 7));
+        }
       }
     }
-    // wait (bounded) for the copies of the last groups
-    if (lane == 0)
-      for (int q = max(0, j - nxb); q < j; ++q) {
-        const uint64_t t1 = gtimer();
-        while (!mbar_try(&xfull[q % nxb], uint32_t(q / nxb) & 1u) && gtimer() - t1 < kTimeoutNs) {
-        }
-      }
   } else if (warp == 1 && lane == 0) {
     // ---------------------------------------------------------------- MMA issuer
     uint32_t ca = 0;
@@ -345,8 +350,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
       const int nk = st.K_pad / 16;
       const uint32_t xhalf = uint32_t(st.K_pad) * 256u;
       const uint32_t pb = uint32_t(st.plane_bytes);
-      // kind::f16, FP32 accumulate, BF16 A and B, both K-major, N = M_t, M = 128
-      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(st.M_t >> 3) << 17) | (uint32_t(128 >> 4) << 24);
+      // kind::f16, FP32 accumulate, BF16 A and B, both K-major, M = 128.  While 2 M_t <= 256
+      // the Re and Im planes of the tile form one B operand of N = 2 M_t rows (three MMAs
+      // per K16 fill D1 | D2 at once); wider tiles take N = M_t, one MMA per plane.
+      const bool stack = 2 * st.M_t <= 256;
+      const uint32_t nmma = uint32_t(stack ? 2 * st.M_t : st.M_t);
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((nmma >> 3) << 17) | (uint32_t(128 >> 4) << 24);
       for (int g = blockIdx.x; g < st.n_groups && ok; g += gridDim.x, ++j) {
         const int xs = j % nxb, ds = j % nsets;
         const uint32_t xu = uint32_t(j / nxb), du = uint32_t(j / nsets);
@@ -359,7 +368,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t d1 = taddr + uint32_t(ds) * set_cols, d2 = d1 + uint32_t(a.mt_max);
+        const uint32_t d1 = taddr + uint32_t(ds) * set_cols, d2 = d1 + uint32_t(st.M_t);
         const uint32_t xb = xbase0 + uint32_t(xs) * x_buf;
         for (int kk = 0; kk < nk; ++kk, ++ca) {
           const uint32_t slot = ca % uint32_t(nsa), ph = (ca / uint32_t(nsa)) & 1u;
@@ -371,21 +380,27 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
             ok = false;
             break;
           }
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          // (the chunk was written by the bulk copy the mbarrier tracks: no tcgen05 fence)
           const uint32_t as = abase + slot * a_slot;
           // A: panel half (hi / lo), K-major, next 8 K at +2048, next 8 rows at +128
           const uint64_t xh = sdesc(xb + uint32_t(kk) * 4096u, 2048u, 128u);
           const uint64_t xl = sdesc(xb + xhalf + uint32_t(kk) * 4096u, 2048u, 128u);
-          // B: tile planes 0 Re hi, 1 Re lo, 2 Im hi, 3 Im lo; next 8 K at +128, next 8 rows at +256
+          // B: tile planes 0 Re hi, 1 Im hi, 2 Re lo, 3 Im lo; next 8 K at +128, next 8 rows at +256
           const uint64_t t0 = sdesc(as, 128u, 256u), t1 = sdesc(as + pb, 128u, 256u);
           const uint64_t t2 = sdesc(as + 2u * pb, 128u, 256u), t3 = sdesc(as + 3u * pb, 128u, 256u);
           const uint32_t acc0 = kk > 0 ? 1u : 0u;
-          mma_bf16(d1, xh, t0, idesc, acc0);
-          mma_bf16(d1, xh, t1, idesc, 1u);
-          mma_bf16(d1, xl, t0, idesc, 1u);
-          mma_bf16(d2, xh, t2, idesc, acc0);
-          mma_bf16(d2, xh, t3, idesc, 1u);
-          mma_bf16(d2, xl, t2, idesc, 1u);
+          if (stack) {          // t0 spans [Re hi; Im hi], t2 spans [Re lo; Im lo]
+            mma_bf16(d1, xh, t0, idesc, acc0);
+            mma_bf16(d1, xh, t2, idesc, 1u);
+            mma_bf16(d1, xl, t0, idesc, 1u);
+          } else {
+            mma_bf16(d1, xh, t0, idesc, acc0);
+            mma_bf16(d1, xh, t2, idesc, 1u);
+            mma_bf16(d1, xl, t0, idesc, 1u);
+            mma_bf16(d2, xh, t1, idesc, acc0);
+            mma_bf16(d2, xh, t3, idesc, 1u);
+            mma_bf16(d2, xl, t1, idesc, 1u);
+          }
           mma_commit(&aempty[slot]);
         }
         if (!ok) break;
@@ -436,7 +451,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t d1 = taddr + uint32_t(set) * set_cols + lane_base, d2 = d1 + uint32_t(a.mt_max);
+        const uint32_t d1 = taddr + uint32_t(set) * set_cols + lane_base, d2 = d1 + uint32_t(st.M_t);
         for (int c0 = 0; c0 < st.M_t; c0 += kTcChunk, ++chunk_no) {
           float v1[kTcChunk], v2[kTcChunk];
           tmem_ld16(d1 + uint32_t(c0), v1);
@@ -477,10 +492,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
         mbar_arrive(&dempty[set]);
         // count the written blocks in for the consumers of the next stage
         if (!last) {
-          asm volatile("fence.proxy.async.global;" ::: "memory");
-          __threadfence();
+          // the set's stores are ordered before the counting threads' fence by the
+          // barrier; the fence then makes them visible GPU-wide before the counts
           named_sync(bar_id, 128);
           if (et < c) {
+            __threadfence();
             const int64_t P = pat_blk(st.out_pat, g, et, st, c);
             atomicAdd(cnt_out + pat_group(nst.in_pat, P, nst, c), 1u);
           }
@@ -498,7 +514,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
 // ------------------------------------------------------------------ leaf kernels
 // One CTA per group (its c leaves); the group's points are staged kLeafPts at a time.
 constexpr int kLeafThreads = 256;
-constexpr int kLeafPts = 64;        // points staged per round
+constexpr int kLeafPts = 64;        // points staged per round (= kTcNR)
 constexpr int kLeafMaxR8 = 64;      // largest leaf rank (rounded up to 8) of the tensor path
 constexpr int kLeafMaxC = 8;        // children per node (3-D)
 
@@ -511,114 +527,158 @@ __device__ __forceinline__ float2 item_entry(const uint8_t* base, const Item& it
   return make_float2(__ldg(re + q), __ldg(re + pad4(int64_t(nl) * it.len) + q));
 }
 
-// Split block `leaf` from the accumulators of thread (n, kq) (rows k = 4 (m KT + kq) + j):
-// byte (hl, k, ri, n) as in apply.hpp; 4 consecutive k = 8 bytes per plane.
-template <int MM, int KT>
-__device__ __forceinline__ void store_split_rows(uint8_t* outs, int64_t leaf, int R8, int n, int kq,
-                                                 float2 (&acc)[MM][4]) {
-  const int64_t half = int64_t(R8) * 256;
-  uint8_t* ob = outs + leaf * split_block_bytes(R8) + (n >> 3) * 128 + (n & 7) * 16;
+// Panel in tree order: gt[inv(i)][n] = g[rhs0 + n][i] for the natural Omega indices i
+// (inv(i) < 0: not in the tree), zero for rhs0 + n >= nrhs.  A CTA moves kPermPts
+// consecutive natural indices for the 64 RHS of the panel: rows of g are read as
+// 16-byte runs, and each point's 64 values are written as one 512-byte row of gt.  In
+// shared memory an entry (n, i) sits in float4 (n / 2, i) at half n % 2, so that a warp
+// reads one point's row without bank conflicts.
+constexpr int kPermPts = 128;
+constexpr int kPermStride = kPermPts + 1;   // float4 per pair of RHS rows
+__global__ void __launch_bounds__(kLeafThreads) permute_in_kernel(const __grid_constant__ LeafArgs a) {
+  extern __shared__ __align__(16) float4 ptile[];      // [kTcNR / 2][kPermStride]
+  __shared__ int ptp[kPermPts];                        // tree positions of the tile's points
+  const int64_t i0 = int64_t(blockIdx.x) * kPermPts;
+  const int tid = threadIdx.x;
+  if (tid < kPermPts) ptp[tid] = i0 + tid < a.len_vec ? __ldg(a.perm + i0 + tid) : -1;
+  // rows of g start 16-byte aligned: 16-byte loads
+  const bool vec = (a.len_vec & 1) == 0 && (reinterpret_cast<uintptr_t>(a.vec) & 15) == 0;
+  constexpr int Q4 = kPermPts / 2;                     // float4 per row of the tile
+  constexpr int NQ = kTcNR * Q4 / kLeafThreads;       // float4 per thread (all loads first)
+  float4 v[NQ];
 #pragma unroll
-  for (int m = 0; m < MM; ++m) {
-    const int k0 = 4 * (m * KT + kq);
-    if (k0 < R8) {
-      uint32_t hr[2], lr[2], hi[2], li[2];
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const float r0 = acc[m][2 * i].x, r1 = acc[m][2 * i + 1].x;
-        const float i0 = acc[m][2 * i].y, i1 = acc[m][2 * i + 1].y;
-        hr[i] = tc::pack_bf16x2(r0, r1);
-        lr[i] = tc::pack_bf16x2(r0 - __uint_as_float(hr[i] << 16), r1 - __uint_as_float(hr[i] & 0xffff0000u));
-        hi[i] = tc::pack_bf16x2(i0, i1);
-        li[i] = tc::pack_bf16x2(i0 - __uint_as_float(hi[i] << 16), i1 - __uint_as_float(hi[i] & 0xffff0000u));
+  for (int u = 0; u < NQ; ++u) {
+    const int q = tid + u * kLeafThreads, n = q / Q4, i2 = q - n * Q4, rhs = a.rhs0 + n;
+    const int64_t i = i0 + 2 * i2;
+    v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (rhs < a.nrhs) {
+      const float2* row = a.vec + int64_t(rhs) * a.len_vec;
+      if (vec && i + 1 < a.len_vec) {
+        v[u] = __ldg(reinterpret_cast<const float4*>(row + i));
+      } else {
+        if (i < a.len_vec) {
+          const float2 x = __ldg(row + i);
+          v[u].x = x.x;
+          v[u].y = x.y;
+        }
+        if (i + 1 < a.len_vec) {
+          const float2 x = __ldg(row + i + 1);
+          v[u].z = x.x;
+          v[u].w = x.y;
+        }
       }
-      uint8_t* o = ob + (k0 >> 3) * 2048 + (k0 & 7) * 2;
-      *reinterpret_cast<uint2*>(o) = make_uint2(hr[0], hr[1]);                 // Re hi
-      *reinterpret_cast<uint2*>(o + 1024) = make_uint2(hi[0], hi[1]);          // Im hi
-      *reinterpret_cast<uint2*>(o + half) = make_uint2(lr[0], lr[1]);          // Re lo
-      *reinterpret_cast<uint2*>(o + half + 1024) = make_uint2(li[0], li[1]);   // Im lo
     }
+  }
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[m][j] = make_float2(0.f, 0.f);
+  for (int u = 0; u < NQ; ++u) {
+    const int q = tid + u * kLeafThreads, n = q / Q4, i2 = q - n * Q4;
+    float2* t0 = reinterpret_cast<float2*>(ptile + (n >> 1) * kPermStride + 2 * i2) + (n & 1);
+    t0[0] = make_float2(v[u].x, v[u].y);
+    t0[2] = make_float2(v[u].z, v[u].w);
+  }
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31;
+#pragma unroll 4
+  for (int ii = warp; ii < kPermPts; ii += kLeafThreads / 32) {
+    const int tp = ptp[ii];
+    if (tp >= 0)
+      reinterpret_cast<float4*>(a.outp + int64_t(tp) * kTcNR)[lane] = ptile[lane * kPermStride + ii];
   }
 }
 
-// (V^L)^* for a panel of 64 RHS, one CTA per group g (leaves j = c g + t):
-//   y_j[k][n] = sum over the points b of leaf j of conj(V^L_j[b][k]) g[rhs0 + n][w_perm(b)],
-// stored as split block j (rows k >= R are zero).  g is read in natural order through
-// the tree permutation w_perm (the input permutation folded into the loads; a thread
-// gathers one point for 16 RHS rows).  The group's item holds conj(V) with line = point
-// (tree order from the group's first point), entry = k.  Thread (n, kq) accumulates
-// column n for the rows k = 4 (m KT + kq) + 0..3 and emits a leaf's block when the
-// points pass the leaf's end (empty leaves give zero blocks).
-// MM = ceil(R8 / 16): row blocks of 4 per thread.
-template <int MM>
-__global__ void __launch_bounds__(kLeafThreads) leaf_v_kernel(const __grid_constant__ LeafArgs a) {
-  constexpr int NR = kTcNR, KT = kLeafThreads / NR, NRP = NR + 1;
-  constexpr int GQ = kLeafThreads / kLeafPts, GR = NR / GQ;   // gather: rows per thread
+// Rows k0 .. k0 + 7 of column n of split block `leaf` from 8 accumulators: byte
+// (hl, k, ri, n) as in apply.hpp, so 8 consecutive k are one 16-byte run per plane.
+__device__ __forceinline__ void store_split8(uint8_t* outs, int64_t leaf, int R8, int n, int k0, float2 (&acc)[8]) {
+  float re[8], im[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    re[j] = acc[j].x;
+    im[j] = acc[j].y;
+    acc[j] = make_float2(0.f, 0.f);
+  }
+  uint4 rh, rl, ih, il;
+  tc::split8(re, rh, rl);
+  tc::split8(im, ih, il);
+  uint8_t* o = outs + leaf * split_block_bytes(R8) + (k0 >> 3) * 2048 + (n >> 3) * 128 + (n & 7) * 16;
+  const int64_t half = int64_t(R8) * 256;
+  *reinterpret_cast<uint4*>(o) = rh;                 // Re hi
+  *reinterpret_cast<uint4*>(o + 1024) = ih;          // Im hi
+  *reinterpret_cast<uint4*>(o + half) = rl;          // Re lo
+  *reinterpret_cast<uint4*>(o + half + 1024) = il;   // Im lo
+}
+
+// (V^L)^* for a panel of 64 RHS, one CTA of 64 R8 / 8 threads per group g (leaves
+// j = c g + t):
+//   y_j[k][n] = sum over the points b of leaf j of conj(V^L_j[b][k]) gt[b][n],
+// gt = the panel in tree order (permute_in_kernel), stored as split block j (rows
+// k >= R are zero).  The group's item holds conj(V) with line = point (tree order from
+// the group's first point), entry = k; it is staged kLeafPts points at a time in shared
+// memory.  Thread (n, kg) accumulates column n for the 8 rows k = 8 kg + 0..7 over the
+// points of one leaf, reading gt[b][n] straight from L2 eight points ahead, then stores
+// the rows; empty leaves give zero blocks.  Little shared memory per CTA, so that every
+// group's CTA is resident at once.
+__device__ __forceinline__ void leaf_v_point(float2 (&acc)[8], const float2* vrow, float2 x) {
+  const float4* vp = reinterpret_cast<const float4*>(vrow);
+#pragma unroll
+  for (int j2 = 0; j2 < 4; ++j2) {
+    const float4 v = vp[j2];
+    acc[2 * j2].x = fmaf(v.x, x.x, fmaf(-v.y, x.y, acc[2 * j2].x));
+    acc[2 * j2].y = fmaf(v.x, x.y, fmaf(v.y, x.x, acc[2 * j2].y));
+    acc[2 * j2 + 1].x = fmaf(v.z, x.x, fmaf(-v.w, x.y, acc[2 * j2 + 1].x));
+    acc[2 * j2 + 1].y = fmaf(v.z, x.y, fmaf(v.w, x.x, acc[2 * j2 + 1].y));
+  }
+}
+
+__global__ void __launch_bounds__(kTcNR * kLeafMaxR8 / 8) leaf_v_kernel(const __grid_constant__ LeafArgs a) {
+  constexpr int NR = kTcNR;
   extern __shared__ __align__(16) float2 lsm[];
   __shared__ int lend[kLeafMaxC + 1];
-  const int g = blockIdx.x, c = a.c, R = a.R, R8 = a.R8;
-  const int tid = threadIdx.x, n = tid % NR, kq = tid / NR;
+  const int g = blockIdx.x, c = a.c, R = a.R, R8 = a.R8, nth = int(blockDim.x);
+  const int tid = threadIdx.x, n = tid % NR, kg = tid / NR, k0 = 8 * kg;
   if (tid <= c) lend[tid] = a.off[c * g + tid];
   const Item it = a.items[a.item_base + int64_t(g) * a.item_stride];
   const uint8_t* ibase = a.arena + size_t(it.off128) * 128;
   const int pg = a.off[c * g], np = a.off[c * g + c] - pg;
   float2* vs = lsm;                        // [kLeafPts][R8], zero for k >= R
-  float2* xs = vs + kLeafPts * R8;         // [kLeafPts][NR + 1]
-  float2 acc[MM][4];
+  const float2* xg = a.vec + int64_t(pg) * NR + n;   // gt[pg + b][n] = xg[b * NR]
+  float2 acc[8];
 #pragma unroll
-  for (int m = 0; m < MM; ++m)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[m][j] = make_float2(0.f, 0.f);
+  for (int j = 0; j < 8; ++j) acc[j] = make_float2(0.f, 0.f);
+  __syncthreads();                         // lend
   int t = 0;                               // leaf being accumulated
   for (int b0 = 0; b0 < np; b0 += kLeafPts) {
     const int nb = min(kLeafPts, np - b0);
-    __syncthreads();                       // previous round's reads done (and lend written)
-    for (int q = tid; q < nb * R8; q += kLeafThreads) {
-      const int b = q / R8, k = q - b * R8;
-      vs[q] = k < R ? item_entry(ibase, it, b0 + b, k) : make_float2(0.f, 0.f);
-    }
-    {
-      const int b = tid % kLeafPts, n0 = tid / kLeafPts;
-      if (b < nb) {
-        const int nat = __ldg(a.perm + pg + b0 + b);
-        float2 v[GR];
+    if (b0 > 0) __syncthreads();           // previous round's reads done
+    for (int q0 = tid; q0 < nb * R8; q0 += 8 * nth) {   // 8 loads in flight per thread
+      float2 v[8];
 #pragma unroll
-        for (int i = 0; i < GR; ++i) {
-          const int rhs = a.rhs0 + n0 + i * GQ;
-          v[i] = rhs < a.nrhs ? __ldg(a.vec + int64_t(rhs) * a.len_vec + nat) : make_float2(0.f, 0.f);
-        }
-#pragma unroll
-        for (int i = 0; i < GR; ++i) xs[b * NRP + n0 + i * GQ] = v[i];
+      for (int u = 0; u < 8; ++u) {
+        const int q = q0 + u * nth, b = q / R8, k = q - b * R8;
+        v[u] = q < nb * R8 && k < R ? item_entry(ibase, it, b0 + b, k) : make_float2(0.f, 0.f);
       }
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (q0 + u * nth < nb * R8) vs[q0 + u * nth] = v[u];
     }
     __syncthreads();
-    for (int b = 0; b < nb; ++b) {
-      const int p = pg + b0 + b;
-      while (p >= lend[t + 1]) {           // leaves that end before point p (uniform branch)
-        store_split_rows<MM, KT>(a.outs, int64_t(c) * g + t, R8, n, kq, acc);
-        ++t;
-      }
-      const float2 x = xs[b * NRP + n];
+    int b = 0;
+    while (t < c) {
+      const int le = lend[t + 1] - pg - b0;          // end of leaf t in this round's points
+      const int bend = min(le, nb);
+      for (; b + 8 <= bend; b += 8) {
+        float2 x[8];
 #pragma unroll
-      for (int m = 0; m < MM; ++m) {
-        const int k0 = 4 * (m * KT + kq);
-        if (k0 < R8) {
-          const float4 v01 = *reinterpret_cast<const float4*>(vs + b * R8 + k0);
-          const float4 v23 = *reinterpret_cast<const float4*>(vs + b * R8 + k0 + 2);
-          const float vr[4] = {v01.x, v01.z, v23.x, v23.z}, vi[4] = {v01.y, v01.w, v23.y, v23.w};
+        for (int u = 0; u < 8; ++u) x[u] = __ldcg(xg + int64_t(b0 + b + u) * NR);
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            acc[m][j].x = fmaf(vr[j], x.x, fmaf(-vi[j], x.y, acc[m][j].x));
-            acc[m][j].y = fmaf(vr[j], x.y, fmaf(vi[j], x.x, acc[m][j].y));
-          }
-        }
+        for (int u = 0; u < 8; ++u) leaf_v_point(acc, vs + (b + u) * R8 + k0, x[u]);
       }
+      for (; b < bend; ++b) leaf_v_point(acc, vs + b * R8 + k0, __ldcg(xg + int64_t(b0 + b) * NR));
+      if (le > nb) break;                            // leaf t continues in the next round
+      store_split8(a.outs, int64_t(c) * g + t, R8, n, k0, acc);
+      ++t;
     }
   }
-  if (np == 0) __syncthreads();            // lend visible
-  for (; t < c; ++t) store_split_rows<MM, KT>(a.outs, int64_t(c) * g + t, R8, n, kq, acc);
+  for (; t < c; ++t) store_split8(a.outs, int64_t(c) * g + t, R8, n, k0, acc);
 }
 
 // U^L for a panel, one CTA per group g (leaves i = c g + t):
@@ -644,15 +704,33 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_u_kernel(const __grid_const
   {
     const float4* src = reinterpret_cast<const float4*>(a.wl + int64_t(c) * g * R * 2 * NR);
     float4* dst = reinterpret_cast<float4*>(ws);
-    for (int q = tid; q < c * R * (2 * NR / 4); q += kLeafThreads) dst[q] = __ldcg(src + q);
+    const int nq4 = c * R * (2 * NR / 4);
+    for (int q0 = tid; q0 < nq4; q0 += 8 * kLeafThreads) {      // 8 loads in flight per thread
+      float4 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (q0 + u * kLeafThreads < nq4) v[u] = __ldcg(src + q0 + u * kLeafThreads);
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (q0 + u * kLeafThreads < nq4) dst[q0 + u * kLeafThreads] = v[u];
+    }
   }
   const int bb = tid % kLeafPts, nq = tid / kLeafPts;
   for (int b0 = 0; b0 < np; b0 += kLeafPts) {
     const int nb = min(kLeafPts, np - b0);
     __syncthreads();
-    for (int q = tid; q < R * nb; q += kLeafThreads) {
-      const int k = q / nb, b = q - k * nb;
-      us[k * kLeafPts + b] = item_entry(ibase, it, k, b0 + b);
+    for (int q0 = tid; q0 < R * nb; q0 += 8 * kLeafThreads) {   // 8 loads in flight per thread
+      float2 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int q = q0 + u * kLeafThreads, k = q / nb, b = q - k * nb;
+        v[u] = q < R * nb ? item_entry(ibase, it, k, b0 + b) : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int q = q0 + u * kLeafThreads, k = q / nb, b = q - k * nb;
+        if (q < R * nb) us[k * kLeafPts + b] = v[u];
+      }
     }
     __syncthreads();
     if (bb < nb) {
@@ -708,7 +786,7 @@ size_t tc_smem_bytes(int nsa, int nxb, int nsets, int mt_max, int kpad_max) {
 size_t leaf_smem_bytes(int R, int c, bool u_side) {
   const int R8 = (R + 7) & ~7;
   return u_side ? size_t(c) * R * 2 * kTcNR * sizeof(float) + size_t(R) * kLeafPts * sizeof(float2)
-                : sizeof(float2) * (size_t(kLeafPts) * R8 + size_t(kLeafPts) * (kTcNR + 1));
+                : sizeof(float2) * size_t(kLeafPts) * R8;
 }
 
 bool leaf_fits(int R8, int c) { return R8 <= kLeafMaxR8 && c <= kLeafMaxC; }
@@ -737,17 +815,22 @@ size_t tc_counter_bytes(const TCPlan& plan) {
   return (n * sizeof(unsigned) + 255) & ~size_t(255);
 }
 
+cudaError_t launch_permute_in(const LeafArgs& a, cudaStream_t stream) {
+  const size_t smem = sizeof(float4) * (kTcNR / 2) * kPermStride;
+  cudaError_t err = cudaFuncSetAttribute(permute_in_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (err != cudaSuccess) return err;
+  permute_in_kernel<<<unsigned((a.len_vec + kPermPts - 1) / kPermPts), kLeafThreads, smem, stream>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_leaf(const LeafArgs& a, bool u_side, int n_groups, cudaStream_t stream) {
   const size_t smem = leaf_smem_bytes(a.R, a.c, u_side);
-  void (*kern)(LeafArgs) = leaf_u_kernel;
-  if (!u_side) {
-    constexpr int KT = kLeafThreads / kTcNR;
-    const int mm = (a.R8 + 4 * KT - 1) / (4 * KT);
-    kern = mm <= 1 ? leaf_v_kernel<1> : mm <= 2 ? leaf_v_kernel<2> : leaf_v_kernel<kLeafMaxR8 / (4 * KT)>;
-  }
+  void (*kern)(LeafArgs) = u_side ? leaf_u_kernel : leaf_v_kernel;
+  // (V^L)^*: one thread per RHS column and group of 8 rows
+  const int threads = u_side ? kLeafThreads : kTcNR * (a.R8 / 8);
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (err != cudaSuccess) return err;
-  kern<<<n_groups, kLeafThreads, smem, stream>>>(a);
+  kern<<<n_groups, threads, smem, stream>>>(a);
   return cudaGetLastError();
 }
 

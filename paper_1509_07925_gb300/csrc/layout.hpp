@@ -72,7 +72,7 @@ struct Plan {
 
 // Tensor-core path: one main stage (a G^l or (H^l)^* level) of c^(L-1) group tiles.
 // A tile is M_t = c R_out rows by K_t = c R_in columns, stored as K_pad/16 chunks; a
-// chunk is 4 planes (Re hi, Re lo, Im hi, Im lo in bf16, the split T = hi + lo), each
+// chunk is 4 planes (Re hi, Im hi, Re lo, Im lo in bf16, the split T = hi + lo), each
 // plane M8 = roundup(M_t, 8) rows by 16 columns in 8x8 core matrices (128 B), the two
 // core matrices of a row group adjacent (K-major, no swizzle).
 struct TCStage {

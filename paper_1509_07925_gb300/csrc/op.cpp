@@ -286,7 +286,7 @@ void pack_tc(const mbf_factors_t& f, const Plan& sp, TCPlan& tp, std::vector<uin
           const uint16_t rh = bf16_rn(re), ih = bf16_rn(im);
           const uint16_t rl = bf16_rn(float(v.real() - double(bf16_to_float(rh))));
           const uint16_t il = bf16_rn(float(v.imag() - double(bf16_to_float(ih))));
-          const uint16_t vals[4] = {rh, rl, ih, il};
+          const uint16_t vals[4] = {rh, ih, rl, il};   // planes: Re hi, Im hi, Re lo, Im lo
           const int kk16 = k / 16, kc = k % 16;
           const size_t in_plane = size_t(((m / 8) * 2 + kc / 8) * 128 + (m % 8) * 16 + (kc % 8) * 2);
           for (int pl = 0; pl < 4; ++pl)
@@ -473,6 +473,8 @@ void op_free(mbf_op_s* op) {
     cudaEventDestroy(r.e1);
   }
   cudaFree(op->d_tc_counters);
+  cudaFree(op->d_tc_gt);
+  cudaFree(op->d_w_inv);
   cudaSetDevice(prev);
   delete op;
 }
@@ -547,6 +549,9 @@ mbf_op_s* op_create(const mbf_factors_t& f) {
       // more than half the SM's shared memory: one CTA per SM, so that each CTA's
       // 512-column TMEM allocation never waits on another CTA of the same launch
       op->tc_smem = std::max(smem(op->tc_nsa), size_t(optin) / 2 + 1024);
+      std::vector<int32_t> winv(size_t(std::max<int64_t>(f.n_in, 1)), -1);
+      for (int64_t p = 0; p < f.n_w; ++p) winv[size_t(f.w_perm[p])] = int32_t(p);
+      op->d_w_inv = dev_upload(winv, "inverse Omega permutation");
       op->tc_bytes = int64_t(tc_arena.size());
       op->d_tc_arena = dev_upload(tc_arena, "tensor-core arena");
     } catch (const Error& err) {
@@ -560,8 +565,8 @@ mbf_op_s* op_create(const mbf_factors_t& f) {
 }
 
 // ---------------------------------------------------------------- kernel timing
-enum ProfKind { PK_SIMT = 0, PK_LEAF_V, PK_TC, PK_LEAF_U, PK_COUNT };
-const char* const kProfNames[PK_COUNT] = {"bf_apply_simt", "leaf_v", "bf_apply_tc", "leaf_u"};
+enum ProfKind { PK_SIMT = 0, PK_PERMUTE, PK_LEAF_V, PK_TC, PK_LEAF_U, PK_COUNT };
+const char* const kProfNames[PK_COUNT] = {"bf_apply_simt", "permute_in", "leaf_v", "bf_apply_tc", "leaf_u"};
 
 // Records an event before a launch when profiling is on (nullptr otherwise).
 cudaEvent_t prof_begin(mbf_op_s* op, cudaStream_t st) {
@@ -592,8 +597,8 @@ void prof_collect(mbf_op_s* op) {
   op->prof_pending.clear();
 }
 
-// Tensor-core apply, per panel of 64 RHS: the (V^L)^* leaf kernel (which gathers g from
-// natural order), the persistent tcgen05 kernel over the G / H levels, the U^L leaf
+// Tensor-core apply, per panel of 64 RHS: permute the panel into Omega-tree order, the
+// (V^L)^* leaf kernel, the persistent tcgen05 kernel over the G / H levels, the U^L leaf
 // kernel (which scatters u to natural order).
 void apply_tc(mbf_op_s* op, const float2* g, float2* u, int64_t nrhs, cudaStream_t st, int grid, bool accumulate) {
   if (!op->tc_unavailable.empty()) fail(MBF_ERR_INVALID, "tensor path unavailable: " + op->tc_unavailable);
@@ -609,23 +614,30 @@ void apply_tc(mbf_op_s* op, const float2* g, float2* u, int64_t nrhs, cudaStream
   uint8_t* bufs = yl + vec_bytes;                    // main stage e < S - 1 writes bufs + e * vec_bytes
   float* ylast = reinterpret_cast<float*>(yl + int64_t(S) * vec_bytes);   // last main stage
   for (int64_t r0 = 0; r0 < nrhs; r0 += kTcNR) {
-    // (V^L)^*: g (natural order, gathered through w_perm) -> yl
+    // g -> panel in tree order
+    LeafArgs pa{};
+    pa.perm = op->d_w_inv;
+    pa.vec = g;
+    pa.outp = op->d_tc_gt;
+    pa.len_vec = op->n_in;
+    pa.nrhs = int32_t(nrhs);
+    pa.rhs0 = int32_t(r0);
+    cudaEvent_t e0 = prof_begin(op, st);
+    cuda_check(launch_permute_in(pa, st), "panel permute launch");
+    prof_end(op, PK_PERMUTE, e0, st);
+    // (V^L)^*: panel -> yl
     LeafArgs la{};
     la.arena = op->d_arena;
     la.items = op->d_items;
     la.item_base = leaf_st.item_base;
     la.item_stride = leaf_st.n_items;
-    la.perm = op->d_w_perm;
     la.off = op->d_w_off;
-    la.vec = g;
-    la.len_vec = op->n_in;
-    la.nrhs = int32_t(nrhs);
-    la.rhs0 = int32_t(r0);
+    la.vec = op->d_tc_gt;
     la.outs = yl;
     la.c = op->c;
     la.R = op->RV[size_t(op->L)];
     la.R8 = tp.st[0].R8_in;
-    cudaEvent_t e0 = prof_begin(op, st);
+    e0 = prof_begin(op, st);
     cuda_check(launch_leaf(la, false, leaf_st.n_groups, st), "leaf (V^L)^* launch");
     prof_end(op, PK_LEAF_V, e0, st);
     // G / H levels on tensor cores
@@ -760,6 +772,8 @@ void tc_prepare(mbf_op_s* op) {
     fail(MBF_ERR_OOM, "cudaMalloc tensor-path workspace");
   if (cudaMalloc(&op->d_tc_counters, tc_counter_bytes(op->tcplan)) != cudaSuccess)
     fail(MBF_ERR_OOM, "cudaMalloc tensor-path counters");
+  if (cudaMalloc(&op->d_tc_gt, size_t(std::max<int64_t>(op->n_w, 1)) * kTcNR * sizeof(float2)) != cudaSuccess)
+    fail(MBF_ERR_OOM, "cudaMalloc tensor-path input panel");
 }
 
 void apply_dev(mbf_op_s* op, const void* in, void* out, int64_t nrhs, int32_t precision, cudaStream_t st,

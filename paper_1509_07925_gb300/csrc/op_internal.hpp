@@ -38,6 +38,8 @@ struct mbf_op_s {
   size_t tc_smem = 0;
   uint8_t* d_tc_bufs = nullptr;       // S_main + 1 vectors of c^L blocks x R8 x 64 entries (8 bytes each)
   unsigned* d_tc_counters = nullptr;
+  float2* d_tc_gt = nullptr;          // input panel in Omega-tree order [n_w][64]
+  int32_t* d_w_inv = nullptr;         // natural Omega index -> tree position (-1: not in the tree)
   std::string tc_unavailable;         // why the tensor path cannot run for this operator ("" if it can)
   int sms = 0;                        // SMs of the device (the persistent grids)
   int64_t tc_min_rhs = 8;             // AUTO: tensor cores from this many RHS (tuner may change it)
