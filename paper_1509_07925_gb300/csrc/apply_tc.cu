@@ -15,14 +15,15 @@
 // Warp roles in a CTA (one per SM, persistent, cooperative):
 //   warp 0     one lane streams each group's tile, chunk by chunk (K = 16 columns,
 //              4 planes), into a ring of shared-memory slots (full/empty mbarriers);
-//   warp 1     allocates TMEM; one lane issues the MMAs into an accumulator set and
-//              commits completions to the mbarriers;
+//   warp 1     allocates TMEM; runs the MMA loop (warp-uniform operands), one elected
+//              lane issuing the MMAs into an accumulator set and the commits;
 //   warps 2-3  thread 0 waits for a group's inputs (dependency counters); the 64
 //              threads copy its c blocks into a panel buffer with cp.async and drop
 //              the consumed blocks from L2;
 //   warps 4-7, 8-11   epilogue sets, one per accumulator set: read the accumulators
 //              (tcgen05.ld), pair the halves through shared memory, split and store the
-//              group's output blocks, then count them in for the consumers.
+//              group's output blocks, and hand them to
+//   warp 12    the signal warp, which fences and counts them in for the consumers.
 // The (V^L)^* and U^L leaf products run before and after it (leaf kernels below).
 // Every wait is bounded; on a timeout the status word is set and all roles drain.
 #include <cuda_runtime.h>
@@ -123,6 +124,13 @@ __device__ __forceinline__ bool named_sync_or(int id, int n, bool v) {
   return r != 0;
 }
 
+// One lane of the (converged) warp: true in exactly one lane.
+__device__ __forceinline__ bool elect_one() {
+  uint32_t pred = 0;
+  asm volatile("{\n .reg .pred P;\n elect.sync _|P, 0xffffffff;\n selp.u32 %0, 1, 0, P;\n}\n" : "=r"(pred));
+  return pred != 0;
+}
+
 // 16 consecutive TMEM columns of this thread's lane (one row of the accumulator).
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   uint32_t r[16];
@@ -187,7 +195,7 @@ __device__ __forceinline__ bool wait_bar(uint64_t* b, uint32_t ph, volatile int*
 
 }  // namespace tc
 
-constexpr int kTcThreads = 384;
+constexpr int kTcThreads = 416;   // 13 warps (roles above)
 constexpr int kTcChunk = 16;   // accumulator columns per epilogue step
 
 __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_constant__ TCArgs a) {
@@ -205,7 +213,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
   uint64_t* xempty = xfull + 2;
   uint64_t* dfull = xempty + 2;
   uint64_t* dempty = dfull + 2;
-  uint64_t* done = dempty + 2;
+  uint64_t* stored = dempty + 2;     // [set]: the set's output blocks of a group are written
+  uint64_t* signaled = stored + 2;   // [set]: the signal warp has counted them in
+  uint64_t* done = signaled + 2;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
   volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
 
@@ -220,6 +230,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
       mbar_init(&xempty[s], 1);
       mbar_init(&dfull[s], 1);
       mbar_init(&dempty[s], 128);
+    }
+    for (int s2 = 0; s2 < 2; ++s2) {
+      mbar_init(&stored[s2], 128);
+      mbar_init(&signaled[s2], 1);
     }
     mbar_init(done, 1);
     *abort = 0;
@@ -339,8 +353,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
         }
       }
     }
-  } else if (warp == 1 && lane == 0) {
+  } else if (warp == 1) {
     // ---------------------------------------------------------------- MMA issuer
+    // The whole warp runs the loop, so that descriptors and addresses are warp-uniform;
+    // one elected lane issues the MMAs and the commits.
     uint32_t ca = 0;
     int j = 0;
     bool ok = true;
@@ -359,8 +375,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
       for (int g = blockIdx.x; g < st.n_groups && ok; g += gridDim.x, ++j) {
         const int xs = j % nxb, ds = j % nsets;
         const uint32_t xu = uint32_t(j / nxb), du = uint32_t(j / nsets);
-        if (!wait_bar(&xfull[xs], xu & 1u, abort) || !wait_bar(&dempty[ds], (du & 1u) ^ 1u, abort)) {
-          if (!*abort) {
+        const bool got = wait_bar(&xfull[xs], xu & 1u, abort) && wait_bar(&dempty[ds], (du & 1u) ^ 1u, abort);
+        if (!__all_sync(0xffffffffu, got)) {
+          if (lane == 0 && !*abort) {
             atomicCAS(a.status, 0, ST_FULL_TIMEOUT);
             *abort = 1;
           }
@@ -372,8 +389,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
         const uint32_t xb = xbase0 + uint32_t(xs) * x_buf;
         for (int kk = 0; kk < nk; ++kk, ++ca) {
           const uint32_t slot = ca % uint32_t(nsa), ph = (ca / uint32_t(nsa)) & 1u;
-          if (!wait_bar(&afull[slot], ph, abort)) {
-            if (!*abort) {
+          if (!__all_sync(0xffffffffu, wait_bar(&afull[slot], ph, abort))) {
+            if (lane == 0 && !*abort) {
               atomicCAS(a.status, 0, ST_FULL_TIMEOUT);
               *abort = 1;
             }
@@ -389,27 +406,34 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
           const uint64_t t0 = sdesc(as, 128u, 256u), t1 = sdesc(as + pb, 128u, 256u);
           const uint64_t t2 = sdesc(as + 2u * pb, 128u, 256u), t3 = sdesc(as + 3u * pb, 128u, 256u);
           const uint32_t acc0 = kk > 0 ? 1u : 0u;
-          if (stack) {          // t0 spans [Re hi; Im hi], t2 spans [Re lo; Im lo]
-            mma_bf16(d1, xh, t0, idesc, acc0);
-            mma_bf16(d1, xh, t2, idesc, 1u);
-            mma_bf16(d1, xl, t0, idesc, 1u);
-          } else {
-            mma_bf16(d1, xh, t0, idesc, acc0);
-            mma_bf16(d1, xh, t2, idesc, 1u);
-            mma_bf16(d1, xl, t0, idesc, 1u);
-            mma_bf16(d2, xh, t1, idesc, acc0);
-            mma_bf16(d2, xh, t3, idesc, 1u);
-            mma_bf16(d2, xl, t1, idesc, 1u);
+          if (elect_one()) {
+            if (stack) {          // t0 spans [Re hi; Im hi], t2 spans [Re lo; Im lo]
+              mma_bf16(d1, xh, t0, idesc, acc0);
+              mma_bf16(d1, xh, t2, idesc, 1u);
+              mma_bf16(d1, xl, t0, idesc, 1u);
+            } else {
+              mma_bf16(d1, xh, t0, idesc, acc0);
+              mma_bf16(d1, xh, t2, idesc, 1u);
+              mma_bf16(d1, xl, t0, idesc, 1u);
+              mma_bf16(d2, xh, t1, idesc, acc0);
+              mma_bf16(d2, xh, t3, idesc, 1u);
+              mma_bf16(d2, xl, t1, idesc, 1u);
+            }
+            mma_commit(&aempty[slot]);
           }
-          mma_commit(&aempty[slot]);
+          __syncwarp();
         }
         if (!ok) break;
-        mma_commit(&dfull[ds]);
-        mma_commit(&xempty[xs]);
+        if (elect_one()) {
+          mma_commit(&dfull[ds]);
+          mma_commit(&xempty[xs]);
+        }
+        __syncwarp();
       }
     }
-    // every MMA this thread issued has completed before TMEM is freed
-    mma_commit(done);
+    // every MMA this warp issued has completed before TMEM is freed
+    if (elect_one()) mma_commit(done);
+    __syncwarp();
     const uint64_t t1 = gtimer();
     while (!mbar_try(done, 0) && gtimer() - t1 < kTimeoutNs) {
     }
@@ -490,17 +514,48 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         mbar_arrive(&dempty[set]);
-        // count the written blocks in for the consumers of the next stage
-        if (!last) {
-          // the set's stores are ordered before the counting threads' fence by the
-          // barrier; the fence then makes them visible GPU-wide before the counts
-          named_sync(bar_id, 128);
-          if (et < c) {
-            __threadfence();
-            const int64_t P = pat_blk(st.out_pat, g, et, st, c);
-            atomicAdd(cnt_out + pat_group(nst.in_pat, P, nst, c), 1u);
+        // hand the written blocks to the signal warp (which counts them in for the next
+        // stage off this set's path); first make sure it took the set's previous group,
+        // so that the two never get a full phase apart
+        if (du > 0 && !wait_bar(&signaled[set], (du - 1) & 1u, abort)) {
+          if (!*abort) {
+            atomicCAS(a.status, 0, ST_FULL_TIMEOUT);
+            *abort = 1;
           }
+        } else {
+          mbar_arrive(&stored[set]);   // release: the set's stores before the signal warp's fence
         }
+      }
+    }
+  } else if (warp == 12) {
+    // ---------------------------------------------------------------- signal warp
+    // For each group in order: wait until its epilogue set has stored the output
+    // blocks, make them visible GPU-wide (fence) and count them in for the consumers.
+    int j = 0;
+    bool ok = true;
+    for (int e = 0; e < S && ok; ++e) {
+      const TCStage& st = plan.st[e];
+      const bool last = st.last != 0;
+      const TCStage& nst = plan.st[e + 1 < S ? e + 1 : e];
+      unsigned* cnt_out = a.counters + int64_t(e + 1) * nst.n_groups;
+      for (int g = blockIdx.x; g < st.n_groups && ok; g += gridDim.x, ++j) {
+        const int set = j % nsets;
+        const uint32_t du = uint32_t(j / nsets);
+        if (!__all_sync(0xffffffffu, wait_bar(&stored[set], du & 1u, abort))) {
+          if (lane == 0 && !*abort) {
+            atomicCAS(a.status, 0, ST_FULL_TIMEOUT);
+            *abort = 1;
+          }
+          ok = false;
+          break;
+        }
+        if (!last && lane < c) {
+          __threadfence();
+          const int64_t P = pat_blk(st.out_pat, g, lane, st, c);
+          atomicAdd(cnt_out + pat_group(nst.in_pat, P, nst, c), 1u);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&signaled[set]);
       }
     }
   }
@@ -780,7 +835,7 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_u_kernel(const __grid_const
 
 size_t tc_smem_bytes(int nsa, int nxb, int nsets, int mt_max, int kpad_max) {
   return size_t(nsa) * 4 * size_t(mt_max) * 32 + size_t(nxb) * 2 * size_t(kpad_max) * 256 +
-         size_t(nsets) * 2 * kTcChunk * 128 * sizeof(float) + (2 * size_t(nsa) + 16) * 8 + 64;
+         size_t(nsets) * 2 * kTcChunk * 128 * sizeof(float) + (2 * size_t(nsa) + 20) * 8 + 64;
 }
 
 size_t leaf_smem_bytes(int R, int c, bool u_side) {
