@@ -184,8 +184,11 @@ mbf_status mbf_apply(mbf_op_t op, const void* g, void* u, int64_t nrhs, int32_t 
 /* g = K_f^* u (adjoint): the same factors conjugate-transposed in reverse order. */
 mbf_status mbf_apply_adjoint(mbf_op_t op, const void* u, void* g, int64_t nrhs,
                              int32_t precision, void* stream);
-/* Same as mbf_apply but g and u are HOST buffers: copies in, applies, copies out,
- * and synchronizes `stream` before returning. */
+/* Same as mbf_apply but g and u are HOST buffers; synchronizes `stream` before
+ * returning.  Page-locked buffers the device can address (cudaHostAlloc,
+ * cudaHostRegister) are read and written by the tensor path's kernels across the host
+ * link directly; other buffers are copied in and out through device staging buffers
+ * (allocated on first use, kept by the operator). */
 mbf_status mbf_apply_host(mbf_op_t op, const void* g_host, void* u_host, int64_t nrhs,
                           int32_t precision, void* stream);
 /* Allocation-free forward apply.  The paper has no counterpart: this is a service

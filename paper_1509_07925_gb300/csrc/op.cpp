@@ -918,6 +918,20 @@ mbf_status mbf_apply_host(mbf_op_t op, const void* g_host, void* u_host, int64_t
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const size_t in_b = size_t(nrhs) * size_t(op->n_in) * sizeof(float2);
     const size_t out_b = size_t(nrhs) * size_t(op->n_out) * sizeof(float2);
+    // Page-locked host buffers that the device can address (the usual case for
+    // cudaHostAlloc / cudaHostRegister memory): the tensor path's permute kernel reads g
+    // and its U^L kernel writes u across the host link directly, each element once, so
+    // the transfers overlap the apply instead of preceding and following it.
+    if (uses_tensor(op, nrhs, precision, false)) {
+      cudaPointerAttributes ag{}, au{};
+      if (cudaPointerGetAttributes(&ag, g_host) == cudaSuccess && cudaPointerGetAttributes(&au, u_host) == cudaSuccess &&
+          ag.type == cudaMemoryTypeHost && au.type == cudaMemoryTypeHost && ag.devicePointer && au.devicePointer) {
+        apply_impl(op, ag.devicePointer, au.devicePointer, nrhs, precision, stream, false);
+        cuda_check(cudaStreamSynchronize(st), "sync");
+        return;
+      }
+      cudaGetLastError();   // clear a failed query (not page-locked): copy below
+    }
     if (in_b > op->stage_in_bytes) {
       cuda_check(cudaStreamSynchronize(st), "sync");
       cudaFree(op->d_stage_in);

@@ -88,3 +88,24 @@ def test_tensor_adjoint_is_rejected(ops, bd):
     # AUTO falls back to the FP32 path for the adjoint
     g = gpu_apply(torch, op, w, adjoint=True, precision=MBF_PREC_AUTO)
     assert rel(g, sb.adjoint(w)) <= 1e-5
+
+
+def test_host_buffers_on_tensor_path(ops, bd):
+    """mbf_apply_host with 70 RHS on the tensor path: page-locked host buffers (read and
+    written by the kernels across the host link) and pageable ones (staged copies) give
+    the oracle's result."""
+    import ctypes as C
+    op, fs, sb = ops(("fio_iso", 64, 2, 4, 24, "polar"))
+    g = complex_normal(fs.n_in, 70, seed=7)
+    ref = sb.apply(g)
+    st = torch.cuda.current_stream().cuda_stream
+    gp = torch.from_numpy(g.astype(np.complex64)).pin_memory()
+    up = torch.full((70, fs.n_out), float("nan"), dtype=torch.complex64).pin_memory()
+    bd._check(bd.lib().mbf_apply_host(op.handle, C.c_void_p(gp.data_ptr()), C.c_void_p(up.data_ptr()), 70,
+                                      MBF_PREC_BF16X3, C.c_void_p(st)))
+    u_pinned = up.numpy().astype(np.complex128)
+    u_paged = op.apply_host(g.astype(np.complex64), 70, MBF_PREC_BF16X3, st).astype(np.complex128)
+    for k in range(70):
+        assert rel(u_pinned[k], ref[k]) <= TOL_BF16X3, (k, rel(u_pinned[k], ref[k]))
+        assert rel(u_paged[k], ref[k]) <= TOL_BF16X3, (k, rel(u_paged[k], ref[k]))
+    assert np.array_equal(u_pinned, u_paged)
