@@ -42,7 +42,7 @@ def parse():
     p.add_argument("--impl", default="mbf", choices=["mbf", "reference"])
     p.add_argument("--workload", default="fio2_polar_n256_L6_r24")
     p.add_argument("--nrhs", type=int, default=0, help="override the workload's RHS count")
-    p.add_argument("--precision", default="auto", choices=["auto", "fp32_simt", "bf16x3"],
+    p.add_argument("--precision", default="auto", choices=["auto", "fp32_simt", "bf16x3", "tf32"],
                    help="auto: FP32 SIMT below 8 RHS, split-BF16x3 tensor cores from 8 RHS")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-serve", action="store_true", help="skip the served-mix experiment")
@@ -340,10 +340,15 @@ def main():
     nrhs = args.nrhs or 64
     if args.precision == "auto":
         args.precision = "bf16x3" if nrhs >= 8 else "fp32_simt"
-    prec = {"fp32_simt": bd.MBF_PREC_FP32_SIMT, "bf16x3": bd.MBF_PREC_BF16X3}[args.precision]
+    prec = {"fp32_simt": bd.MBF_PREC_FP32_SIMT, "bf16x3": bd.MBF_PREC_BF16X3,
+            "tf32": bd.MBF_PREC_TF32}[args.precision]
     legs = [("headline", nrhs, prec, args.precision)]
     if not (nrhs == 1 and args.precision == "fp32_simt"):
         legs.append(("simt_1rhs", 1, bd.MBF_PREC_FP32_SIMT, "fp32_simt"))
+    if nrhs >= 8 and args.precision == "bf16x3":
+        # the same panel with TF32 operands (precision sweep: about 1e-3 relative error
+        # against 1e-5 for split-BF16x3, measured by the full-size GPU test)
+        legs.append(("tf32", nrhs, bd.MBF_PREC_TF32, "tf32"))
     res = {}
     clocks = ClockSampler(local)
     clk = None
@@ -378,7 +383,7 @@ def main():
     # roofline of the dominant kernel of the headline leg
     head = res["headline"]
     R = head["nrhs"]
-    if head["precision"] == "bf16x3":
+    if head["precision"] in ("bf16x3", "tf32"):
         kname = "bf_apply_tc"
         nnz_tc = sum(info.nnz_stage[s] for s in range(1, info.n_stages)) - info.nnz_leaf_u
         nL = info.c ** info.L

@@ -54,6 +54,7 @@ typedef enum mbf_precision {
   MBF_PREC_AUTO = 0,     /* FP32 SIMT for nrhs < 8, split-BF16x3 tensor path otherwise */
   MBF_PREC_FP32_SIMT = 1,/* complex64 factors, FP32 FMA, FP32 accumulate               */
   MBF_PREC_TF32 = 2,     /* tensor cores, TF32-rounded operands, FP32 accumulate       */
+                         /* (forward only; about 1e-3 relative error; never AUTO)      */
   MBF_PREC_BF16X3 = 3    /* tensor cores, split-BF16 (hi*hi + hi*lo + lo*hi), FP32 acc  */
 } mbf_precision;
 

@@ -47,6 +47,9 @@ enum DeviceStatus : int {
 // A consumer copies each hi / lo half of a block into shared memory as it is.
 constexpr int kTcNR = 64;   // RHS per tensor-core panel
 MBF_HD int64_t split_block_bytes(int R8) { return int64_t(R8) * kTcNR * 8; }
+// With TF32 operands the same block holds FP32 (TF32-rounded) values instead, byte
+//   (k, ri, n) = (k / 4) 2048 + (8 ri + n / 8) 128 + (n % 8) 16 + (k % 4) 4
+// (the MMA's K-major A operand for 32-bit types): the same R8 x 512 bytes.
 
 struct TCArgs {
   const uint8_t* arena;
@@ -91,9 +94,12 @@ size_t tc_smem_bytes(int nsa, int nxb, int nsets, int mt_max, int kpad_max);
 size_t tc_counter_bytes(const TCPlan& plan);
 size_t leaf_smem_bytes(int R, int c, bool u_side);
 bool leaf_fits(int R8, int c);   // leaf kernels: R8 <= 64, c <= 8
-cudaError_t launch_apply_tc(const TCArgs& a, int grid, size_t smem, cudaStream_t stream);
+// tf32: TF32 tiles and vectors (kind::tf32 MMAs), else split-BF16x3.
+cudaError_t launch_apply_tc(const TCArgs& a, int grid, size_t smem, cudaStream_t stream, bool tf32);
+// TF32 tiles (two FP32 planes per K16 chunk) converted from n_chunks split-BF16 chunks of M_t rows.
+cudaError_t launch_tf32_tiles(const uint8_t* src, uint8_t* dst, int64_t n_chunks, int M_t, cudaStream_t stream);
 // One CTA per group of c leaves.
-cudaError_t launch_leaf(const LeafArgs& a, bool u_side, int n_groups, cudaStream_t stream);
+cudaError_t launch_leaf(const LeafArgs& a, bool u_side, int n_groups, cudaStream_t stream, bool tf32 = false);
 // vec = g [nrhs][len_vec], perm = inverse tree permutation (natural -> tree, -1 if absent),
 // outp = panel in tree order [tree point][64]
 cudaError_t launch_permute_in(const LeafArgs& a, cudaStream_t stream);

@@ -108,6 +108,21 @@ __device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t ad, uint64_t bd, u
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
       "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
 }
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+// FP32 -> TF32 (round to nearest, ties away from zero), kept in an FP32 container.
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+__device__ __forceinline__ uint4 tf32x4(const float* y) {
+  return make_uint4(__float_as_uint(to_tf32(y[0])), __float_as_uint(to_tf32(y[1])), __float_as_uint(to_tf32(y[2])),
+                    __float_as_uint(to_tf32(y[3])));
+}
 __device__ __forceinline__ void mma_commit(uint64_t* b) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(sa(b)) : "memory");
 }
@@ -198,6 +213,9 @@ __device__ __forceinline__ bool wait_bar(uint64_t* b, uint32_t ph, volatile int*
 constexpr int kTcThreads = 416;   // 13 warps (roles above)
 constexpr int kTcChunk = 16;   // accumulator columns per epilogue step
 
+// TF32: the vectors between stages are TF32 blocks (apply.hpp) and the tiles two FP32
+// planes (Re, Im) per K16 chunk; kind::tf32 MMAs of K = 8.  Otherwise split-BF16x3.
+template <bool TF32>
 __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_constant__ TCArgs a) {
   using namespace tc;
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -300,10 +318,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
       const TCStage& st = plan.st[e];
       const uint8_t* src = e == 0 ? a.x_in : a.bufs + int64_t(e - 1) * a.buf_stride;
       const unsigned* cnt_in = a.counters + int64_t(e) * st.n_groups;
-      const uint32_t half = uint32_t(st.R8_in) * 256u;      // hi or lo half of one block
+      // split-BF16: hi and lo halves of each block go to the two halves of the panel
+      // buffer; TF32: each block is one run
+      const uint32_t half = TF32 ? uint32_t(st.R8_in) * 512u : uint32_t(st.R8_in) * 256u;
       const uint32_t xhalf = uint32_t(st.K_pad) * 256u;     // hi or lo half of the panel buffer
       const int64_t blk = split_block_bytes(st.R8_in);
-      const int pieces = int(half >> 4);                      // 16-byte pieces of one half
+      const int pieces = int(half >> 4);                      // 16-byte pieces of one part
+      constexpr int kParts = TF32 ? 1 : 2;
       for (int g = blockIdx.x; g < st.n_groups && ok; g += gridDim.x, ++j) {
         const int xs = j % nxb;
         const uint32_t xu = uint32_t(j / nxb);
@@ -337,7 +358,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
         for (int t = 0; t < c; ++t) {
           const uint8_t* sb = src + int64_t(pat_blk(st.in_pat, g, t, st, c)) * blk;
 #pragma unroll 4
-          for (int q = xt; q < 2 * pieces; q += 64) {
+          for (int q = xt; q < kParts * pieces; q += 64) {
             const int hl = q >= pieces, pq = q - hl * pieces;
             cp_async16(xb + uint32_t(hl) * xhalf + uint32_t(t) * half + uint32_t(pq) * 16u,
                        sb + int64_t(hl) * half + int64_t(pq) * 16);
@@ -369,9 +390,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
       // kind::f16, FP32 accumulate, BF16 A and B, both K-major, M = 128.  While 2 M_t <= 256
       // the Re and Im planes of the tile form one B operand of N = 2 M_t rows (three MMAs
       // per K16 fill D1 | D2 at once); wider tiles take N = M_t, one MMA per plane.
+      // (TF32: kind::tf32, A and B TF32, K = 8 per MMA; planes Re, Im of M_t x 16 FP32)
       const bool stack = 2 * st.M_t <= 256;
       const uint32_t nmma = uint32_t(stack ? 2 * st.M_t : st.M_t);
-      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((nmma >> 3) << 17) | (uint32_t(128 >> 4) << 24);
+      const uint32_t ab = TF32 ? 2u : 1u;   // operand format: BF16 = 1, TF32 = 2
+      const uint32_t idesc = (1u << 4) | (ab << 7) | (ab << 10) | ((nmma >> 3) << 17) | (uint32_t(128 >> 4) << 24);
+      const uint32_t pbt = uint32_t(st.M_t) * 64u;   // TF32: one K16 chunk of one plane
       for (int g = blockIdx.x; g < st.n_groups && ok; g += gridDim.x, ++j) {
         const int xs = j % nxb, ds = j % nsets;
         const uint32_t xu = uint32_t(j / nxb), du = uint32_t(j / nsets);
@@ -399,6 +423,27 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
           }
           // (the chunk was written by the bulk copy the mbarrier tracks: no tcgen05 fence)
           const uint32_t as = abase + slot * a_slot;
+          if constexpr (TF32) {
+            // A: K-major, 4 K (16 bytes) per core matrix: next 4 K at +2048, next 8 rows at
+            // +128; chunk kk at +8192, its second K = 8 at +4096.  B: planes 0 Re, 1 Im,
+            // next 4 K at +128, next 8 rows at +512; second K = 8 at +256.
+            const uint64_t x0 = sdesc(xb + uint32_t(kk) * 8192u, 2048u, 128u);
+            const uint64_t x1 = sdesc(xb + uint32_t(kk) * 8192u + 4096u, 2048u, 128u);
+            const uint64_t r0 = sdesc(as, 128u, 512u), r1 = sdesc(as + 256u, 128u, 512u);
+            const uint64_t i0 = sdesc(as + pbt, 128u, 512u), i1 = sdesc(as + pbt + 256u, 128u, 512u);
+            const uint32_t acc0 = kk > 0 ? 1u : 0u;
+            if (elect_one()) {
+              mma_tf32(d1, x0, r0, idesc, acc0);   // stacked: r0 spans [Re; Im]
+              mma_tf32(d1, x1, r1, idesc, 1u);
+              if (!stack) {
+                mma_tf32(d2, x0, i0, idesc, acc0);
+                mma_tf32(d2, x1, i1, idesc, 1u);
+              }
+              mma_commit(&aempty[slot]);
+            }
+            __syncwarp();
+            continue;
+          }
           // A: panel half (hi / lo), K-major, next 8 K at +2048, next 8 rows at +128
           const uint64_t xh = sdesc(xb + uint32_t(kk) * 4096u, 2048u, 128u);
           const uint64_t xl = sdesc(xb + xhalf + uint32_t(kk) * 4096u, 2048u, 128u);
@@ -503,6 +548,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
 #pragma unroll
               for (int i = 0; i < 8; ++i)
                 if (k2 + i < st.R_out) o[i * 2 * kTcNR] = y[8 * r8 + i];
+            } else if (TF32) {   // two runs of 4 rows: byte (k / 4) 2048 + (8 h + n / 8) 128 + (n % 8) 16
+              uint8_t* o = dst + P * blk + (k2 >> 2) * 2048 + (8 * h + (n >> 3)) * 128 + (n & 7) * 16;
+              *reinterpret_cast<uint4*>(o) = tf32x4(y + 8 * r8);
+              *reinterpret_cast<uint4*>(o + 2048) = tf32x4(y + 8 * r8 + 4);
             } else {
               uint4 hi, lo;
               split8(y + 8 * r8, hi, lo);
@@ -643,7 +692,23 @@ __global__ void __launch_bounds__(kLeafThreads) permute_in_kernel(const __grid_c
 
 // Rows k0 .. k0 + 7 of column n of split block `leaf` from 8 accumulators: byte
 // (hl, k, ri, n) as in apply.hpp, so 8 consecutive k are one 16-byte run per plane.
+template <bool TF32>
 __device__ __forceinline__ void store_split8(uint8_t* outs, int64_t leaf, int R8, int n, int k0, float2 (&acc)[8]) {
+  if constexpr (TF32) {   // TF32 block: byte (k / 4) 2048 + (8 ri + n / 8) 128 + (n % 8) 16 + (k % 4) 4
+    float re[8], im[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      re[j] = acc[j].x;
+      im[j] = acc[j].y;
+      acc[j] = make_float2(0.f, 0.f);
+    }
+    uint8_t* o = outs + leaf * split_block_bytes(R8) + (k0 >> 2) * 2048 + (n >> 3) * 128 + (n & 7) * 16;
+    *reinterpret_cast<uint4*>(o) = tc::tf32x4(re);
+    *reinterpret_cast<uint4*>(o + 2048) = tc::tf32x4(re + 4);
+    *reinterpret_cast<uint4*>(o + 1024) = tc::tf32x4(im);
+    *reinterpret_cast<uint4*>(o + 2048 + 1024) = tc::tf32x4(im + 4);
+    return;
+  }
   float re[8], im[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
@@ -684,6 +749,7 @@ __device__ __forceinline__ void leaf_v_point(float2 (&acc)[8], const float2* vro
   }
 }
 
+template <bool TF32>
 __global__ void __launch_bounds__(kTcNR * kLeafMaxR8 / 8) leaf_v_kernel(const __grid_constant__ LeafArgs a) {
   constexpr int NR = kTcNR;
   extern __shared__ __align__(16) float2 lsm[];
@@ -729,11 +795,11 @@ __global__ void __launch_bounds__(kTcNR * kLeafMaxR8 / 8) leaf_v_kernel(const __
       }
       for (; b < bend; ++b) leaf_v_point(acc, vs + b * R8 + k0, __ldcg(xg + int64_t(b0 + b) * NR));
       if (le > nb) break;                            // leaf t continues in the next round
-      store_split8(a.outs, int64_t(c) * g + t, R8, n, k0, acc);
+      store_split8<TF32>(a.outs, int64_t(c) * g + t, R8, n, k0, acc);
       ++t;
     }
   }
-  for (; t < c; ++t) store_split8(a.outs, int64_t(c) * g + t, R8, n, k0, acc);
+  for (; t < c; ++t) store_split8<TF32>(a.outs, int64_t(c) * g + t, R8, n, k0, acc);
 }
 
 // U^L for a panel, one CTA per group g (leaves i = c g + t):
@@ -846,10 +912,11 @@ size_t leaf_smem_bytes(int R, int c, bool u_side) {
 
 bool leaf_fits(int R8, int c) { return R8 <= kLeafMaxR8 && c <= kLeafMaxC; }
 
-cudaError_t launch_apply_tc(const TCArgs& a, int grid, size_t smem, cudaStream_t stream) {
+cudaError_t launch_apply_tc(const TCArgs& a, int grid, size_t smem, cudaStream_t stream, bool tf32) {
   cudaError_t err = cudaMemsetAsync(a.counters, 0, tc_counter_bytes(a.plan), stream);
   if (err != cudaSuccess) return err;
-  if ((err = cudaFuncSetAttribute(bf_apply_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem))) != cudaSuccess)
+  void (*kern)(TCArgs) = tf32 ? bf_apply_tc<true> : bf_apply_tc<false>;
+  if ((err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem))) != cudaSuccess)
     return err;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(unsigned(grid));
@@ -861,7 +928,37 @@ cudaError_t launch_apply_tc(const TCArgs& a, int grid, size_t smem, cudaStream_t
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, bf_apply_tc, a);
+  return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+// TF32 tiles from the split-BF16 tiles: T = hi + lo (FP32), rounded to TF32, in the
+// TF32 chunk layout (planes Re, Im; byte ((m / 8) 4 + k / 4) 128 + (m % 8) 16 + (k % 4) 4).
+// One CTA per K16 chunk of a tile, one thread per entry of the chunk's M_t x 16 block.
+__global__ void __launch_bounds__(256) tf32_tiles_kernel(const uint8_t* __restrict__ src, uint8_t* __restrict__ dst,
+                                                        int64_t n_chunks, int M_t) {
+  const int64_t chunk = blockIdx.x;
+  if (chunk >= n_chunks) return;
+  const int64_t cb = int64_t(M_t) * 128;   // bytes of one chunk (both layouts)
+  const uint32_t pb = uint32_t(M_t) * 32, pbt = uint32_t(M_t) * 64;
+  const uint8_t* s0 = src + chunk * cb;
+  uint8_t* d0 = dst + chunk * cb;
+  for (int q = threadIdx.x; q < M_t * 16; q += blockDim.x) {
+    const int m = q >> 4, k = q & 15;
+    const uint32_t sb = uint32_t(((m >> 3) * 2 + (k >> 3)) * 128 + (m & 7) * 16 + (k & 7) * 2);
+    const auto bf = [&](uint32_t off) {
+      return __uint_as_float(uint32_t(*reinterpret_cast<const uint16_t*>(s0 + off)) << 16);
+    };
+    const float re = bf(sb) + bf(2 * pb + sb), im = bf(pb + sb) + bf(3 * pb + sb);   // hi + lo
+    const uint32_t db = uint32_t(((m >> 3) * 4 + (k >> 2)) * 128 + (m & 7) * 16 + (k & 3) * 4);
+    *reinterpret_cast<float*>(d0 + db) = tc::to_tf32(re);
+    *reinterpret_cast<float*>(d0 + pbt + db) = tc::to_tf32(im);
+  }
+}
+
+cudaError_t launch_tf32_tiles(const uint8_t* src, uint8_t* dst, int64_t n_chunks, int M_t, cudaStream_t stream) {
+  if (n_chunks <= 0) return cudaSuccess;
+  tf32_tiles_kernel<<<unsigned(n_chunks), 256, 0, stream>>>(src, dst, n_chunks, M_t);
+  return cudaGetLastError();
 }
 
 size_t tc_counter_bytes(const TCPlan& plan) {
@@ -878,9 +975,9 @@ cudaError_t launch_permute_in(const LeafArgs& a, cudaStream_t stream) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_leaf(const LeafArgs& a, bool u_side, int n_groups, cudaStream_t stream) {
+cudaError_t launch_leaf(const LeafArgs& a, bool u_side, int n_groups, cudaStream_t stream, bool tf32) {
   const size_t smem = leaf_smem_bytes(a.R, a.c, u_side);
-  void (*kern)(LeafArgs) = u_side ? leaf_u_kernel : leaf_v_kernel;
+  void (*kern)(LeafArgs) = u_side ? leaf_u_kernel : (tf32 ? leaf_v_kernel<true> : leaf_v_kernel<false>);
   // (V^L)^*: one thread per RHS column and group of 8 rows
   const int threads = u_side ? kLeafThreads : kTcNR * (a.R8 / 8);
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));

@@ -467,6 +467,7 @@ void op_free(mbf_op_s* op) {
   cudaFree(op->d_stage_in);
   cudaFree(op->d_stage_out);
   cudaFree(op->d_tc_arena);
+  cudaFree(op->d_tc_arena_tf32);
   cudaFree(op->d_tc_bufs);
   for (auto& r : op->prof_pending) {
     cudaEventDestroy(r.e0);
@@ -600,12 +601,25 @@ void prof_collect(mbf_op_s* op) {
 // Tensor-core apply, per panel of 64 RHS: permute the panel into Omega-tree order, the
 // (V^L)^* leaf kernel, the persistent tcgen05 kernel over the G / H levels, the U^L leaf
 // kernel (which scatters u to natural order).
-void apply_tc(mbf_op_s* op, const float2* g, float2* u, int64_t nrhs, cudaStream_t st, int grid, bool accumulate) {
+void apply_tc(mbf_op_s* op, const float2* g, float2* u, int64_t nrhs, cudaStream_t st, int grid, bool accumulate,
+              bool tf32) {
   if (!op->tc_unavailable.empty()) fail(MBF_ERR_INVALID, "tensor path unavailable: " + op->tc_unavailable);
   const TCPlan& tp = op->tcplan;
   const int S = tp.n_stages;
   const int64_t vec_bytes = tc_vec_bytes(op);
   tc_prepare(op);
+  if (tf32 && !op->d_tc_arena_tf32) {   // first TF32 apply: convert the tiles (kept, like the split ones)
+    if (cudaMalloc(&op->d_tc_arena_tf32, size_t(op->tc_bytes)) != cudaSuccess) {
+      op->d_tc_arena_tf32 = nullptr;
+      fail(MBF_ERR_OOM, "cudaMalloc TF32 tiles");
+    }
+    for (int e = 0; e < S; ++e) {
+      const TCStage& ts = tp.st[e];
+      cuda_check(launch_tf32_tiles(op->d_tc_arena + ts.base, op->d_tc_arena_tf32 + ts.base,
+                                   int64_t(ts.n_groups) * (ts.K_pad / 16), ts.M_t, st),
+                 "TF32 tile conversion");
+    }
+  }
   int sms = op->sms;
   if (grid > 0) sms = std::min(sms, grid);
   const Stage& leaf_st = op->plan.st[0];
@@ -638,11 +652,11 @@ void apply_tc(mbf_op_s* op, const float2* g, float2* u, int64_t nrhs, cudaStream
     la.R = op->RV[size_t(op->L)];
     la.R8 = tp.st[0].R8_in;
     e0 = prof_begin(op, st);
-    cuda_check(launch_leaf(la, false, leaf_st.n_groups, st), "leaf (V^L)^* launch");
+    cuda_check(launch_leaf(la, false, leaf_st.n_groups, st, tf32), "leaf (V^L)^* launch");
     prof_end(op, PK_LEAF_V, e0, st);
     // G / H levels on tensor cores
     TCArgs ta{};
-    ta.arena = op->d_tc_arena;
+    ta.arena = tf32 ? op->d_tc_arena_tf32 : op->d_tc_arena;
     ta.x_in = yl;
     ta.bufs = bufs;
     ta.y_out = ylast;
@@ -656,7 +670,7 @@ void apply_tc(mbf_op_s* op, const float2* g, float2* u, int64_t nrhs, cudaStream
     ta.kpad_max = op->tc_kpad_max;
     ta.plan = tp;
     e0 = prof_begin(op, st);
-    cuda_check(launch_apply_tc(ta, sms, op->tc_smem, st), "tensor-core launch");
+    cuda_check(launch_apply_tc(ta, sms, op->tc_smem, st, tf32), "tensor-core launch");
     prof_end(op, PK_TC, e0, st);
     // U^L: last main stage output -> u
     LeafArgs lu{};
@@ -686,13 +700,15 @@ void apply_impl(mbf_op_s* op, const void* in, void* out, int64_t nrhs, int32_t p
   if (nrhs < 0) fail(MBF_ERR_INVALID, "nrhs < 0");
   if (nrhs == 0) return;
   if ((!in || !out)) fail(MBF_ERR_INVALID, "NULL vector");
-  if (precision != MBF_PREC_AUTO && precision != MBF_PREC_FP32_SIMT && precision != MBF_PREC_BF16X3)
+  if (precision != MBF_PREC_AUTO && precision != MBF_PREC_FP32_SIMT && precision != MBF_PREC_BF16X3 &&
+      precision != MBF_PREC_TF32)
     fail(MBF_ERR_INVALID, "precision not available");
   if (nrhs > (int64_t(1) << 24)) fail(MBF_ERR_INVALID, "nrhs too large");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (uses_tensor(op, nrhs, precision, adj)) {
     if (adj) fail(MBF_ERR_INVALID, "the tensor-core path applies the forward operator only");
-    apply_tc(op, static_cast<const float2*>(in), static_cast<float2*>(out), nrhs, st, grid, accumulate);
+    apply_tc(op, static_cast<const float2*>(in), static_cast<float2*>(out), nrhs, st, grid, accumulate,
+             precision == MBF_PREC_TF32);
     return;
   }
   const int nrb = nrhs >= 4 ? 4 : (nrhs >= 2 ? 2 : 1);
@@ -747,10 +763,10 @@ mbf_status guard(F&& fn) {
 
 void set_last_error(const std::string& m) { g_last_error = m; }
 
-// Which path an apply takes: split-BF16x3 on request; AUTO uses the tensor cores for
+// Which path an apply takes: split-BF16x3 or TF32 on request; AUTO uses the tensor cores for
 // forward applies from tc_min_rhs right-hand sides (8, or what the tuner measured).
 bool uses_tensor(const mbf_op_s* op, int64_t nrhs, int32_t precision, bool adj) {
-  return precision == MBF_PREC_BF16X3 ||
+  return precision == MBF_PREC_BF16X3 || precision == MBF_PREC_TF32 ||
          (precision == MBF_PREC_AUTO && nrhs >= op->tc_min_rhs && !adj && op->tc_unavailable.empty());
 }
 

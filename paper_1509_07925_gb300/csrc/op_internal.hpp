@@ -33,6 +33,7 @@ struct mbf_op_s {
   // panel workspace (allocated on first use)
   mbf::TCPlan tcplan{};
   uint8_t* d_tc_arena = nullptr;
+  uint8_t* d_tc_arena_tf32 = nullptr; // the same tiles as TF32 planes (converted on first TF32 apply)
   int64_t tc_bytes = 0;
   int tc_mt_max = 16, tc_kpad_max = 16, tc_nsa = 2, tc_nxb = 2, tc_nsets = 2;
   size_t tc_smem = 0;

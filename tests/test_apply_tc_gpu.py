@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 from mbf_synth import complex_normal
-from paper_1509_07925_gb300.binding import MBF_PREC_AUTO, MBF_PREC_BF16X3, MBF_PREC_FP32_SIMT
+from paper_1509_07925_gb300.binding import MBF_PREC_AUTO, MBF_PREC_BF16X3, MBF_PREC_FP32_SIMT, MBF_PREC_TF32
 
 from gpu_util import gpu_apply, import_factors, oracle_case, rel
 
@@ -15,6 +15,9 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL_BF16X3 = 1e-4
+# TF32 operands (10-bit mantissa, unit roundoff 2^-11) through 2 (L - h) levels: about
+# 1e-3 relative; the gate is a bound on that, not the 1e-4 of the split-BF16x3 path.
+TOL_TF32 = 5e-3
 
 CASES = [
     ("dft", 16, 2, 2, 8, "none"),         # L = 2: one H and one G stage, 32 x 32 tiles
@@ -109,3 +112,19 @@ def test_host_buffers_on_tensor_path(ops, bd):
         assert rel(u_pinned[k], ref[k]) <= TOL_BF16X3, (k, rel(u_pinned[k], ref[k]))
         assert rel(u_paged[k], ref[k]) <= TOL_BF16X3, (k, rel(u_paged[k], ref[k]))
     assert np.array_equal(u_pinned, u_paged)
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_tf32_forward_matches_oracle_within_tf32_error(ops, case):
+    """The TF32 tensor path (tiles converted from the split ones on first use, kind::tf32
+    MMAs) against the oracle; its error is larger than the split-BF16x3 path's."""
+    op, fs, sb = ops(case)
+    g = complex_normal(fs.n_in, 64, seed=23)
+    ref = sb.apply(g)
+    u32 = gpu_apply(torch, op, g, precision=MBF_PREC_TF32)
+    u3 = gpu_apply(torch, op, g, precision=MBF_PREC_BF16X3)
+    assert np.all(np.isfinite(u32))
+    e32 = max(rel(u32[k], ref[k]) for k in range(64))
+    e3 = max(rel(u3[k], ref[k]) for k in range(64))
+    assert e32 <= TOL_TF32, (case, e32)
+    assert e3 <= TOL_BF16X3 and e3 < e32, (case, e3, e32)

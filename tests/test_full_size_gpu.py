@@ -14,7 +14,7 @@ from mbf_synth import WORKLOADS, complex_normal, sample_outputs
 from oracle import bf as B
 from oracle import direct as D
 from oracle import problem as P
-from paper_1509_07925_gb300.binding import MBF_PREC_BF16X3, MBF_PREC_FP32_SIMT
+from paper_1509_07925_gb300.binding import MBF_PREC_BF16X3, MBF_PREC_FP32_SIMT, MBF_PREC_TF32
 
 from gpu_util import export_factors, gpu_apply, rel
 
@@ -63,3 +63,18 @@ def test_full_size_tensor_64_rhs(full):
     assert np.all(np.isfinite(u))
     errs = [rel(u[k], uf[k]) for k in range(64)]
     assert max(errs) <= 1e-4, max(errs)
+
+
+def test_full_size_precision_sweep_64_rhs(full):
+    """FP32 SIMT, TF32 and split-BF16x3 on the same 64 RHS against the FP64 factor apply:
+    each within its own bound, and in the order of their operand precision."""
+    op, fs, sb = full
+    g = complex_normal(fs.n_in, 64, seed=WL.seed_g + 2)
+    uf = sb.apply(g)
+    err = {}
+    for name, prec in (("fp32_simt", MBF_PREC_FP32_SIMT), ("tf32", MBF_PREC_TF32), ("bf16x3", MBF_PREC_BF16X3)):
+        u = gpu_apply(torch, op, g, precision=prec)
+        err[name] = max(rel(u[k], uf[k]) for k in range(64))
+    print("precision sweep, max rel err over 64 RHS:", err)
+    assert err["fp32_simt"] <= 1e-5 and err["bf16x3"] <= 1e-4 and err["tf32"] <= 5e-3, err
+    assert err["fp32_simt"] < err["bf16x3"] < err["tf32"], err
