@@ -203,24 +203,26 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def timed_applies(torch, op, g, u, nrhs, prec, steps, stream):
+def timed_applies(torch, op, g, u, nrhs, prec, steps, stream, adjoint=False):
     """Device time per apply over `steps` back-to-back applies (CUDA events on the stream)."""
     sp = stream.cuda_stream
+    fn = op.apply_adjoint if adjoint else op.apply
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(steps):
-        op.apply(g.data_ptr(), u.data_ptr(), nrhs, prec, sp)
+        fn(g.data_ptr(), u.data_ptr(), nrhs, prec, sp)
     ev1.record(stream)
     torch.cuda.synchronize()
     return ev0.elapsed_time(ev1) / steps
 
 
-def kernel_times(torch, op, g, u, nrhs, prec, steps, stream):
+def kernel_times(torch, op, g, u, nrhs, prec, steps, stream, adjoint=False):
     """Per-kernel device time per apply: a second pass with the library's kernel timing
     on (CUDA events around each launch, on the apply's stream)."""
+    fn = op.apply_adjoint if adjoint else op.apply
     op.set_profiling(True)
     for _ in range(steps):
-        op.apply(g.data_ptr(), u.data_ptr(), nrhs, prec, stream.cuda_stream)
+        fn(g.data_ptr(), u.data_ptr(), nrhs, prec, stream.cuda_stream)
     torch.cuda.synchronize()
     prof = op.profile()
     op.set_profiling(False)
@@ -349,14 +351,18 @@ def main():
         # the same panel with TF32 operands (precision sweep: about 1e-3 relative error
         # against 1e-5 for split-BF16x3, measured by the full-size GPU test)
         legs.append(("tf32", nrhs, bd.MBF_PREC_TF32, "tf32"))
+        # the adjoint K^* u of the same panel on the tensor cores
+        legs.append(("adjoint", nrhs, bd.MBF_PREC_BF16X3, "bf16x3"))
     res = {}
     clocks = ClockSampler(local)
     clk = None
     for name, R, pr, prname in legs:
+        adj = name == "adjoint"
+        apply_fn = op.apply_adjoint if adj else op.apply
         g = torch.from_numpy(complex_normal(N, R, seed=wl.seed_g).astype(np.complex64)).cuda()
         u = torch.empty((R, N), dtype=torch.complex64, device="cuda")
         for _ in range(max(3, args.warmup)):
-            op.apply(g.data_ptr(), u.data_ptr(), R, pr, sp)
+            apply_fn(g.data_ptr(), u.data_ptr(), R, pr, sp)
         op.check(sp)
         torch.cuda.synchronize()
         if name == "headline":
@@ -365,7 +371,7 @@ def main():
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
-        ms = timed_applies(torch, op, g, u, R, pr, args.steps, stream)
+        ms = timed_applies(torch, op, g, u, R, pr, args.steps, stream, adjoint=adj)
         if world > 1:
             torch.distributed.barrier()
             t = torch.tensor([ms], device="cuda")
@@ -374,7 +380,7 @@ def main():
         if name == "headline":
             clk = clocks.stop()
         op.check(sp)
-        kt = kernel_times(torch, op, g, u, R, pr, args.steps, stream)
+        kt = kernel_times(torch, op, g, u, R, pr, args.steps, stream, adjoint=adj)
         op.check(sp)
         res[name] = {"nrhs": R, "precision": prname, "ms": ms, "value": world * N * R / (ms * 1e-3),
                      "kernels": kt}

@@ -182,7 +182,10 @@ mbf_status mbf_op_info(mbf_op_t op, mbf_op_info_t* info);
  * out of time sets the operator's status word; mbf_op_check() reports it. */
 mbf_status mbf_apply(mbf_op_t op, const void* g, void* u, int64_t nrhs, int32_t precision,
                      void* stream);
-/* g = K_f^* u (adjoint): the same factors conjugate-transposed in reverse order. */
+/* g = K_f^* u (adjoint): the same factors conjugate-transposed in reverse order.  On
+ * the tensor cores (MBF_PREC_BF16X3, or AUTO from the tensor crossover) the tiles are
+ * conjugate-transposed on the device on the first such call and kept (as much device
+ * memory again as the forward tiles); MBF_PREC_TF32 is rejected for the adjoint. */
 mbf_status mbf_apply_adjoint(mbf_op_t op, const void* u, void* g, int64_t nrhs,
                              int32_t precision, void* stream);
 /* Same as mbf_apply but g and u are HOST buffers; synchronizes `stream` before
@@ -249,7 +252,8 @@ mbf_status mbf_op_profile(mbf_op_t op, mbf_profile_t* out);
  *                      take_ownership the parts are destroyed with it.
  *   mbf_msbf_apply     u = K_C g_C + sum_t BF_t g, device [nrhs][n] buffers, stream-ordered:
  *                      the centre product writes u, each part adds into it.
- *   mbf_msbf_apply_adjoint  g = K^* u (FP32 SIMT parts; MBF_PREC_BF16X3 is rejected). */
+ *   mbf_msbf_apply_adjoint  g = K^* u (FP32 SIMT or split-BF16x3 tensor-core parts;
+ *                           MBF_PREC_TF32 is rejected). */
 typedef struct mbf_msbf_info {
   int32_t n_parts;
   int32_t part_t[16], part_L[16];

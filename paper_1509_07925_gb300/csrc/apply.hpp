@@ -99,7 +99,11 @@ cudaError_t launch_apply_tc(const TCArgs& a, int grid, size_t smem, cudaStream_t
 // TF32 tiles (two FP32 planes per K16 chunk) converted from n_chunks split-BF16 chunks of M_t rows.
 cudaError_t launch_tf32_tiles(const uint8_t* src, uint8_t* dst, int64_t n_chunks, int M_t, cudaStream_t stream);
 // One CTA per group of c leaves.
-cudaError_t launch_leaf(const LeafArgs& a, bool u_side, int n_groups, cudaStream_t stream, bool tf32 = false);
+// xpose: the adjoint's leaf products (U^* from the U^L items, V from the (V^L)^* items).
+cudaError_t launch_leaf(const LeafArgs& a, bool u_side, int n_groups, cudaStream_t stream, bool tf32 = false,
+                        bool xpose = false);
+// Adjoint (conjugate-transposed) split-BF16 tiles of one stage from its forward tiles.
+cudaError_t launch_adjoint_tiles(const uint8_t* src, uint8_t* dst, int n_groups, int M_t, int K_t, cudaStream_t stream);
 // vec = g [nrhs][len_vec], perm = inverse tree permutation (natural -> tree, -1 if absent),
 // outp = panel in tree order [tree point][64]
 cudaError_t launch_permute_in(const LeafArgs& a, cudaStream_t stream);

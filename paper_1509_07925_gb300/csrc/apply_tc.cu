@@ -499,8 +499,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
       const TCStage& st = plan.st[e];
       const bool last = st.last != 0;
       uint8_t* dst = a.bufs + int64_t(e) * a.buf_stride;
-      const TCStage& nst = plan.st[e + 1 < S ? e + 1 : e];
-      unsigned* cnt_out = a.counters + int64_t(e + 1) * nst.n_groups;
       const int64_t blk = split_block_bytes(st.R8_out);
       const uint32_t half = uint32_t(st.R8_out) * 256u;
       for (int g = blockIdx.x; g < st.n_groups && ok; g += gridDim.x, ++j) {
@@ -694,21 +692,6 @@ __global__ void __launch_bounds__(kLeafThreads) permute_in_kernel(const __grid_c
 // (hl, k, ri, n) as in apply.hpp, so 8 consecutive k are one 16-byte run per plane.
 template <bool TF32>
 __device__ __forceinline__ void store_split8(uint8_t* outs, int64_t leaf, int R8, int n, int k0, float2 (&acc)[8]) {
-  if constexpr (TF32) {   // TF32 block: byte (k / 4) 2048 + (8 ri + n / 8) 128 + (n % 8) 16 + (k % 4) 4
-    float re[8], im[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      re[j] = acc[j].x;
-      im[j] = acc[j].y;
-      acc[j] = make_float2(0.f, 0.f);
-    }
-    uint8_t* o = outs + leaf * split_block_bytes(R8) + (k0 >> 2) * 2048 + (n >> 3) * 128 + (n & 7) * 16;
-    *reinterpret_cast<uint4*>(o) = tc::tf32x4(re);
-    *reinterpret_cast<uint4*>(o + 2048) = tc::tf32x4(re + 4);
-    *reinterpret_cast<uint4*>(o + 1024) = tc::tf32x4(im);
-    *reinterpret_cast<uint4*>(o + 2048 + 1024) = tc::tf32x4(im + 4);
-    return;
-  }
   float re[8], im[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
@@ -716,15 +699,23 @@ __device__ __forceinline__ void store_split8(uint8_t* outs, int64_t leaf, int R8
     im[j] = acc[j].y;
     acc[j] = make_float2(0.f, 0.f);
   }
-  uint4 rh, rl, ih, il;
-  tc::split8(re, rh, rl);
-  tc::split8(im, ih, il);
-  uint8_t* o = outs + leaf * split_block_bytes(R8) + (k0 >> 3) * 2048 + (n >> 3) * 128 + (n & 7) * 16;
-  const int64_t half = int64_t(R8) * 256;
-  *reinterpret_cast<uint4*>(o) = rh;                 // Re hi
-  *reinterpret_cast<uint4*>(o + 1024) = ih;          // Im hi
-  *reinterpret_cast<uint4*>(o + half) = rl;          // Re lo
-  *reinterpret_cast<uint4*>(o + half + 1024) = il;   // Im lo
+  if constexpr (TF32) {   // TF32 block: byte (k / 4) 2048 + (8 ri + n / 8) 128 + (n % 8) 16 + (k % 4) 4
+    uint8_t* o = outs + leaf * split_block_bytes(R8) + (k0 >> 2) * 2048 + (n >> 3) * 128 + (n & 7) * 16;
+    *reinterpret_cast<uint4*>(o) = tc::tf32x4(re);
+    *reinterpret_cast<uint4*>(o + 2048) = tc::tf32x4(re + 4);
+    *reinterpret_cast<uint4*>(o + 1024) = tc::tf32x4(im);
+    *reinterpret_cast<uint4*>(o + 2048 + 1024) = tc::tf32x4(im + 4);
+  } else {
+    uint4 rh, rl, ih, il;
+    tc::split8(re, rh, rl);
+    tc::split8(im, ih, il);
+    uint8_t* o = outs + leaf * split_block_bytes(R8) + (k0 >> 3) * 2048 + (n >> 3) * 128 + (n & 7) * 16;
+    const int64_t half = int64_t(R8) * 256;
+    *reinterpret_cast<uint4*>(o) = rh;                 // Re hi
+    *reinterpret_cast<uint4*>(o + 1024) = ih;          // Im hi
+    *reinterpret_cast<uint4*>(o + half) = rl;          // Re lo
+    *reinterpret_cast<uint4*>(o + half + 1024) = il;   // Im lo
+  }
 }
 
 // (V^L)^* for a panel of 64 RHS, one CTA of 64 R8 / 8 threads per group g (leaves
@@ -749,7 +740,9 @@ __device__ __forceinline__ void leaf_v_point(float2 (&acc)[8], const float2* vro
   }
 }
 
-template <bool TF32>
+// XPOSE (the adjoint's U^* leaf products): the group's item is a U^L item (line = k,
+// entry = point, U itself), read transposed and conjugated.
+template <bool TF32, bool XPOSE>
 __global__ void __launch_bounds__(kTcNR * kLeafMaxR8 / 8) leaf_v_kernel(const __grid_constant__ LeafArgs a) {
   constexpr int NR = kTcNR;
   extern __shared__ __align__(16) float2 lsm[];
@@ -775,7 +768,16 @@ __global__ void __launch_bounds__(kTcNR * kLeafMaxR8 / 8) leaf_v_kernel(const __
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int q = q0 + u * nth, b = q / R8, k = q - b * R8;
-        v[u] = q < nb * R8 && k < R ? item_entry(ibase, it, b0 + b, k) : make_float2(0.f, 0.f);
+        if (q < nb * R8 && k < R) {
+          if (XPOSE) {
+            const float2 e = item_entry(ibase, it, k, b0 + b);
+            v[u] = make_float2(e.x, -e.y);
+          } else {
+            v[u] = item_entry(ibase, it, b0 + b, k);
+          }
+        } else {
+          v[u] = make_float2(0.f, 0.f);
+        }
       }
 #pragma unroll
       for (int u = 0; u < 8; ++u)
@@ -809,6 +811,9 @@ __global__ void __launch_bounds__(kTcNR * kLeafMaxR8 / 8) leaf_v_kernel(const __
 // rows of 64 real then 64 imaginary parts, staged whole in shared memory.  Thread
 // (b, nq) computes point b of the round for the 16 RHS n = 16 nq + 0..15, so that a
 // warp stores 32 consecutive points of one RHS row.
+// XPOSE (the adjoint's V^L leaf products): the group's item is a (V^L)^* item (line =
+// point, entry = k, conj V), read transposed and conjugated.
+template <bool XPOSE>
 __global__ void __launch_bounds__(kLeafThreads) leaf_u_kernel(const __grid_constant__ LeafArgs a) {
   constexpr int NR = kTcNR, NQ = kLeafThreads / kLeafPts, MN = NR / NQ;
   extern __shared__ __align__(16) float2 lsm[];
@@ -845,7 +850,16 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_u_kernel(const __grid_const
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int q = q0 + u * kLeafThreads, k = q / nb, b = q - k * nb;
-        v[u] = q < R * nb ? item_entry(ibase, it, k, b0 + b) : make_float2(0.f, 0.f);
+        if (q < R * nb) {
+          if (XPOSE) {
+            const float2 e = item_entry(ibase, it, b0 + b, k);
+            v[u] = make_float2(e.x, -e.y);
+          } else {
+            v[u] = item_entry(ibase, it, k, b0 + b);
+          }
+        } else {
+          v[u] = make_float2(0.f, 0.f);
+        }
       }
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
@@ -955,6 +969,43 @@ __global__ void __launch_bounds__(256) tf32_tiles_kernel(const uint8_t* __restri
   }
 }
 
+// Adjoint tiles from the forward split-BF16 tiles of one stage: tile T (M_t x K_t,
+// chunks along K) -> T^H (K_t x M_t, chunks along M_t): entry (i, k) of T^H is
+// conj(T[k][i]); Im planes change sign (hi and lo).  One CTA per K16 chunk of the
+// adjoint tile (n_groups x M_t / 16), one thread per entry.
+__global__ void __launch_bounds__(256) adjoint_tiles_kernel(const uint8_t* __restrict__ src, uint8_t* __restrict__ dst,
+                                                           int64_t n_chunks, int M_t, int K_t) {
+  const int64_t chunk = blockIdx.x;
+  if (chunk >= n_chunks) return;
+  const int nka = M_t / 16;                    // adjoint chunks per tile
+  const int64_t g = chunk / nka;
+  const int kka = int(chunk - g * nka);
+  const int64_t tile = int64_t(M_t) * K_t * 8;
+  const uint32_t pbf = uint32_t(M_t) * 32, pba = uint32_t(K_t) * 32;   // plane bytes of a chunk
+  const uint8_t* t0 = src + g * tile;
+  uint8_t* a0 = dst + g * tile + int64_t(kka) * 4 * pba;
+  for (int q = threadIdx.x; q < K_t * 16; q += blockDim.x) {
+    const int i = q >> 4, kc = q & 15;          // adjoint row i (= forward column), K kc
+    const int m = 16 * kka + kc, k = i;         // forward row m, column k
+    const uint8_t* fc = t0 + int64_t(k >> 4) * 4 * pbf;
+    const uint32_t fo = uint32_t(((m >> 3) * 2 + ((k & 15) >> 3)) * 128 + (m & 7) * 16 + (k & 7) * 2);
+    const uint32_t ao = uint32_t(((i >> 3) * 2 + (kc >> 3)) * 128 + (i & 7) * 16 + (kc & 7) * 2);
+#pragma unroll
+    for (int pl = 0; pl < 4; ++pl) {            // planes Re hi, Im hi, Re lo, Im lo
+      uint16_t v = *reinterpret_cast<const uint16_t*>(fc + pl * pbf + fo);
+      if (pl & 1) v ^= 0x8000u;                 // conj
+      *reinterpret_cast<uint16_t*>(a0 + pl * pba + ao) = v;
+    }
+  }
+}
+
+cudaError_t launch_adjoint_tiles(const uint8_t* src, uint8_t* dst, int n_groups, int M_t, int K_t, cudaStream_t stream) {
+  const int64_t n_chunks = int64_t(n_groups) * (M_t / 16);
+  if (n_chunks <= 0) return cudaSuccess;
+  adjoint_tiles_kernel<<<unsigned(n_chunks), 256, 0, stream>>>(src, dst, n_chunks, M_t, K_t);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_tf32_tiles(const uint8_t* src, uint8_t* dst, int64_t n_chunks, int M_t, cudaStream_t stream) {
   if (n_chunks <= 0) return cudaSuccess;
   tf32_tiles_kernel<<<unsigned(n_chunks), 256, 0, stream>>>(src, dst, n_chunks, M_t);
@@ -975,9 +1026,12 @@ cudaError_t launch_permute_in(const LeafArgs& a, cudaStream_t stream) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_leaf(const LeafArgs& a, bool u_side, int n_groups, cudaStream_t stream, bool tf32) {
+cudaError_t launch_leaf(const LeafArgs& a, bool u_side, int n_groups, cudaStream_t stream, bool tf32, bool xpose) {
   const size_t smem = leaf_smem_bytes(a.R, a.c, u_side);
-  void (*kern)(LeafArgs) = u_side ? leaf_u_kernel : (tf32 ? leaf_v_kernel<true> : leaf_v_kernel<false>);
+  void (*kern)(LeafArgs) =
+      u_side ? (xpose ? leaf_u_kernel<true> : leaf_u_kernel<false>)
+             : (tf32 ? (xpose ? leaf_v_kernel<true, true> : leaf_v_kernel<true, false>)
+                     : (xpose ? leaf_v_kernel<false, true> : leaf_v_kernel<false, false>));
   // (V^L)^*: one thread per RHS column and group of 8 rows
   const int threads = u_side ? kLeafThreads : kTcNR * (a.R8 / 8);
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));

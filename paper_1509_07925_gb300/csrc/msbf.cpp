@@ -227,7 +227,7 @@ mbf_status mbf_msbf_apply_adjoint(mbf_msbf_t m, const void* u, void* g, int64_t 
     if (!m || !g || !u) fail(MBF_ERR_INVALID, "NULL argument");
     if (nrhs < 0 || nrhs > (int64_t(1) << 24)) fail(MBF_ERR_INVALID, "nrhs out of range");
     if (nrhs == 0) return;
-    if (precision == MBF_PREC_BF16X3) fail(MBF_ERR_INVALID, "the tensor-core path applies the forward operator only");
+    if (precision == MBF_PREC_TF32) fail(MBF_ERR_INVALID, "TF32 operands apply the forward operator only");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // the parts and the centre write disjoint entries of g (they partition Omega)
     cuda_ok(cudaMemsetAsync(g, 0, size_t(nrhs) * size_t(m->n_in) * sizeof(float2), st), "cudaMemsetAsync");

@@ -468,6 +468,8 @@ void op_free(mbf_op_s* op) {
   cudaFree(op->d_stage_out);
   cudaFree(op->d_tc_arena);
   cudaFree(op->d_tc_arena_tf32);
+  cudaFree(op->d_tc_arena_adj);
+  cudaFree(op->d_x_inv);
   cudaFree(op->d_tc_bufs);
   for (auto& r : op->prof_pending) {
     cudaEventDestroy(r.e0);
@@ -539,17 +541,58 @@ mbf_op_s* op_create(const mbf_factors_t& f) {
       if (!leaf_fits(op->tcplan.st[0].R8_in, op->c) || leaf_smem_bytes(op->RU[size_t(op->L)], op->c, true) > size_t(optin) ||
           leaf_smem_bytes(op->RV[size_t(op->L)], op->c, false) > size_t(optin))
         fail(MBF_ERR_INVALID, "leaf rank too large for the tensor path");
-      // accumulator sets (2 M_t TMEM columns each), panel buffers, A ring slots
-      op->tc_nsets = 4 * op->tc_mt_max <= 512 ? 2 : 1;
-      op->tc_nxb = 2;
-      auto smem = [&](int nsa) { return tc_smem_bytes(nsa, op->tc_nxb, op->tc_nsets, op->tc_mt_max, op->tc_kpad_max); };
-      if (smem(2) > size_t(optin)) op->tc_nxb = 1;
-      if (smem(2) > size_t(optin)) fail(MBF_ERR_INVALID, "tiles too large for the tensor path");
-      op->tc_nsa = 2;
-      while (op->tc_nsa < 8 && smem(op->tc_nsa + 1) <= size_t(optin)) ++op->tc_nsa;
-      // more than half the SM's shared memory: one CTA per SM, so that each CTA's
-      // 512-column TMEM allocation never waits on another CTA of the same launch
-      op->tc_smem = std::max(smem(op->tc_nsa), size_t(optin) / 2 + 1024);
+      // accumulator sets (2 M_t TMEM columns each), panel buffers, A ring slots; more
+      // than half the SM's shared memory, so one CTA per SM and each CTA's 512-column
+      // TMEM allocation never waits on another CTA of the same launch
+      auto config = [&](int mt, int kp, int& nsets, int& nxb, int& nsa, size_t& sm) {
+        nsets = 4 * mt <= 512 ? 2 : 1;
+        nxb = 2;
+        auto smem = [&](int n) { return tc_smem_bytes(n, nxb, nsets, mt, kp); };
+        if (smem(2) > size_t(optin)) nxb = 1;
+        if (smem(2) > size_t(optin)) fail(MBF_ERR_INVALID, "tiles too large for the tensor path");
+        nsa = 2;
+        while (nsa < 8 && smem(nsa + 1) <= size_t(optin)) ++nsa;
+        sm = std::max(smem(nsa), size_t(optin) / 2 + 1024);
+      };
+      config(op->tc_mt_max, op->tc_kpad_max, op->tc_nsets, op->tc_nxb, op->tc_nsa, op->tc_smem);
+      // the adjoint plan: stage e of it is forward stage S - 1 - e with its tile
+      // conjugate-transposed (M_t <-> K_t), reading where the forward stage writes and
+      // writing where it reads (same pattern parameters)
+      try {
+        const TCPlan& fp = op->tcplan;
+        TCPlan& ap = op->tcplan_adj;
+        ap = fp;
+        for (int e = 0; e < fp.n_stages; ++e) {
+          const TCStage& fs = fp.st[fp.n_stages - 1 - e];
+          TCStage& as = ap.st[e];
+          as = fs;
+          as.M_t = fs.K_t;
+          as.K_t = fs.M_t;
+          as.K_pad = fs.M_t;
+          as.in_pat = fs.out_pat;
+          as.out_pat = fs.in_pat;
+          as.R_in = fs.R_out;
+          as.R_out = fs.R_in;
+          as.R8_in = fs.R8_out;
+          as.R8_out = fs.R8_in;
+          as.plane_bytes = as.M_t * 32;
+          as.last = e == fp.n_stages - 1;
+          if (fs.K_pad != fs.K_t || as.M_t > kTcMaxRows || as.K_pad % 16 != 0 ||
+              int64_t(as.K_pad / 16) * 4 * as.plane_bytes != fs.tile_bytes)
+            fail(MBF_ERR_INVALID, "tile shape not supported by the tensor adjoint");
+        }
+        op->tca_mt_max = op->tc_kpad_max;
+        op->tca_kpad_max = op->tc_mt_max;
+        if (!leaf_fits(ap.st[0].R8_in, op->c) || leaf_smem_bytes(op->RV[size_t(op->L)], op->c, true) > size_t(optin) ||
+            leaf_smem_bytes(op->RU[size_t(op->L)], op->c, false) > size_t(optin))
+          fail(MBF_ERR_INVALID, "leaf rank too large for the tensor adjoint");
+        config(op->tca_mt_max, op->tca_kpad_max, op->tca_nsets, op->tca_nxb, op->tca_nsa, op->tca_smem);
+        std::vector<int32_t> xinv(size_t(std::max<int64_t>(f.n_out, 1)), -1);
+        for (int64_t p = 0; p < f.n_out; ++p) xinv[size_t(f.x_perm[p])] = int32_t(p);
+        op->d_x_inv = dev_upload(xinv, "inverse X permutation");
+      } catch (const Error& err) {
+        op->tc_adj_unavailable = err.what();
+      }
       std::vector<int32_t> winv(size_t(std::max<int64_t>(f.n_in, 1)), -1);
       for (int64_t p = 0; p < f.n_w; ++p) winv[size_t(f.w_perm[p])] = int32_t(p);
       op->d_w_inv = dev_upload(winv, "inverse Omega permutation");
@@ -694,6 +737,106 @@ void apply_tc(mbf_op_s* op, const float2* g, float2* u, int64_t nrhs, cudaStream
   }
 }
 
+// Tensor-core adjoint g = K^* u, per panel of 64 RHS: permute the panel into X-tree
+// order, the U^* leaf products (from the U^L items), the persistent tcgen05 kernel over
+// the reversed levels with conjugate-transposed tiles, the V^L leaf products (from the
+// (V^L)^* items) scattered to natural Omega order.
+void apply_tc_adj(mbf_op_s* op, const float2* u, float2* g, int64_t nrhs, cudaStream_t st, int grid, bool accumulate) {
+  if (!op->tc_unavailable.empty()) fail(MBF_ERR_INVALID, "tensor path unavailable: " + op->tc_unavailable);
+  if (!op->tc_adj_unavailable.empty()) fail(MBF_ERR_INVALID, "tensor adjoint unavailable: " + op->tc_adj_unavailable);
+  const TCPlan& fp = op->tcplan;
+  const TCPlan& ap = op->tcplan_adj;
+  const int S = ap.n_stages;
+  const int64_t vec_bytes = tc_vec_bytes(op);
+  tc_prepare(op);
+  if (!op->d_tc_arena_adj) {   // first adjoint apply: conjugate-transpose the tiles (kept)
+    if (cudaMalloc(&op->d_tc_arena_adj, size_t(op->tc_bytes)) != cudaSuccess) {
+      op->d_tc_arena_adj = nullptr;
+      fail(MBF_ERR_OOM, "cudaMalloc adjoint tiles");
+    }
+    for (int e = 0; e < fp.n_stages; ++e) {
+      const TCStage& fs = fp.st[e];
+      cuda_check(launch_adjoint_tiles(op->d_tc_arena + fs.base, op->d_tc_arena_adj + fs.base, fs.n_groups, fs.M_t,
+                                      fs.K_t, st),
+                 "adjoint tile conversion");
+    }
+  }
+  if (op->n_w < op->n_in && !accumulate)   // Omega points outside the tree: zero
+    cuda_check(cudaMemsetAsync(g, 0, size_t(nrhs) * size_t(op->n_in) * sizeof(float2), st), "cudaMemsetAsync");
+  int sms = op->sms;
+  if (grid > 0) sms = std::min(sms, grid);
+  const Stage& leaf_st = op->plan.st[0];                        // (V^L)^* items
+  const Stage& last_st = op->plan.st[op->plan.n_stages - 1];    // U^L items (item 1)
+  uint8_t* yl = op->d_tc_bufs;
+  uint8_t* bufs = yl + vec_bytes;
+  float* ylast = reinterpret_cast<float*>(yl + int64_t(S) * vec_bytes);
+  for (int64_t r0 = 0; r0 < nrhs; r0 += kTcNR) {
+    // u -> panel in X-tree order
+    LeafArgs pa{};
+    pa.perm = op->d_x_inv;
+    pa.vec = u;
+    pa.outp = op->d_tc_gt;
+    pa.len_vec = op->n_out;
+    pa.nrhs = int32_t(nrhs);
+    pa.rhs0 = int32_t(r0);
+    cudaEvent_t e0 = prof_begin(op, st);
+    cuda_check(launch_permute_in(pa, st), "panel permute launch");
+    prof_end(op, PK_PERMUTE, e0, st);
+    // (U^L)^*: panel -> yl (X-leaf blocks)
+    LeafArgs la{};
+    la.arena = op->d_arena;
+    la.items = op->d_items;
+    la.item_base = last_st.item_base + 1;
+    la.item_stride = last_st.n_items;
+    la.off = op->d_x_off;
+    la.vec = op->d_tc_gt;
+    la.outs = yl;
+    la.c = op->c;
+    la.R = op->RU[size_t(op->L)];
+    la.R8 = ap.st[0].R8_in;
+    e0 = prof_begin(op, st);
+    cuda_check(launch_leaf(la, false, last_st.n_groups, st, false, true), "leaf (U^L)^* launch");
+    prof_end(op, PK_LEAF_V, e0, st);
+    // (G^l)^*, l = L-1 .. h, (M^h)^*, H^l, l = h .. L-1 on tensor cores
+    TCArgs ta{};
+    ta.arena = op->d_tc_arena_adj;
+    ta.x_in = yl;
+    ta.bufs = bufs;
+    ta.y_out = ylast;
+    ta.buf_stride = vec_bytes;
+    ta.counters = op->d_tc_counters;
+    ta.status = op->d_status;
+    ta.nsa = op->tca_nsa;
+    ta.nxb = op->tca_nxb;
+    ta.nsets = op->tca_nsets;
+    ta.mt_max = op->tca_mt_max;
+    ta.kpad_max = op->tca_kpad_max;
+    ta.plan = ap;
+    e0 = prof_begin(op, st);
+    cuda_check(launch_apply_tc(ta, sms, op->tca_smem, st, false), "tensor-core launch");
+    prof_end(op, PK_TC, e0, st);
+    // V^L: last stage output -> g (natural Omega order)
+    LeafArgs lv{};
+    lv.arena = op->d_arena;
+    lv.items = op->d_items;
+    lv.item_base = leaf_st.item_base;
+    lv.item_stride = leaf_st.n_items;
+    lv.perm = op->d_w_perm;
+    lv.off = op->d_w_off;
+    lv.wl = ylast;
+    lv.outp = g;
+    lv.len_out = op->n_in;
+    lv.nrhs = int32_t(nrhs);
+    lv.rhs0 = int32_t(r0);
+    lv.c = op->c;
+    lv.R = op->RV[size_t(op->L)];
+    lv.accumulate = accumulate ? 1 : 0;
+    e0 = prof_begin(op, st);
+    cuda_check(launch_leaf(lv, true, leaf_st.n_groups, st, false, true), "leaf V^L launch");
+    prof_end(op, PK_LEAF_U, e0, st);
+  }
+}
+
 void apply_impl(mbf_op_s* op, const void* in, void* out, int64_t nrhs, int32_t precision, void* stream,
                 bool adj, int grid = 0, bool accumulate = false) {
   if (!op) fail(MBF_ERR_INVALID, "operator is NULL");
@@ -706,7 +849,11 @@ void apply_impl(mbf_op_s* op, const void* in, void* out, int64_t nrhs, int32_t p
   if (nrhs > (int64_t(1) << 24)) fail(MBF_ERR_INVALID, "nrhs too large");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (uses_tensor(op, nrhs, precision, adj)) {
-    if (adj) fail(MBF_ERR_INVALID, "the tensor-core path applies the forward operator only");
+    if (adj) {
+      if (precision == MBF_PREC_TF32) fail(MBF_ERR_INVALID, "TF32 operands apply the forward operator only");
+      apply_tc_adj(op, static_cast<const float2*>(in), static_cast<float2*>(out), nrhs, st, grid, accumulate);
+      return;
+    }
     apply_tc(op, static_cast<const float2*>(in), static_cast<float2*>(out), nrhs, st, grid, accumulate,
              precision == MBF_PREC_TF32);
     return;
@@ -763,11 +910,13 @@ mbf_status guard(F&& fn) {
 
 void set_last_error(const std::string& m) { g_last_error = m; }
 
-// Which path an apply takes: split-BF16x3 or TF32 on request; AUTO uses the tensor cores for
-// forward applies from tc_min_rhs right-hand sides (8, or what the tuner measured).
+// Which path an apply takes: split-BF16x3 or TF32 on request; AUTO uses the split-BF16x3
+// tensor cores from tc_min_rhs right-hand sides (8, or what the tuner measured), for the
+// adjoint too where its conjugate-transposed tiles fit.
 bool uses_tensor(const mbf_op_s* op, int64_t nrhs, int32_t precision, bool adj) {
   return precision == MBF_PREC_BF16X3 || precision == MBF_PREC_TF32 ||
-         (precision == MBF_PREC_AUTO && nrhs >= op->tc_min_rhs && !adj && op->tc_unavailable.empty());
+         (precision == MBF_PREC_AUTO && nrhs >= op->tc_min_rhs && op->tc_unavailable.empty() &&
+          (!adj || op->tc_adj_unavailable.empty()));
 }
 
 // Bytes of one tensor-path vector: every block of a level at the largest R8, split or
@@ -788,7 +937,7 @@ void tc_prepare(mbf_op_s* op) {
     fail(MBF_ERR_OOM, "cudaMalloc tensor-path workspace");
   if (cudaMalloc(&op->d_tc_counters, tc_counter_bytes(op->tcplan)) != cudaSuccess)
     fail(MBF_ERR_OOM, "cudaMalloc tensor-path counters");
-  if (cudaMalloc(&op->d_tc_gt, size_t(std::max<int64_t>(op->n_w, 1)) * kTcNR * sizeof(float2)) != cudaSuccess)
+  if (cudaMalloc(&op->d_tc_gt, size_t(std::max<int64_t>({op->n_w, op->n_out, 1})) * kTcNR * sizeof(float2)) != cudaSuccess)
     fail(MBF_ERR_OOM, "cudaMalloc tensor-path input panel");
 }
 

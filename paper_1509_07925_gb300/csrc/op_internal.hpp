@@ -42,6 +42,14 @@ struct mbf_op_s {
   float2* d_tc_gt = nullptr;          // input panel in Omega-tree order [n_w][64]
   int32_t* d_w_inv = nullptr;         // natural Omega index -> tree position (-1: not in the tree)
   std::string tc_unavailable;         // why the tensor path cannot run for this operator ("" if it can)
+  // adjoint on the tensor cores: the stages reversed with conjugate-transposed tiles
+  // (converted on the device from the forward tiles on the first adjoint apply)
+  mbf::TCPlan tcplan_adj{};
+  uint8_t* d_tc_arena_adj = nullptr;
+  int tca_mt_max = 16, tca_kpad_max = 16, tca_nsa = 2, tca_nxb = 2, tca_nsets = 2;
+  size_t tca_smem = 0;
+  int32_t* d_x_inv = nullptr;         // natural x index -> X-tree position
+  std::string tc_adj_unavailable;     // why the adjoint cannot run on the tensor cores
   int sms = 0;                        // SMs of the device (the persistent grids)
   int64_t tc_min_rhs = 8;             // AUTO: tensor cores from this many RHS (tuner may change it)
   std::vector<int64_t> nnz_stage;     // nonzero factor entries per forward stage

@@ -83,14 +83,37 @@ def test_tensor_path_is_deterministic_and_panel_independent(ops):
     assert np.array_equal(one[0], a[65])
 
 
-def test_tensor_adjoint_is_rejected(ops, bd):
-    op, fs, sb = ops(("dft", 16, 2, 2, 8, "none"))
-    w = complex_normal(fs.n_out, 8, seed=6)
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("nrhs", [8, 64, 70])
+def test_tensor_adjoint_matches_oracle(ops, case, nrhs):
+    """K^* on the tensor cores (reversed levels, conjugate-transposed tiles converted on
+    the device, U^* and V^L leaf products) against the oracle's FP64 adjoint."""
+    op, fs, sb = ops(case)
+    w = complex_normal(fs.n_out, nrhs, seed=6)
+    g = gpu_apply(torch, op, w, adjoint=True, precision=MBF_PREC_BF16X3)
+    ref = sb.adjoint(w)
+    assert np.all(np.isfinite(g))
+    for k in range(nrhs):
+        assert rel(g[k], ref[k]) <= TOL_BF16X3, (case, nrhs, k, rel(g[k], ref[k]))
+
+
+def test_auto_adjoint_uses_tensor_path_and_agrees_with_simt(ops, bd):
+    op, fs, sb = ops(("fio_iso", 64, 2, 4, 24, "polar"))
+    w = complex_normal(fs.n_out, 40, seed=8)
+    ga = gpu_apply(torch, op, w, adjoint=True, precision=MBF_PREC_AUTO)
+    gt = gpu_apply(torch, op, w, adjoint=True, precision=MBF_PREC_BF16X3)
+    gs = gpu_apply(torch, op, w, adjoint=True, precision=MBF_PREC_FP32_SIMT)
+    assert np.array_equal(ga, gt)              # AUTO with 40 RHS is the tensor path
+    assert rel(gt, gs) <= TOL_BF16X3
+    # the adjoint identity <K g, w> = <g, K^* w> across the two tensor applies
+    g = complex_normal(fs.n_in, 40, seed=9)
+    u = gpu_apply(torch, op, g, precision=MBF_PREC_BF16X3)
+    lhs = np.vdot(w, u)
+    rhs = np.vdot(gt, g)
+    assert abs(lhs - rhs) <= 1e-4 * abs(lhs)
+    # TF32 operands are forward only
     with pytest.raises(bd.MbfError):
-        gpu_apply(torch, op, w, adjoint=True, precision=MBF_PREC_BF16X3)
-    # AUTO falls back to the FP32 path for the adjoint
-    g = gpu_apply(torch, op, w, adjoint=True, precision=MBF_PREC_AUTO)
-    assert rel(g, sb.adjoint(w)) <= 1e-5
+        gpu_apply(torch, op, w, adjoint=True, precision=MBF_PREC_TF32)
 
 
 def test_host_buffers_on_tensor_path(ops, bd):

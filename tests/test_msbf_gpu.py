@@ -84,6 +84,19 @@ def test_msbf_adjoint(bd, cases, n):
         assert rel(g[k], ref[k]) <= 1e-5
 
 
+@pytest.mark.parametrize("n", [c[0] for c in CASES])
+def test_msbf_adjoint_tensor(bd, cases, n):
+    """The multiscale adjoint with 64 RHS on the tensor cores: each corona's adjoint
+    scatters into its own Omega points (zero elsewhere for the first part, accumulated
+    for the others), the centre adds its part."""
+    m, sm, gm = cases[n]
+    w = complex_normal(n * n, 64, seed=35)
+    g = _apply(bd, gm, w, n * n, MBF_PREC_BF16X3, adjoint=True)
+    ref = sm.adjoint(w)
+    for k in range(64):
+        assert rel(g[k], ref[k]) <= 1e-4
+
+
 def test_library_construction_matches_assembled_parts_and_direct_sum(bd):
     """mbf_build_msbf (its own corona split) equals the parts built one by one on the
     oracle's split with the same seeds; the GPU result matches the FP64 apply of the
