@@ -60,6 +60,8 @@ void apply_static_impl(mbf_op_s* op, const void* g, void* u, int64_t nrhs, void*
   if (nrhs == 0) return;
   if (!g || !u) mbf::fail(MBF_ERR_INVALID, "NULL vector");
   if (nrhs > (int64_t(1) << 24)) mbf::fail(MBF_ERR_INVALID, "nrhs too large");
+  if (!op->simt_unavailable.empty())
+    mbf::fail(MBF_ERR_INVALID, "FP32 SIMT path unavailable: " + op->simt_unavailable);
   const int nrb = nrhs >= 4 ? 4 : (nrhs >= 2 ? 2 : 1);
   const size_t vec_bytes = size_t(op->positions) * size_t(nrb) * sizeof(float2);
   const size_t sync_bytes = kBarrierBytes + mbf::counter_bytes(op->plan);

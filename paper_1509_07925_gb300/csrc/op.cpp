@@ -311,8 +311,8 @@ void validate(const mbf_factors_t& f) {
     if (int64_t(c) * f.RU[l] > kMaxLen || int64_t(c) * f.RV[l] > kMaxLen)
       fail(MBF_ERR_INVALID, "c * rank exceeds " + std::to_string(kMaxLen));
   }
-  if (f.max_leaf_x > kMaxLeaf || f.max_leaf_w > kMaxLeaf)
-    fail(MBF_ERR_INVALID, "leaf with more than " + std::to_string(kMaxLeaf) + " points");
+  if (int64_t(c) * f.max_leaf_x > 65535 || int64_t(c) * f.max_leaf_w > 65535)
+    fail(MBF_ERR_INVALID, "the leaves of a group hold more than 65535 points");
   const int64_t nL = Tree::ipow(c, f.L);
   if (f.x_off[0] != 0 || f.x_off[nL] != f.n_out) fail(MBF_ERR_INVALID, "x_off must span n_out");
   if (f.w_off[0] != 0 || f.w_off[nL] != f.n_w) fail(MBF_ERR_INVALID, "w_off must span n_w");
@@ -386,9 +386,14 @@ void check_dependencies(const Plan& plan) {
   }
 }
 
+// Limits that only the SIMT kernel has (its leaf gathers and pipeline slots) are
+// returned in *simt_reason instead of failing: such an operator applies on the tensor
+// cores only.
 void check_plan(const Plan& plan, const std::vector<Item>& items, size_t arena_bytes, int64_t positions,
-                const mbf_factors_t& f) {
+                const mbf_factors_t& f, std::string* simt_reason) {
   const int c = plan.c;
+  if (f.max_leaf_x > kMaxLeaf || f.max_leaf_w > kMaxLeaf)
+    *simt_reason = "a leaf holds more than " + std::to_string(kMaxLeaf) + " points";
   check_dependencies(plan);
   std::vector<char> wrote, read;
   for (int e = 0; e < plan.n_stages; ++e) {
@@ -421,16 +426,16 @@ void check_plan(const Plan& plan, const std::vector<Item>& items, size_t arena_b
       const int64_t* off = st.in_pat == PAT_LEAF ? f.w_off : f.x_off;
       for (int64_t g = 0; g < st.n_groups; ++g)
         if (off[c * g + c] - off[c * g] > kMaxGroupPoints)
-          fail(MBF_ERR_INVALID, "plan: the leaves of one group hold more than " +
-                                    std::to_string(kMaxGroupPoints) + " points");
+          *simt_reason = "the leaves of one group hold more than " + std::to_string(kMaxGroupPoints) + " points";
     }
     for (int64_t g = 0; g < st.n_groups; ++g)
       for (int m = 0; m < st.n_items; ++m) {
         const Item& it = items[size_t(st.item_base + g * st.n_items + m)];
         if (size_t(it.off128) * 128 + size_t(item_bytes(it.nlines, it.len, it.lpc)) > arena_bytes)
           fail(MBF_ERR_INVALID, "plan: item outside the arena");
-        if (chunk_bytes(std::min<int64_t>(it.lpc, std::max<int64_t>(it.nlines, 1)), it.len) > kSlotBytes)
-          fail(MBF_ERR_INVALID, "plan: chunk larger than a pipeline slot");
+        if (chunk_bytes(std::min<int64_t>(it.lpc, std::max<int64_t>(it.nlines, 1)), it.len) > kSlotBytes ||
+            it.len > kMaxLen || (it.kind != ITEM_MAIN && it.nlines > kMaxLeaf))
+          *simt_reason = "an item line or chunk exceeds the SIMT kernel's pipeline slot";
         const int64_t leaf = c * g;
         if (it.kind == ITEM_MAIN) {
           if (it.nlines != c * st.R_in || it.len != c * st.R_out) fail(MBF_ERR_INVALID, "plan: main block shape");
@@ -503,7 +508,7 @@ mbf_op_s* op_create(const mbf_factors_t& f) {
     int64_t rmax = 1;
     for (int l = op->h; l <= op->L; ++l) rmax = std::max<int64_t>({rmax, op->RU[size_t(l)], op->RV[size_t(l)]});
     op->positions = Tree::ipow(op->c, op->L) * rmax;
-    check_plan(op->plan, pk.items, pk.arena.size(), op->positions, f);
+    check_plan(op->plan, pk.items, pk.arena.size(), op->positions, f, &op->simt_unavailable);
     // ---- device side
     cuda_check(cudaGetDevice(&op->device), "cudaGetDevice");
     op->d_arena = dev_upload(pk.arena, "factor arena");
@@ -601,6 +606,8 @@ mbf_op_s* op_create(const mbf_factors_t& f) {
     } catch (const Error& err) {
       op->tc_unavailable = err.what();
     }
+    if (!op->simt_unavailable.empty() && !op->tc_unavailable.empty())
+      fail(MBF_ERR_INVALID, "no apply path: SIMT (" + op->simt_unavailable + "), tensor cores (" + op->tc_unavailable + ")");
   } catch (...) {
     op_free(op);
     throw;
@@ -858,6 +865,7 @@ void apply_impl(mbf_op_s* op, const void* in, void* out, int64_t nrhs, int32_t p
              precision == MBF_PREC_TF32);
     return;
   }
+  if (!op->simt_unavailable.empty()) fail(MBF_ERR_INVALID, "FP32 SIMT path unavailable: " + op->simt_unavailable);
   const int nrb = nrhs >= 4 ? 4 : (nrhs >= 2 ? 2 : 1);
   ApplyArgs a{};
   a.arena = op->d_arena;
@@ -914,6 +922,9 @@ void set_last_error(const std::string& m) { g_last_error = m; }
 // tensor cores from tc_min_rhs right-hand sides (8, or what the tuner measured), for the
 // adjoint too where its conjugate-transposed tiles fit.
 bool uses_tensor(const mbf_op_s* op, int64_t nrhs, int32_t precision, bool adj) {
+  if (precision == MBF_PREC_AUTO && !op->simt_unavailable.empty() && op->tc_unavailable.empty() &&
+      (!adj || op->tc_adj_unavailable.empty()))
+    return true;   // an operator the SIMT kernel cannot take: tensor cores for any RHS count
   return precision == MBF_PREC_BF16X3 || precision == MBF_PREC_TF32 ||
          (precision == MBF_PREC_AUTO && nrhs >= op->tc_min_rhs && op->tc_unavailable.empty() &&
           (!adj || op->tc_adj_unavailable.empty()));

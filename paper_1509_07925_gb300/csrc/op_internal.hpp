@@ -42,6 +42,7 @@ struct mbf_op_s {
   float2* d_tc_gt = nullptr;          // input panel in Omega-tree order [n_w][64]
   int32_t* d_w_inv = nullptr;         // natural Omega index -> tree position (-1: not in the tree)
   std::string tc_unavailable;         // why the tensor path cannot run for this operator ("" if it can)
+  std::string simt_unavailable;       // why the FP32 SIMT path cannot (leaves beyond its limits; "" if it can)
   // adjoint on the tensor cores: the stages reversed with conjugate-transposed tiles
   // (converted on the device from the forward tiles on the first adjoint apply)
   mbf::TCPlan tcplan_adj{};

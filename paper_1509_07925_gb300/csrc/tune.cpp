@@ -65,6 +65,7 @@ extern "C" mbf_status mbf_op_tune(mbf_op_t op, void* stream, mbf_tune_result_t* 
     cuda_ok(cudaEventCreate(&ev.b), "event");
     const int rhs_list[] = {1, 2, 4, 8, 16, 32, 64};
     for (int R : rhs_list) {
+      if (!op->simt_unavailable.empty()) break;   // tensor-only operator
       out->simt_rhs[out->n_simt] = R;
       out->simt_ms[out->n_simt] = time_apply(op, g.p, u.p, R, MBF_PREC_FP32_SIMT, st, ev, 3);
       ++out->n_simt;
@@ -110,6 +111,7 @@ extern "C" mbf_status mbf_op_tune(mbf_op_t op, void* stream, mbf_tune_result_t* 
           break;
         }
       if (out->tc_min_rhs > kMaxRhs) out->tc_min_rhs = kMaxRhs + 1;
+      if (!op->simt_unavailable.empty()) out->tc_min_rhs = 1;
       op->tc_min_rhs = out->tc_min_rhs;
     }
     cuda_ok(cudaStreamSynchronize(st), "sync");

@@ -151,3 +151,33 @@ def test_tf32_forward_matches_oracle_within_tf32_error(ops, case):
     e3 = max(rel(u3[k], ref[k]) for k in range(64))
     assert e32 <= TOL_TF32, (case, e32)
     assert e3 <= TOL_BF16X3 and e3 < e32, (case, e3, e32)
+
+
+def test_tensor_only_operator_with_large_leaf_groups(bd):
+    """An operator whose leaf groups exceed the SIMT kernel's limits (2-D DFT n = 64, depth 2:
+    256-point leaves, 1024 points per group) applies on the tensor cores only: AUTO takes
+    them for any RHS count, forward and adjoint, and FP32 SIMT (and the allocation-free
+    entry, which is SIMT) report the path as unavailable."""
+    import ctypes as C
+    fs, sb = oracle_case("dft", 64, 2, 2, 16, "none")
+    op = bd.Operator(import_factors(bd, fs))
+    for nrhs in (1, 3, 64):
+        g = complex_normal(fs.n_in, nrhs, seed=50 + nrhs)
+        u = gpu_apply(torch, op, g, precision=MBF_PREC_AUTO)
+        ref = sb.apply(g)
+        for k in range(nrhs):
+            assert rel(u[k], ref[k]) <= TOL_BF16X3, (nrhs, k)
+        w = complex_normal(fs.n_out, nrhs, seed=60 + nrhs)
+        ga = gpu_apply(torch, op, w, adjoint=True, precision=MBF_PREC_AUTO)
+        refa = sb.adjoint(w)
+        for k in range(nrhs):
+            assert rel(ga[k], refa[k]) <= TOL_BF16X3, (nrhs, k)
+    g = complex_normal(fs.n_in, 2, seed=70)
+    with pytest.raises(bd.MbfError):
+        gpu_apply(torch, op, g, precision=MBF_PREC_FP32_SIMT)
+    gt = torch.from_numpy(g.astype(np.complex64)).cuda()
+    ut = torch.empty((2, fs.n_out), dtype=torch.complex64, device="cuda")
+    st = torch.cuda.current_stream().cuda_stream
+    assert bd.lib().mbf_apply_static(op.handle, C.c_void_p(gt.data_ptr()), C.c_void_p(ut.data_ptr()), 2,
+                                     C.c_void_p(st)) == bd.MBF_ERR_INVALID
+    op.close()

@@ -136,3 +136,49 @@ def test_library_construction_matches_assembled_parts_and_direct_sum(bd):
     assert D.rel_err(u_lib[:, S], ud) <= eps + 1e-5
     asm.close()
     lib_m.close()
+
+
+def test_msbf_n256_with_a_tensor_only_corona(bd):
+    """n = 256 (coronas t = 0..3): the t = 3 corona's X tree has depth 4, so its leaf groups
+    hold 1024 points, beyond the SIMT kernel; that part applies on the tensor cores for
+    any RHS count while the others take the SIMT path at 3 RHS.  Parts built one by one
+    (library host builder), checked against the FP64 apply of their exported factors
+    plus the centre, and against the direct sum on sampled outputs."""
+    from oracle import bf as B
+    n, r, nc = 256, 12, 16
+    coronas, centre = MS.corona_sets(n, nc)
+    assert len(coronas) == 4
+    L = int(np.log2(n))
+    parts, sbs = [], []
+    for t, idx in coronas:
+        Lt = 2 * ((L - t) // 2)
+        half = n / 2 ** (t + 1)
+        hf = bd.HostFactors.build(2, n, Lt, r, tree=bd.MBF_TREE_SQUARE, kernel="fio_iso", seed=7 + 101 * (t + 1),
+                                  w_index=idx, w_lo=-half, w_side=2 * half)
+        sbs.append(B.SparseBF(export_factors(hf.arrays())))
+        parts.append(bd.Operator(hf))
+    X, W = P.grid_x(n, 2), P.grid_omega(n, 2)
+    Kc = P.kernel_fio_iso(X[:, None, :], W[centre][None, :, :])
+    m = bd.MsBF.create(parts, Kc.T, centre)
+    S = sample_outputs(n * n, 256, seed=1)
+    for nrhs, prec in ((3, 0), (64, MBF_PREC_BF16X3)):
+        g = complex_normal(n * n, nrhs, seed=80 + nrhs)
+        u = _apply(bd, m, g, n * n, prec)
+        ref = (Kc @ g[:, centre].T).T
+        for sb in sbs:
+            ref = ref + sb.apply(g)
+        for k in range(nrhs):
+            assert rel(u[k], ref[k]) <= 1e-4, (nrhs, k, rel(u[k], ref[k]))
+        ud = D.direct_sum(P.kernel_fio_iso, X, W, g, rows=S)
+        eps = D.rel_err(ref[:, S], ud)
+        assert D.rel_err(u[:, S], ud) <= eps + 1e-4
+    w = complex_normal(n * n, 3, seed=90)
+    ga = _apply(bd, m, w, n * n, 0, adjoint=True)
+    refa = (np.conj(Kc).T @ w.T).T
+    refa_full = np.zeros_like(ga)
+    refa_full[:, centre] = refa
+    for sb in sbs:
+        refa_full = refa_full + sb.adjoint(w)
+    for k in range(3):
+        assert rel(ga[k], refa_full[k]) <= 1e-4
+    m.close()
