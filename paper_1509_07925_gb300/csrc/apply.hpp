@@ -78,7 +78,8 @@ struct LeafArgs {
   int64_t len_vec, len_out;
   int32_t nrhs, rhs0, c, R;
   int32_t R8, item_stride;
-  int32_t accumulate, pad_;   // U^L: 1 adds into u
+  int32_t accumulate;       // U^L: 1 adds into u
+  int32_t pts_cap;          // (V^L)^*: points staged per round (leaf_pts_cap of the largest leaf)
 };
 
 size_t simt_smem_bytes(int nrb, int ns);
@@ -92,7 +93,11 @@ size_t counter_bytes(const Plan& plan);
 // tensor-core path (apply_tc.cu)
 size_t tc_smem_bytes(int nsa, int nxb, int nsets, int mt_max, int kpad_max);
 size_t tc_counter_bytes(const TCPlan& plan);
-size_t leaf_smem_bytes(int R, int c, bool u_side);
+// Dynamic shared memory of a leaf kernel; the (V^L)^* side stages pts_cap points a round.
+size_t leaf_smem_bytes(int R, int c, bool u_side, int pts_cap = 64);
+// Points per round of the (V^L)^* leaf kernel for leaves of at most max_leaf_points
+// points: rounded up to 8, within [8, 64].
+int leaf_pts_cap(int64_t max_leaf_points);
 bool leaf_fits(int R8, int c);   // leaf kernels: R8 <= 64, c <= 8
 // tf32: TF32 tiles and vectors (kind::tf32 MMAs), else split-BF16x3.
 cudaError_t launch_apply_tc(const TCArgs& a, int grid, size_t smem, cudaStream_t stream, bool tf32);

@@ -718,16 +718,19 @@ __device__ __forceinline__ void store_split8(uint8_t* outs, int64_t leaf, int R8
   }
 }
 
-// (V^L)^* for a panel of 64 RHS, one CTA of 64 R8 / 8 threads per group g (leaves
-// j = c g + t):
+// (V^L)^* for a panel of 64 RHS, one CTA of 64 R8 / 8 threads per leaf j (of group
+// g = j / c):
 //   y_j[k][n] = sum over the points b of leaf j of conj(V^L_j[b][k]) gt[b][n],
-// gt = the panel in tree order (permute_in_kernel), stored as split block j (rows
-// k >= R are zero).  The group's item holds conj(V) with line = point (tree order from
-// the group's first point), entry = k; it is staged kLeafPts points at a time in shared
-// memory.  Thread (n, kg) accumulates column n for the 8 rows k = 8 kg + 0..7 over the
-// points of one leaf, reading gt[b][n] straight from L2 eight points ahead, then stores
-// the rows; empty leaves give zero blocks.  Little shared memory per CTA, so that every
-// group's CTA is resident at once.
+// gt = the panel in tree order (permute_in_kernel), stored as split block j (rows k >= R
+// are zero).  The group's item holds conj(V) with line = point (tree order from the
+// group's first point), entry = k.  Up to a.pts_cap points at a time, the leaf's panel
+// rows (contiguous, 512 bytes each) are copied into shared memory by 16-byte cp.async
+// while its item entries are loaded, every load of the round in flight at once; then
+// thread (n, kg) accumulates rows 8 kg .. 8 kg + 7 of column n from shared memory only.
+// One CTA per leaf bounds a CTA's work by the largest leaf, not the largest group (a
+// ragged tree puts several times the mean number of points into some groups).  The
+// panel rows are read by this CTA alone and never again: their L2 lines are discarded
+// rather than written back.  Empty leaves give zero blocks.
 __device__ __forceinline__ void leaf_v_point(float2 (&acc)[8], const float2* vrow, float2 x) {
   const float4* vp = reinterpret_cast<const float4*>(vrow);
 #pragma unroll
@@ -741,67 +744,60 @@ __device__ __forceinline__ void leaf_v_point(float2 (&acc)[8], const float2* vro
 }
 
 // XPOSE (the adjoint's U^* leaf products): the group's item is a U^L item (line = k,
-// entry = point, U itself), read transposed and conjugated.
+// entry = point of the group, U itself), read transposed and conjugated.
 template <bool TF32, bool XPOSE>
 __global__ void __launch_bounds__(kTcNR * kLeafMaxR8 / 8) leaf_v_kernel(const __grid_constant__ LeafArgs a) {
+  using tc::sa;
+  using tc::cp_async16;
+  using tc::cp_async_wait_all;
+  using tc::l2_discard;
   constexpr int NR = kTcNR;
   extern __shared__ __align__(16) float2 lsm[];
-  __shared__ int lend[kLeafMaxC + 1];
-  const int g = blockIdx.x, c = a.c, R = a.R, R8 = a.R8, nth = int(blockDim.x);
-  const int tid = threadIdx.x, n = tid % NR, kg = tid / NR, k0 = 8 * kg;
-  if (tid <= c) lend[tid] = a.off[c * g + tid];
-  const Item it = a.items[a.item_base + int64_t(g) * a.item_stride];
-  const uint8_t* ibase = a.arena + size_t(it.off128) * 128;
-  const int pg = a.off[c * g], np = a.off[c * g + c] - pg;
-  float2* vs = lsm;                        // [kLeafPts][R8], zero for k >= R
-  const float2* xg = a.vec + int64_t(pg) * NR + n;   // gt[pg + b][n] = xg[b * NR]
+  const int j = blockIdx.x, c = a.c, g = j / c, R = a.R, R8 = a.R8, cap = a.pts_cap;
+  const int tid = threadIdx.x, nth = int(blockDim.x), n = tid % NR, k0 = 8 * (tid / NR);
+  float2* xs = lsm;                        // [cap][NR]: the round's panel rows
+  float2* vs = lsm + cap * NR;             // [cap][R8]: conj V, zero for k >= R
+  const int pg = __ldg(a.off + c * g), p0 = __ldg(a.off + j), np = __ldg(a.off + j + 1) - p0;
   float2 acc[8];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) acc[j] = make_float2(0.f, 0.f);
-  __syncthreads();                         // lend
-  int t = 0;                               // leaf being accumulated
-  for (int b0 = 0; b0 < np; b0 += kLeafPts) {
-    const int nb = min(kLeafPts, np - b0);
-    if (b0 > 0) __syncthreads();           // previous round's reads done
-    for (int q0 = tid; q0 < nb * R8; q0 += 8 * nth) {   // 8 loads in flight per thread
-      float2 v[8];
+  for (int u = 0; u < 8; ++u) acc[u] = make_float2(0.f, 0.f);
+  if (np > 0) {
+    const Item it = a.items[a.item_base + int64_t(g) * a.item_stride];
+    const uint8_t* ibase = a.arena + size_t(it.off128) * 128;
+    const int kq = tid % R8, bq = tid / R8, bstep = nth / R8;   // entry k = kq of points bq + bstep u
+    for (int b0 = 0; b0 < np; b0 += cap) {
+      const int nb = min(cap, np - b0);
+      if (b0 > 0) __syncthreads();         // previous round's shared reads done
+      const float2* src = a.vec + int64_t(p0 + b0) * NR;
+      for (int q = tid; q < nb * (NR / 2); q += nth) cp_async16(sa(xs) + uint32_t(q) * 16u, src + 2 * q);
+      for (int b1 = bq; b1 < nb; b1 += 8 * bstep) {             // 8 loads in flight per thread
+        float2 v[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int q = q0 + u * nth, b = q / R8, k = q - b * R8;
-        if (q < nb * R8 && k < R) {
-          if (XPOSE) {
-            const float2 e = item_entry(ibase, it, k, b0 + b);
-            v[u] = make_float2(e.x, -e.y);
-          } else {
-            v[u] = item_entry(ibase, it, b0 + b, k);
-          }
-        } else {
+        for (int u = 0; u < 8; ++u) {
+          const int b = b1 + u * bstep, pt = p0 - pg + b0 + b;
           v[u] = make_float2(0.f, 0.f);
+          if (b < nb && kq < R) {
+            if (XPOSE) {
+              const float2 e = item_entry(ibase, it, kq, pt);
+              v[u] = make_float2(e.x, -e.y);
+            } else {
+              v[u] = item_entry(ibase, it, pt, kq);
+            }
+          }
         }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (b1 + u * bstep < nb) vs[(b1 + u * bstep) * R8 + kq] = v[u];
       }
-#pragma unroll
-      for (int u = 0; u < 8; ++u)
-        if (q0 + u * nth < nb * R8) vs[q0 + u * nth] = v[u];
-    }
-    __syncthreads();
-    int b = 0;
-    while (t < c) {
-      const int le = lend[t + 1] - pg - b0;          // end of leaf t in this round's points
-      const int bend = min(le, nb);
-      for (; b + 8 <= bend; b += 8) {
-        float2 x[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) x[u] = __ldcg(xg + int64_t(b0 + b + u) * NR);
-#pragma unroll
-        for (int u = 0; u < 8; ++u) leaf_v_point(acc, vs + (b + u) * R8 + k0, x[u]);
-      }
-      for (; b < bend; ++b) leaf_v_point(acc, vs + b * R8 + k0, __ldcg(xg + int64_t(b0 + b) * NR));
-      if (le > nb) break;                            // leaf t continues in the next round
-      store_split8<TF32>(a.outs, int64_t(c) * g + t, R8, n, k0, acc);
-      ++t;
+      cp_async_wait_all();
+      __syncthreads();
+      const char* lines = reinterpret_cast<const char*>(src);
+      for (int q = tid; q < nb * (NR * int(sizeof(float2)) / 128); q += nth) l2_discard(lines + 128 * q);
+#pragma unroll 4
+      for (int b = 0; b < nb; ++b) leaf_v_point(acc, vs + b * R8 + k0, xs[b * NR + n]);
     }
   }
-  for (; t < c; ++t) store_split8<TF32>(a.outs, int64_t(c) * g + t, R8, n, k0, acc);
+  store_split8<TF32>(a.outs, j, R8, n, k0, acc);
 }
 
 // U^L for a panel, one CTA per group g (leaves i = c g + t):
@@ -842,9 +838,15 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_u_kernel(const __grid_const
     }
   }
   const int bb = tid % kLeafPts, nq = tid / kLeafPts;
+  __syncthreads();
+  {   // the group's rows are read by this CTA alone and never again: drop them from L2
+    using tc::l2_discard;
+    const char* rows = reinterpret_cast<const char*>(a.wl + int64_t(c) * g * R * 2 * NR);
+    for (int q = tid; q < c * R * (2 * NR * int(sizeof(float)) / 128); q += kLeafThreads) l2_discard(rows + 128 * q);
+  }
   for (int b0 = 0; b0 < np; b0 += kLeafPts) {
     const int nb = min(kLeafPts, np - b0);
-    __syncthreads();
+    if (b0 > 0) __syncthreads();
     for (int q0 = tid; q0 < R * nb; q0 += 8 * kLeafThreads) {   // 8 loads in flight per thread
       float2 v[8];
 #pragma unroll
@@ -918,10 +920,15 @@ size_t tc_smem_bytes(int nsa, int nxb, int nsets, int mt_max, int kpad_max) {
          size_t(nsets) * 2 * kTcChunk * 128 * sizeof(float) + (2 * size_t(nsa) + 20) * 8 + 64;
 }
 
-size_t leaf_smem_bytes(int R, int c, bool u_side) {
+size_t leaf_smem_bytes(int R, int c, bool u_side, int pts_cap) {
   const int R8 = (R + 7) & ~7;
   return u_side ? size_t(c) * R * 2 * kTcNR * sizeof(float) + size_t(R) * kLeafPts * sizeof(float2)
-                : sizeof(float2) * size_t(kLeafPts) * R8;
+                : sizeof(float2) * size_t(pts_cap) * (kTcNR + R8);
+}
+
+int leaf_pts_cap(int64_t max_leaf_points) {
+  const int64_t r8 = (max_leaf_points + 7) & ~int64_t(7);
+  return int(std::min<int64_t>(kLeafPts, std::max<int64_t>(8, r8)));
 }
 
 bool leaf_fits(int R8, int c) { return R8 <= kLeafMaxR8 && c <= kLeafMaxC; }
@@ -1027,16 +1034,19 @@ cudaError_t launch_permute_in(const LeafArgs& a, cudaStream_t stream) {
 }
 
 cudaError_t launch_leaf(const LeafArgs& a, bool u_side, int n_groups, cudaStream_t stream, bool tf32, bool xpose) {
-  const size_t smem = leaf_smem_bytes(a.R, a.c, u_side);
+  const size_t smem = u_side ? leaf_smem_bytes(a.R, a.c, true) : sizeof(float2) * size_t(a.pts_cap) * (kTcNR + a.R8);
   void (*kern)(LeafArgs) =
       u_side ? (xpose ? leaf_u_kernel<true> : leaf_u_kernel<false>)
              : (tf32 ? (xpose ? leaf_v_kernel<true, true> : leaf_v_kernel<true, false>)
                      : (xpose ? leaf_v_kernel<false, true> : leaf_v_kernel<false, false>));
-  // (V^L)^*: one thread per RHS column and group of 8 rows
+  // U^L: a CTA per group; (V^L)^*: a CTA per leaf, one thread per RHS column and group of 8 rows
   const int threads = u_side ? kLeafThreads : kTcNR * (a.R8 / 8);
+  const int64_t blocks = u_side ? int64_t(n_groups) : int64_t(n_groups) * a.c;
+  if (!u_side && (a.pts_cap < 8 || a.pts_cap > kLeafPts || a.pts_cap % 8 != 0)) return cudaErrorInvalidValue;
+  if (blocks <= 0) return cudaSuccess;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (err != cudaSuccess) return err;
-  kern<<<n_groups, threads, smem, stream>>>(a);
+  kern<<<unsigned(blocks), threads, smem, stream>>>(a);
   return cudaGetLastError();
 }
 

@@ -519,6 +519,10 @@ mbf_op_s* op_create(const mbf_factors_t& f) {
       return v;
     };
     const int64_t nL = Tree::ipow(op->c, op->L);
+    for (int64_t q = 0; q < nL; ++q) {
+      op->leaf_pts_x = std::max(op->leaf_pts_x, f.x_off[q + 1] - f.x_off[q]);
+      op->leaf_pts_w = std::max(op->leaf_pts_w, f.w_off[q + 1] - f.w_off[q]);
+    }
     op->d_x_perm = dev_upload(to32(f.x_perm, f.n_out), "x_perm");
     op->d_x_off = dev_upload(to32(f.x_off, nL + 1), "x_off");
     op->d_w_perm = dev_upload(to32(f.w_perm, std::max<int64_t>(f.n_w, 1)), "w_perm");
@@ -701,6 +705,7 @@ void apply_tc(mbf_op_s* op, const float2* g, float2* u, int64_t nrhs, cudaStream
     la.c = op->c;
     la.R = op->RV[size_t(op->L)];
     la.R8 = tp.st[0].R8_in;
+    la.pts_cap = leaf_pts_cap(op->leaf_pts_w);
     e0 = prof_begin(op, st);
     cuda_check(launch_leaf(la, false, leaf_st.n_groups, st, tf32), "leaf (V^L)^* launch");
     prof_end(op, PK_LEAF_V, e0, st);
@@ -801,6 +806,7 @@ void apply_tc_adj(mbf_op_s* op, const float2* u, float2* g, int64_t nrhs, cudaSt
     la.c = op->c;
     la.R = op->RU[size_t(op->L)];
     la.R8 = ap.st[0].R8_in;
+    la.pts_cap = leaf_pts_cap(op->leaf_pts_x);
     e0 = prof_begin(op, st);
     cuda_check(launch_leaf(la, false, last_st.n_groups, st, false, true), "leaf (U^L)^* launch");
     prof_end(op, PK_LEAF_V, e0, st);

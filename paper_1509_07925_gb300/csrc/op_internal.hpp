@@ -24,6 +24,7 @@ struct mbf_op_s {
   uint8_t* d_arena = nullptr;
   mbf::Item* d_items = nullptr;
   int32_t *d_x_perm = nullptr, *d_x_off = nullptr, *d_w_perm = nullptr, *d_w_off = nullptr;
+  int64_t leaf_pts_x = 0, leaf_pts_w = 0;   // points of the largest X / Omega leaf
   float2* d_bufs = nullptr;         // one coefficient vector per stage, 4 RHS wide
   unsigned* d_barrier = nullptr;    // barrier word, then (256 bytes on) the dependency counters
   int* d_status = nullptr;
