@@ -57,6 +57,18 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x, world, device):
+    """The largest x over the ranks (the slowest replica sets the job's time); x itself
+    on one rank.  Needs the default process group when world > 1."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -374,9 +386,7 @@ def main():
         ms = timed_applies(torch, op, g, u, R, pr, args.steps, stream, adjoint=adj)
         if world > 1:
             torch.distributed.barrier()
-            t = torch.tensor([ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, world, "cuda")
         if name == "headline":
             clk = clocks.stop()
         op.check(sp)
@@ -414,12 +424,14 @@ def main():
     for _ in range(2):
         bd._check(lib.mbf_apply_host(op.handle, C.c_void_p(g_host.data_ptr()),
                                      C.c_void_p(u_host.data_ptr()), R, hprec, C.c_void_p(sp)))
+    if world > 1:
+        torch.distributed.barrier()
     t0 = time.perf_counter()
     n_e2e = max(3, args.steps // 2)
     for _ in range(n_e2e):
         bd._check(lib.mbf_apply_host(op.handle, C.c_void_p(g_host.data_ptr()),
                                      C.c_void_p(u_host.data_ptr()), R, hprec, C.c_void_p(sp)))
-    e2e_s = (time.perf_counter() - t0) / n_e2e
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / n_e2e, world, "cuda")
 
     launches = sum(k["launches_per_apply"] for k in head["kernels"].values())
     line = {
