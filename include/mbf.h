@@ -51,8 +51,12 @@ typedef enum mbf_tree_kind {
 } mbf_tree_kind;
 
 typedef enum mbf_precision {
-  MBF_PREC_AUTO = 0,     /* FP32 SIMT for nrhs < 8, split-BF16x3 tensor path otherwise */
-  MBF_PREC_FP32_SIMT = 1,/* complex64 factors, FP32 FMA, FP32 accumulate               */
+  MBF_PREC_AUTO = 0,     /* FP32 SIMT for nrhs < 8 (or the tuner's crossover), split-  */
+                         /* BF16x3 tensor path otherwise; an operator whose leaf groups */
+                         /* exceed the SIMT kernel's limits takes the tensor path for  */
+                         /* any nrhs                                                    */
+  MBF_PREC_FP32_SIMT = 1,/* complex64 factors, FP32 FMA, FP32 accumulate; returns      */
+                         /* MBF_ERR_INVALID on such an operator                         */
   MBF_PREC_TF32 = 2,     /* tensor cores, TF32-rounded operands, FP32 accumulate       */
                          /* (forward only; about 1e-3 relative error; never AUTO)      */
   MBF_PREC_BF16X3 = 3    /* tensor cores, split-BF16 (hi*hi + hi*lo + lo*hi), FP32 acc  */
@@ -195,7 +199,8 @@ mbf_status mbf_apply_adjoint(mbf_op_t op, const void* u, void* g, int64_t nrhs,
  * (allocated on first use, kept by the operator). */
 mbf_status mbf_apply_host(mbf_op_t op, const void* g_host, void* u_host, int64_t nrhs,
                           int32_t precision, void* stream);
-/* Allocation-free forward apply.  The paper has no counterpart: this is a service
+/* Allocation-free forward apply (FP32 SIMT kernel; MBF_ERR_INVALID on an operator it
+ * cannot apply, see MBF_PREC_FP32_SIMT).  The paper has no counterpart: this is a service
  * for callers that may not allocate device memory when they apply an operator --
  * e.g. processes whose device memory is wholly owned by another allocator or held
  * to a fixed budget, or latency-critical loops where an allocation (which may
