@@ -151,6 +151,17 @@ mbf_status mbf_build_factors(const mbf_problem_t* prob, mbf_entry_fn fn, void* c
 mbf_status mbf_factors_view(mbf_factors_h f, mbf_factors_t* view);
 mbf_status mbf_factors_destroy(mbf_factors_h f);
 
+/* Factor files: the checkpoint of the host construction, so that the FP64 build runs
+ * once and later processes load its result.  mbf_factors_save writes a factor set
+ * (validated first, MBF_ERR_INVALID if inconsistent) to `path`: a 64-byte header
+ * (magic, version, byte-order tag, dim, L, sizes, nnz), the arrays of mbf_factors_t in
+ * their order above, and a checksum; it writes `path`.tmp and renames it, so `path` never
+ * holds a partial file.  mbf_factors_load reads such a file into library-owned host
+ * factors (free with mbf_factors_destroy).  A missing, truncated, foreign or corrupt
+ * file, or a failed write, returns MBF_ERR_IO.  Host only; no device is needed. */
+mbf_status mbf_factors_save(const mbf_factors_t* f, const char* path);
+mbf_status mbf_factors_load(const char* path, mbf_factors_h* out);
+
 /* Pack a factor set (built here or supplied by the caller) into the device tile
  * layout on the current CUDA device and return a resident operator.  The factor
  * arrays are only read during the call. */

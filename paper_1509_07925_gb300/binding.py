@@ -115,6 +115,8 @@ SIGNATURES = {
                                     C.POINTER(C.c_void_p)]),
     "mbf_factors_view": (C.c_int, [C.c_void_p, C.POINTER(Factors)]),
     "mbf_factors_destroy": (C.c_int, [C.c_void_p]),
+    "mbf_factors_save": (C.c_int, [C.POINTER(Factors), C.c_char_p]),
+    "mbf_factors_load": (C.c_int, [C.c_char_p, C.POINTER(C.c_void_p)]),
     "mbf_op_create": (C.c_int, [C.POINTER(Factors), C.POINTER(C.c_void_p)]),
     "mbf_build_from_entries": (C.c_int, [C.POINTER(Problem), C.c_void_p, C.c_void_p,
                                          C.POINTER(BuildOpts), C.POINTER(C.c_void_p)]),
@@ -248,6 +250,20 @@ class HostFactors:
         v.H = C.cast(Hp, C.POINTER(C.POINTER(C.c_double)))
         v.S = _ptr(arrs["S"], C.c_double)
         v.nnz = nnz
+        return self
+
+    def save(self, path):
+        """Write the factor set to a factor file (mbf_factors_save)."""
+        _check(lib().mbf_factors_save(C.byref(self.view), os.fsencode(path)))
+
+    @classmethod
+    def load(cls, path):
+        """Factors read from a factor file (mbf_factors_load)."""
+        self = cls()
+        h = C.c_void_p()
+        _check(lib().mbf_factors_load(os.fsencode(path), C.byref(h)))
+        self._handle = h
+        _check(lib().mbf_factors_view(h, C.byref(self.view)))
         return self
 
     # ---- read-only numpy views of the padded arrays (library-built factors)

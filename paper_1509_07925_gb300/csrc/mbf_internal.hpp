@@ -55,6 +55,13 @@ struct FactorSet {
   std::vector<const double*> Gp, Hp;   // pointer tables for the view
   mbf_factors_t view();
 };
+// Consistency checks of a factor set (shapes, offsets, permutations, the apply's
+// limits); throws MBF_ERR_INVALID.
+void validate(const mbf_factors_t& f);
+// Factor files (factor_file.cpp): write a validated factor set; read one back
+// (MBF_ERR_IO for a missing, truncated, foreign or corrupt file).
+void save_factors(const mbf_factors_t& f, const std::string& path);
+FactorSet load_factors(const std::string& path);
 
 // ---------------------------------------------------------------- dense linear algebra
 // Column-major complex matrix.

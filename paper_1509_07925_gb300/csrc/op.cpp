@@ -297,7 +297,7 @@ void pack_tc(const mbf_factors_t& f, const Plan& sp, TCPlan& tp, std::vector<uin
   tp.n_stages = n;
 }
 
-void validate(const mbf_factors_t& f) {
+void validate_factors(const mbf_factors_t& f) {
   if (f.dim != 2 && f.dim != 3) fail(MBF_ERR_INVALID, "dim must be 2 or 3");
   if (f.L < 2 || f.L % 2 || f.L > 20) fail(MBF_ERR_INVALID, "L must be even, 2..20");
   const int c = 1 << f.dim, h = f.L / 2;
@@ -488,7 +488,7 @@ void op_free(mbf_op_s* op) {
 }
 
 mbf_op_s* op_create(const mbf_factors_t& f) {
-  validate(f);
+  validate_factors(f);
   auto* op = new mbf_op_s();
   try {
     op->d = f.dim;
@@ -922,6 +922,8 @@ mbf_status guard(F&& fn) {
 
 }  // namespace
 
+void validate(const mbf_factors_t& f) { validate_factors(f); }
+
 void set_last_error(const std::string& m) { g_last_error = m; }
 
 // Which path an apply takes: split-BF16x3 or TF32 on request; AUTO uses the split-BF16x3
@@ -998,6 +1000,27 @@ mbf_status mbf_factors_view(mbf_factors_h f, mbf_factors_t* view) {
 
 mbf_status mbf_factors_destroy(mbf_factors_h f) {
   return guard([&] { delete f; });
+}
+
+mbf_status mbf_factors_save(const mbf_factors_t* f, const char* path) {
+  return guard([&] {
+    if (!f || !path) fail(MBF_ERR_INVALID, "NULL argument");
+    save_factors(*f, path);
+  });
+}
+
+mbf_status mbf_factors_load(const char* path, mbf_factors_h* out) {
+  return guard([&] {
+    if (!path || !out) fail(MBF_ERR_INVALID, "NULL argument");
+    auto* h = new mbf_factors_s();
+    try {
+      h->fs = load_factors(path);
+    } catch (...) {
+      delete h;
+      throw;
+    }
+    *out = h;
+  });
 }
 
 mbf_status mbf_op_create(const mbf_factors_t* f, mbf_op_t* out) {
