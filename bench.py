@@ -16,6 +16,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import re
 import os
 import statistics
 import subprocess
@@ -137,13 +138,20 @@ KERNEL_SOURCES = {"bf_apply_simt": ("apply_simt.cu", "layout.hpp"),
                   "bf_apply_tc": ("apply_tc.cu", "layout.hpp", "apply.hpp")}
 
 
+def _code_only(text):
+    """Source text without comments and blank lines: edits to comments leave it unchanged."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = (re.sub(r"//.*", "", ln).rstrip() for ln in text.splitlines())
+    return "\n".join(ln for ln in lines if ln)
+
+
 def kernel_source_hash(kernel):
-    """Hash of the sources a kernel is compiled from (its DRAM traffic record is only
-    used while they are unchanged)."""
+    """Hash of the code (comments stripped) of the sources a kernel is compiled from:
+    its DRAM traffic record is only used while that code is unchanged."""
     h = hashlib.sha256()
     for f in KERNEL_SOURCES[kernel]:
-        with open(os.path.join(ROOT, "paper_1509_07925_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1509_07925_gb300", "csrc", f), encoding="utf-8") as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -103,7 +103,7 @@ bool leaf_fits(int R8, int c);   // leaf kernels: R8 <= 64, c <= 8
 cudaError_t launch_apply_tc(const TCArgs& a, int grid, size_t smem, cudaStream_t stream, bool tf32);
 // TF32 tiles (two FP32 planes per K16 chunk) converted from n_chunks split-BF16 chunks of M_t rows.
 cudaError_t launch_tf32_tiles(const uint8_t* src, uint8_t* dst, int64_t n_chunks, int M_t, cudaStream_t stream);
-// One CTA per group of c leaves.
+// U^L side: one CTA per group of c leaves; (V^L)^* side: one CTA per leaf (c n_groups CTAs).
 // xpose: the adjoint's leaf products (U^* from the U^L items, V from the (V^L)^* items).
 cudaError_t launch_leaf(const LeafArgs& a, bool u_side, int n_groups, cudaStream_t stream, bool tf32 = false,
                         bool xpose = false);

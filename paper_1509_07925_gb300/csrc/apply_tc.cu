@@ -614,7 +614,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
 }
 
 // ------------------------------------------------------------------ leaf kernels
-// One CTA per group (its c leaves); the group's points are staged kLeafPts at a time.
+// U^L: one CTA per group (its c leaves), the group's points staged kLeafPts at a time;
+// (V^L)^*: one CTA per leaf, its points staged up to LeafArgs::pts_cap at a time.
 constexpr int kLeafThreads = 256;
 constexpr int kLeafPts = 64;        // points staged per round (= kTcNR)
 constexpr int kLeafMaxR8 = 64;      // largest leaf rank (rounded up to 8) of the tensor path
