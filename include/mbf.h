@@ -104,6 +104,13 @@ typedef struct mbf_build_opts {
   double tol;           /* drop singular values below tol * sigma_1 (default 1e-14)       */
   int32_t threads;      /* host threads (0 = all cores)                                   */
   int32_t reserved;
+  /* Optional checkpoint (NULL: none).  If a factor file exists at this path it is loaded
+   * instead of building (its dim, L, sizes, Omega point set and ranks <= r are checked
+   * against the problem: MBF_ERR_INVALID on a mismatch); otherwise the factors are built
+   * and written there.  The file does not record the kernel, the seed or the options:
+   * name one file per (kernel, seed, options).  mbf_build_msbf uses `path`.t<k> for
+   * corona k. */
+  const char* factor_file;
 } mbf_build_opts_t;
 
 /* Padded FP64 factor set: the interchange layout shared by the builder, the packer

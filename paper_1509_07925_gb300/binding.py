@@ -38,7 +38,8 @@ class Problem(C.Structure):
 
 class BuildOpts(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("sample_factor", C.c_int32), ("max_rounds", C.c_int32),
-                ("tol", C.c_double), ("threads", C.c_int32), ("reserved", C.c_int32)]
+                ("tol", C.c_double), ("threads", C.c_int32), ("reserved", C.c_int32),
+                ("factor_file", C.c_char_p)]
 
 
 class Factors(C.Structure):
@@ -203,7 +204,10 @@ class HostFactors:
 
     @classmethod
     def build(cls, dim, n, L, r, tree=MBF_TREE_UNIFORM, kernel="dft", seed=7, threads=0,
-              w_index=None, w_lo=0.0, w_side=0.0, sample_factor=3, max_rounds=3, tol=1e-14):
+              w_index=None, w_lo=0.0, w_side=0.0, sample_factor=3, max_rounds=3, tol=1e-14,
+              factor_file=None):
+        """Host FP64 construction (mbf_build_factors); with factor_file, loaded from that
+        file if it exists, else built and written there."""
         self = cls()
         prob = Problem(dim=dim, n=n, L=L, r=r, tree=tree)
         if w_index is not None:
@@ -211,7 +215,7 @@ class HostFactors:
             self._keep.append(wi)
             prob.n_w, prob.w_index, prob.w_lo, prob.w_side = wi.size, _ptr(wi, C.c_int64), w_lo, w_side
         opts = BuildOpts(seed=seed, sample_factor=sample_factor, max_rounds=max_rounds, tol=tol,
-                         threads=threads)
+                         threads=threads, factor_file=None if factor_file is None else os.fsencode(factor_file))
         fn = builtin_kernel(kernel) if isinstance(kernel, str) else kernel
         h = C.c_void_p()
         _check(lib().mbf_build_factors(C.byref(prob), fn, None, C.byref(opts), C.byref(h)))
@@ -421,11 +425,13 @@ class MsBF:
 
     @classmethod
     def build(cls, n, r, kernel="fio_iso", n_center=16, seed=7, threads=0, sample_factor=3, max_rounds=3,
-              tol=1e-14):
-        """Host FP64 construction of every part and the centre (mbf_build_msbf)."""
+              tol=1e-14, factor_file=None):
+        """Host FP64 construction of every part and the centre (mbf_build_msbf); with
+        factor_file, corona k's factors are loaded from (or written to) factor_file.t<k>."""
         self = cls()
         prob = Problem(dim=2, n=n, L=2, r=r, tree=MBF_TREE_UNIFORM)
-        opts = BuildOpts(seed=seed, sample_factor=sample_factor, max_rounds=max_rounds, tol=tol, threads=threads)
+        opts = BuildOpts(seed=seed, sample_factor=sample_factor, max_rounds=max_rounds, tol=tol, threads=threads,
+                         factor_file=None if factor_file is None else os.fsencode(factor_file))
         fn = builtin_kernel(kernel) if isinstance(kernel, str) else kernel
         _check(lib().mbf_build_msbf(C.byref(prob), fn, None, C.byref(opts), n_center, C.byref(self._h)))
         return self

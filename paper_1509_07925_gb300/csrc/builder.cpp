@@ -242,6 +242,43 @@ void parallel_for(int64_t count, int threads, F&& fn) {
   if (err) std::rethrow_exception(err);
 }
 
+}  // namespace
+
+// The X tree (uniform) and the Omega tree of a problem (§2.2; §3.2 polar; §4.2 square
+// over a corona).  Frequencies: grid digit - n / 2 per axis, natural row-major order.
+void problem_trees(const mbf_problem_t& prob, Tree& xt, Tree& wt) {
+  const int d = prob.dim, n = prob.n, L = prob.L;
+  if (d != 2 && d != 3) fail(MBF_ERR_INVALID, "dim must be 2 or 3");
+  if (n < 2 || (n & (n - 1)) != 0) fail(MBF_ERR_INVALID, "n must be a power of two");
+  if (L < 2 || (L % 2) != 0) fail(MBF_ERR_INVALID, "L must be even and >= 2");
+  xt = tree_uniform(n, d, L);
+  if (prob.tree == MBF_TREE_UNIFORM) {
+    wt = tree_uniform(n, d, L);
+  } else if (prob.tree == MBF_TREE_POLAR) {
+    if (d != 2) fail(MBF_ERR_INVALID, "polar tree needs dim 2");
+    wt = tree_polar(n, L);
+  } else if (prob.tree == MBF_TREE_SQUARE) {
+    if (!prob.w_index || prob.n_w <= 0) fail(MBF_ERR_INVALID, "square tree needs w_index");
+    if (!(prob.w_side > 0)) fail(MBF_ERR_INVALID, "square tree needs w_side > 0");
+    const int64_t N = Tree::ipow(n, d);
+    std::vector<int64_t> idx(prob.w_index, prob.w_index + prob.n_w);
+    std::vector<double> pts(static_cast<size_t>(prob.n_w * d));
+    for (int64_t q = 0; q < prob.n_w; ++q) {
+      if (idx[size_t(q)] < 0 || idx[size_t(q)] >= N) fail(MBF_ERR_INVALID, "w_index out of range");
+      int64_t rest = idx[size_t(q)];
+      for (int k = d - 1; k >= 0; --k) {
+        pts[size_t(q * d + k)] = double(rest % n) - double(n / 2);
+        rest /= n;
+      }
+    }
+    wt = tree_square(pts, idx, d, prob.w_lo, prob.w_side, L);
+  } else {
+    fail(MBF_ERR_INVALID, "unknown tree kind");
+  }
+}
+
+namespace {
+
 struct Builder {
   const mbf_problem_t& prob;
   mbf_entry_fn fn;
@@ -402,25 +439,7 @@ struct Builder {
         wcoord[size_t(p * d + k)] = double(digit) - double(n / 2);
       }
     }
-    xt = tree_uniform(n, d, L);
-    if (prob.tree == MBF_TREE_UNIFORM) {
-      wt = tree_uniform(n, d, L);
-    } else if (prob.tree == MBF_TREE_POLAR) {
-      if (d != 2) fail(MBF_ERR_INVALID, "polar tree needs dim 2");
-      wt = tree_polar(n, L);
-    } else if (prob.tree == MBF_TREE_SQUARE) {
-      if (!prob.w_index || prob.n_w <= 0) fail(MBF_ERR_INVALID, "square tree needs w_index");
-      if (!(prob.w_side > 0)) fail(MBF_ERR_INVALID, "square tree needs w_side > 0");
-      std::vector<int64_t> idx(prob.w_index, prob.w_index + prob.n_w);
-      std::vector<double> pts(static_cast<size_t>(prob.n_w * d));
-      for (int64_t q = 0; q < prob.n_w; ++q) {
-        if (idx[size_t(q)] < 0 || idx[size_t(q)] >= N) fail(MBF_ERR_INVALID, "w_index out of range");
-        for (int k = 0; k < d; ++k) pts[size_t(q * d + k)] = wcoord[size_t(idx[size_t(q)] * d + k)];
-      }
-      wt = tree_square(pts, idx, d, prob.w_lo, prob.w_side, L);
-    } else {
-      fail(MBF_ERR_INVALID, "unknown tree kind");
-    }
+    problem_trees(prob, xt, wt);
 
     // padded rank caps: R_h = min(r, max |A^h|, max |B^h|); R_{l+1} = min(r, max |node|, c R_l)
     auto max_size = [&](const Tree& T, int l) {

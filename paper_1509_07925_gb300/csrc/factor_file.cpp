@@ -243,4 +243,28 @@ FactorSet load_factors(const std::string& path) {
   return fs;
 }
 
+FactorSet build_or_load(const mbf_problem_t& prob, mbf_entry_fn fn, void* ctx, const mbf_build_opts_t& opts) {
+  const char* path = opts.factor_file;
+  if (!path || !*path) return build_factors(prob, fn, ctx, opts);
+  if (FILE* probe = std::fopen(path, "rb")) {
+    std::fclose(probe);
+    FactorSet fs = load_factors(path);
+    // the file must describe this problem: its dimension, depth, trees (point sets and
+    // orders, which fix n and the tree kind) and ranks within r
+    Tree xt, wt;
+    problem_trees(prob, xt, wt);
+    const std::string who = std::string("factor file ") + path + " was built for another problem: ";
+    if (fs.d != prob.dim || fs.L != prob.L) fail(MBF_ERR_INVALID, who + "dim or L");
+    if (fs.x_perm != xt.perm || fs.x_off != xt.off || fs.n_in != Tree::ipow(prob.n, prob.dim))
+      fail(MBF_ERR_INVALID, who + "X tree or grid size");
+    if (fs.w_perm != wt.perm || fs.w_off != wt.off) fail(MBF_ERR_INVALID, who + "Omega tree or point set");
+    for (int l = fs.L / 2; l <= fs.L; ++l)
+      if (fs.RU[size_t(l)] > prob.r || fs.RV[size_t(l)] > prob.r) fail(MBF_ERR_INVALID, who + "ranks above r");
+    return fs;
+  }
+  FactorSet fs = build_factors(prob, fn, ctx, opts);
+  save_factors(fs.view(), path);
+  return fs;
+}
+
 }  // namespace mbf

@@ -39,6 +39,8 @@ Tree tree_polar(int n, int L);
 Tree tree_square(const std::vector<double>& xi, const std::vector<int64_t>& index, int d,
                  double lo, double side, int L);
 int64_t morton(const int64_t* cell, int d, int L);
+// The X tree and the Omega tree of a problem, as the builder makes them.
+void problem_trees(const mbf_problem_t& prob, Tree& xt, Tree& wt);
 
 // ---------------------------------------------------------------- host factor set
 // Owning version of mbf_factors_t (same layout).
@@ -62,6 +64,9 @@ void validate(const mbf_factors_t& f);
 // (MBF_ERR_IO for a missing, truncated, foreign or corrupt file).
 void save_factors(const mbf_factors_t& f, const std::string& path);
 FactorSet load_factors(const std::string& path);
+// build_factors with the checkpoint of opts.factor_file: load the file if it exists
+// (checked against the problem), else build and write it.
+FactorSet build_or_load(const mbf_problem_t& prob, mbf_entry_fn fn, void* ctx, const mbf_build_opts_t& opts);
 
 // ---------------------------------------------------------------- dense linear algebra
 // Column-major complex matrix.

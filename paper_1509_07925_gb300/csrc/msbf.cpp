@@ -173,7 +173,11 @@ mbf_status mbf_build_msbf(const mbf_problem_t* prob, mbf_entry_fn fn, void* ctx,
         pt.w_side = double(n) / std::ldexp(1.0, t);
         mbf_build_opts_t ot = o;
         ot.seed = o.seed + 101 * uint64_t(t + 1);
-        mbf::FactorSet fs = mbf::build_factors(pt, fn, ctx, ot);
+        const std::string part_file = o.factor_file && *o.factor_file ? std::string(o.factor_file) + ".t" +
+                                                                            std::to_string(t)
+                                                                      : std::string();
+        ot.factor_file = part_file.empty() ? nullptr : part_file.c_str();
+        mbf::FactorSet fs = mbf::build_or_load(pt, fn, ctx, ot);
         mbf_factors_t v = fs.view();
         mbf_op_t op = nullptr;
         const mbf_status s = mbf_op_create(&v, &op);

@@ -982,7 +982,7 @@ mbf_status mbf_build_factors(const mbf_problem_t* prob, mbf_entry_fn fn, void* c
     if (opts) o = *opts;
     auto* h = new mbf_factors_s();
     try {
-      h->fs = build_factors(*prob, fn, ctx, o);
+      h->fs = build_or_load(*prob, fn, ctx, o);
     } catch (...) {
       delete h;
       throw;
@@ -1036,7 +1036,7 @@ mbf_status mbf_build_from_entries(const mbf_problem_t* prob, mbf_entry_fn fn, vo
     if (!prob || !out) fail(MBF_ERR_INVALID, "NULL argument");
     mbf_build_opts_t o{};
     if (opts) o = *opts;
-    FactorSet fs = build_factors(*prob, fn, ctx, o);
+    FactorSet fs = build_or_load(*prob, fn, ctx, o);
     mbf_factors_t v = fs.view();
     *out = op_create(v);
   });

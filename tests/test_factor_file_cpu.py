@@ -134,3 +134,39 @@ def test_inconsistent_factor_set_is_not_written(bd, tmp_path):
     assert e.value.code == bd.MBF_ERR_INVALID
     assert not os.path.exists(tmp_path / "x.mbf") and not os.path.exists(tmp_path / "x.mbf.tmp")
     hf.close()
+
+
+def test_build_option_writes_then_loads_the_checkpoint(bd, tmp_path):
+    """opts.factor_file: the first build writes the file, the second loads it (a damaged
+    file makes the second build fail, so it was read rather than rebuilt)."""
+    p = tmp_path / "ck.mbf"
+    kw = dict(tree=bd.MBF_TREE_POLAR, kernel="fio_iso", seed=5)
+    a = bd.HostFactors.build(2, 16, 4, 8, factor_file=p, **kw)
+    assert p.exists()
+    b = bd.HostFactors.build(2, 16, 4, 8, factor_file=p, **kw)
+    _same(a.arrays(), b.arrays())
+    raw = bytearray(p.read_bytes())
+    raw[len(raw) // 2] ^= 0x01
+    p.write_bytes(bytes(raw))
+    _io_error(bd, lambda: bd.HostFactors.build(2, 16, 4, 8, factor_file=p, **kw))
+    a.close()
+    b.close()
+
+
+def test_build_option_rejects_a_checkpoint_of_another_problem(bd, tmp_path):
+    p = tmp_path / "ck.mbf"
+    bd.HostFactors.build(2, 16, 2, 8, factor_file=p).close()
+    for args, kw in [((2, 32, 2, 8), {}), ((2, 16, 4, 8), {}), ((2, 16, 2, 4), {}),
+                     ((2, 16, 2, 8), dict(tree=bd.MBF_TREE_POLAR))]:
+        with pytest.raises(bd.MbfError) as e:
+            bd.HostFactors.build(*args, factor_file=p, **kw)
+        assert e.value.code == bd.MBF_ERR_INVALID and "another problem" in str(e.value)
+    # a square Omega tree over a point subset: the subset is part of the problem
+    idx = np.arange(0, 256, 2)
+    q = tmp_path / "sq.mbf"
+    kw = dict(tree=bd.MBF_TREE_SQUARE, kernel="fio_iso", w_lo=-8.0, w_side=16.0)
+    bd.HostFactors.build(2, 16, 2, 8, factor_file=q, w_index=idx, **kw).close()
+    bd.HostFactors.build(2, 16, 2, 8, factor_file=q, w_index=idx, **kw).close()
+    with pytest.raises(bd.MbfError) as e:
+        bd.HostFactors.build(2, 16, 2, 8, factor_file=q, w_index=idx + 1, **kw)
+    assert e.value.code == bd.MBF_ERR_INVALID and "point set" in str(e.value)
