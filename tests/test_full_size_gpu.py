@@ -78,3 +78,16 @@ def test_full_size_precision_sweep_64_rhs(full):
     print("precision sweep, max rel err over 64 RHS:", err)
     assert err["fp32_simt"] <= 1e-5 and err["bf16x3"] <= 1e-4 and err["tf32"] <= 5e-3, err
     assert err["fp32_simt"] < err["bf16x3"] < err["tf32"], err
+
+
+def test_full_size_tensor_adjoint_64_rhs(full):
+    """The benchmark's adjoint leg at full size (64 RHS, split-BF16x3 on the tensor cores
+    with the conjugate-transposed tiles) against the FP64 adjoint of the same factors,
+    every output."""
+    op, fs, sb = full
+    w = complex_normal(fs.n_out, 64, seed=WL.seed_g + 3)
+    ga = gpu_apply(torch, op, w, adjoint=True, precision=MBF_PREC_BF16X3)
+    gf = sb.adjoint(w)
+    assert np.all(np.isfinite(ga))
+    errs = [rel(ga[k], gf[k]) for k in range(64)]
+    assert max(errs) <= 1e-4, max(errs)
