@@ -57,3 +57,15 @@ def test_reference_arm_runs_on_rank_zero_only():
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
     assert p.returncode == 0, p.stderr[-2000:]
     assert p.stdout.strip() == ""
+
+
+def test_traffic_record_key_ignores_comments_only():
+    """The DRAM-traffic record of a kernel is keyed to its code: comment or blank-line
+    edits keep the key, any code edit changes it."""
+    sys.path.insert(0, ROOT)
+    import bench
+    base = "int f(int x) {\n  // twice\n  return 2 * x;  /* doubled */\n}\n"
+    assert bench._code_only(base) == bench._code_only(base.replace("// twice", "// two times") + "\n\n")
+    assert bench._code_only(base) == bench._code_only(base.replace("/* doubled */", "/* x2\n spanning */"))
+    assert bench._code_only(base) != bench._code_only(base.replace("2 * x", "3 * x"))
+    assert "twice" not in bench._code_only(base) and "return 2 * x;" in bench._code_only(base)
