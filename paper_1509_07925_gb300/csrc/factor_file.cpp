@@ -130,7 +130,7 @@ void save_factors(const mbf_factors_t& f, const std::string& path) {
   validate(f);
   const Sizes z = sizes_of(f.dim, f.L, f.max_leaf_x, f.max_leaf_w, f.RU, f.RV);
   const std::string tmp = path + ".tmp";
-  {
+  try {
     File file;
     file.f = std::fopen(tmp.c_str(), "wb");
     if (!file.f) fail(MBF_ERR_IO, "cannot create " + tmp);
@@ -164,6 +164,9 @@ void save_factors(const mbf_factors_t& f, const std::string& path) {
     const int rc = std::fclose(file.f);
     file.f = nullptr;
     if (rc != 0) fail(MBF_ERR_IO, "write failed: " + tmp);
+  } catch (...) {   // no partial file is left behind
+    std::remove(tmp.c_str());
+    throw;
   }
   if (std::rename(tmp.c_str(), path.c_str()) != 0) {
     std::remove(tmp.c_str());
