@@ -58,6 +58,15 @@ def dist_env():
     return rank, world, local
 
 
+# arithmetic of each precision: (the type the MMAs / FMAs take, what it means)
+DTYPES = {
+    "bf16x3": ("bf16x3+f32", "complex64 data; tensor cores: each f32 operand split into bf16 hi + lo, "
+                             "hi*hi + hi*lo + lo*hi, f32 accumulation; leaf kernels f32"),
+    "tf32": ("tf32+f32", "complex64 data; tensor cores: tf32 operands, f32 accumulation; leaf kernels f32"),
+    "fp32_simt": ("f32", "complex64 data; f32 FMA, f32 accumulation"),
+}
+
+
 def max_over_ranks(x, world, device):
     """The largest x over the ranks (the slowest replica sets the job's time); x itself
     on one rank.  Needs the default process group when world > 1."""
@@ -428,7 +437,8 @@ def main():
     u_host = torch.empty((R, N), dtype=torch.complex64).pin_memory()
     import ctypes as C
     lib = bd.lib()
-    hprec = {"fp32_simt": bd.MBF_PREC_FP32_SIMT, "bf16x3": bd.MBF_PREC_BF16X3}[head["precision"]]
+    hprec = {"fp32_simt": bd.MBF_PREC_FP32_SIMT, "bf16x3": bd.MBF_PREC_BF16X3,
+             "tf32": bd.MBF_PREC_TF32}[head["precision"]]
     for _ in range(2):
         bd._check(lib.mbf_apply_host(op.handle, C.c_void_p(g_host.data_ptr()),
                                      C.c_void_p(u_host.data_ptr()), R, hprec, C.c_void_p(sp)))
@@ -445,8 +455,8 @@ def main():
     line = {
         "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 (complex64; tensor path: split-bf16x3 operands, f32 accumulate)"
-        if head["precision"] == "bf16x3" else "f32 (complex64)", "data": "synthetic",
+        "vs_baseline": None, "dtype": DTYPES[head["precision"]][0],
+        "dtype_detail": DTYPES[head["precision"]][1], "data": "synthetic",
         "config": {"workload": wl.name, "kernel": wl.kernel, "tree": wl.transform, "n": wl.n, "N": N,
                    "L": wl.L, "r": wl.r, "nrhs": R, "precision": head["precision"],
                    "parallelism": f"replicas{world}",
