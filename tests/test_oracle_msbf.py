@@ -1,7 +1,8 @@
 """Pins of the oracle's multiscale butterfly factorization (§4, eqs. domaindecomp,
 msumd, f1): exact at full rank, the centre-only special case is the dense kernel,
-the coronas and the centre partition Omega, the adjoint identity, and (loose) the
-paper's Table 4 errors."""
+the coronas and the centre partition Omega, the adjoint identity, and the error
+against the Eckart-Young floor of the coronas' middle levels (with the paper's Table 4
+beside it)."""
 import os
 
 import numpy as np
@@ -11,6 +12,8 @@ from mbf_synth import complex_normal, sample_outputs
 from oracle import direct as D
 from oracle import msbf as MS
 from oracle import problem as P
+
+from floor_util import floor_from_tails, middle_level_tails
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -76,17 +79,35 @@ def test_msbf_error_decreases_with_rank():
 @pytest.mark.slow
 def test_msbf_error_against_table_4():
     """§4.3, Table 4: MBF-s on the Example-1 FIO (elliptic phase) at n = 64 with a 16 x 16
-    centre.  Loose pin, like the Table 2 pin: within [1/5, 60] x the printed error at the
-    same r, and falling with r."""
+    centre.
+
+    1. Against the mathematics: the error lies between 0.8x and 4x the Eckart-Young floor
+       summed over the middle levels of every corona's factorization (the centre is exact).
+    2. Against the paper: at r = 20 the printed error is within 2x of that floor; at r = 12
+       it is 2-3x below it, a level no rank-r factorization on these trees reaches for iid
+       g (the paper does not state its input), so the comparison with the printed value
+       is loose there."""
     tab = np.loadtxt(os.path.join(GOLDEN, "table4_mbf_s.txt"))
-    n = 64
+    n, L = 64, 6
     S = sample_outputs(n * n, 256, seed=1)
     g = complex_normal(n * n, 1, seed=0)
-    u = D.direct_sum(P.kernel_fio_ellip, P.grid_x(n, 2), P.grid_omega(n, 2), g, rows=S)
+    X, W = P.grid_x(n, 2), P.grid_omega(n, 2)
+    u = D.direct_sum(P.kernel_fio_ellip, X, W, g, rows=S)
+    coronas, _ = MS.corona_sets(n, 16)
+    tails = {12: 0.0, 20: 0.0}
+    for t, idx in coronas:
+        Lt = 2 * ((L - t) // 2)
+        half = n / 2 ** (t + 1)
+        part = middle_level_tails(P.kernel_fio_ellip, X, W, P.uniform_tree(n, 2, Lt),
+                                  P.square_tree(W[idx], idx, -half, 2 * half, Lt), (12, 20))
+        for r in tails:
+            tails[r] += part[r]
+    floor = floor_from_tails(tails, n * n, n * n)
     errs = {}
     for r in (12, 20):
         m = MS.build(P.kernel_fio_ellip, n, r=r, n_center=16)
         errs[r] = D.rel_err(MS.SparseMsBF(m).apply(g)[:, S], u)
+        assert 0.8 * floor[r] < errs[r] < 4 * floor[r], (r, errs[r], floor[r])
         paper = tab[(tab[:, 0] == n) & (tab[:, 1] == r), 2][0]
-        assert paper / 5 < errs[r] < paper * 60, (r, errs[r], paper)
+        assert floor[r] / 4 < paper < 2 * floor[r], (r, paper, floor[r])
     assert errs[20] < errs[12]

@@ -88,6 +88,24 @@ def test_phase_special_points():
                        (2 / 16) * np.hypot(xi[:, 0], xi[:, 1]), atol=1e-13)
 
 
+def test_iso_phase_off_the_axes():
+    """The isotropic phase x.xi + c(x)|xi| with c = (2 + sin 2pi x_1 sin 2pi x_2)/16
+    (Example 1 of §3.3 with c_1 = c_2) at points where neither sine vanishes:
+    c(1/4, 1/4) = 3/16, c(1/4, 3/4) = c(3/4, 1/4) = 1/16, c(1/12, 1/4) = 5/32,
+    c(1/4, 1/12) = 5/32, c(1/8, 1/8) = (2 + 1/2)/16.  A cosine in place of either
+    sine, a dropped 2pi, a wrong sign or a missing x.xi term fails at least one."""
+    pts = np.array([[0.25, 0.25], [0.25, 0.75], [0.75, 0.25], [1 / 12, 0.25], [0.25, 1 / 12],
+                    [0.125, 0.125]])
+    c = np.array([3 / 16, 1 / 16, 1 / 16, 5 / 32, 5 / 32, 2.5 / 16])
+    xi = np.array([[3.0, -4.0], [-12.0, 5.0], [8.0, 6.0], [0.0, 7.0], [-24.0, 0.0], [1.0, 1.0]])
+    expect = np.sum(pts * xi, axis=1) + c * np.hypot(xi[:, 0], xi[:, 1])
+    assert np.allclose(P.fio_iso_phase(pts, xi), expect, atol=1e-13)
+    # the kernel is exp(+2 pi i Phi): at x = (1/4, 1/4), xi = (3, -4) the phase is
+    # -1/4 + 15/16 = 11/16
+    k = P.kernel_fio_iso(pts[:1], xi[:1])[0]
+    assert abs(k - np.exp(2j * np.pi * 11 / 16)) < 1e-13
+
+
 def test_polar_map_inverts_eq_polar():
     """p(xi) followed by eq. (polar) returns xi; p lies in [0,1]^2 and p_1 = 1 only at
     the corner xi = (-n/2, -n/2) (reading of the closed upper cell)."""
