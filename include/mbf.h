@@ -106,10 +106,11 @@ typedef struct mbf_build_opts {
   int32_t reserved;
   /* Optional checkpoint (NULL: none).  If a factor file exists at this path it is loaded
    * instead of building (its dim, L, sizes, Omega point set and ranks <= r are checked
-   * against the problem: MBF_ERR_INVALID on a mismatch); otherwise the factors are built
-   * and written there.  The file does not record the kernel, the seed or the options:
-   * name one file per (kernel, seed, options).  mbf_build_msbf uses `path`.t<k> for
-   * corona k. */
+   * against the problem, and 16 kernel entries recorded in `path`.kernel against the
+   * entry function: MBF_ERR_INVALID on a mismatch or a missing record); otherwise the
+   * factors are built and written there with their kernel record.  The seed and the
+   * options are not recorded: name one file per (seed, options).  mbf_build_msbf uses
+   * `path`.t<k> for corona k. */
   const char* factor_file;
 } mbf_build_opts_t;
 
@@ -173,7 +174,8 @@ mbf_status mbf_factors_load(const char* path, mbf_factors_h* out);
  * layout on the current CUDA device and return a resident operator.  The factor
  * arrays are only read during the call. */
 mbf_status mbf_op_create(const mbf_factors_t* f, mbf_op_t* out);
-/* mbf_build_factors + mbf_op_create + mbf_factors_destroy. */
+/* mbf_build_factors + mbf_op_create + mbf_factors_destroy, then the error estimate
+ * below on 256 sampled outputs (needs the device; kept for mbf_op_info). */
 mbf_status mbf_build_from_entries(const mbf_problem_t* prob, mbf_entry_fn fn, void* ctx,
                                   const mbf_build_opts_t* opts, mbf_op_t* out);
 mbf_status mbf_op_destroy(mbf_op_t op);
@@ -194,8 +196,25 @@ typedef struct mbf_op_info {
   int64_t bytes_tensor;         /* device bytes of its split-bf16 tiles                   */
   int32_t tensor_smem, tensor_slots;  /* its shared memory per CTA and A-ring depth      */
   char tensor_unavailable[128]; /* why not, if tensor_ok == 0                             */
+  double eps;                   /* error estimate against the direct sum (§3.3), -1 if none */
+  int32_t eps_samples;          /* sampled outputs it was taken on                          */
+  int32_t reserved_eps;
 } mbf_op_info_t;
 mbf_status mbf_op_info(mbf_op_t op, mbf_op_info_t* info);
+
+/* Error estimate of the numerical sections (§3.3, §4.3): the relative L2 error
+ *     e = sqrt( sum_{x in S} |u_f(x) - u(x)|^2 / sum_{x in S} |u(x)|^2 )
+ * of the operator's result u_f = K_f g against the direct sum u = K g (§1.1, eq. kernel)
+ * on n_samples distinct output points S.  g has iid complex standard normal entries on
+ * the Omega points the operator covers (zero elsewhere); g and S are drawn from `seed`
+ * by a counter-based generator (splitmix64).  u_f is one FP32 apply on the current
+ * device on `stream` (synchronized; a device wait that gave up returns MBF_ERR_TIMEOUT);
+ * u(x) is summed in FP64 on the host from entries of fn (as for the builder; called from
+ * several threads).  The operator must be built on the grids X, Omega of eqs. (X),
+ * (Omega) with n^d points.  Allocates two vectors on the device for the call.  The result
+ * is written to *eps (if not NULL) and kept for mbf_op_info. */
+mbf_status mbf_op_estimate_error(mbf_op_t op, mbf_entry_fn fn, void* ctx, int32_t n_samples,
+                                 uint64_t seed, void* stream, double* eps);
 
 /* u = K_f g (forward) for nrhs vectors.  g: device [nrhs][n_in] complex64, u: device
  * [nrhs][n_out] complex64 (fully overwritten).  Asynchronous on `stream`.  Calls on
@@ -239,6 +258,22 @@ mbf_status mbf_apply_static(mbf_op_t op, const void* g, void* u, int64_t nrhs, v
 /* Synchronize `stream` and return MBF_ERR_TIMEOUT if a device wait of a previous
  * apply on this operator ran out of time (and clear the flag), else MBF_OK. */
 mbf_status mbf_op_check(mbf_op_t op, void* stream);
+/* Failure-detection test hook (no counterpart in the paper; off by default).  With
+ * stage >= 0, later FP32 SIMT applies on this operator make the dependency wait of
+ * group 0 of that stage (execution order, 1 .. n_stages - 1) wait for one producer more
+ * than the plan has, so that the wait can only end by running out of time; wait_ns > 0
+ * shortens every wait of those applies on a dependency counter, the pass barrier or a
+ * chunk copy from 2 s to wait_ns.  The apply then stops early, its output undefined,
+ * and mbf_op_check reports MBF_ERR_TIMEOUT, as for a real stall.  stage = -1 and
+ * wait_ns = 0 restore normal applies.  MBF_ERR_INVALID for a stage beyond the plan or a
+ * negative limit. */
+mbf_status mbf_op_debug_stall(mbf_op_t op, int32_t stage, int64_t wait_ns);
+/* Allocation-failure test hook (no counterpart in the paper; off by default).  With
+ * after >= 0, the library's operator allocations (mbf_op_create and the workspaces an
+ * apply allocates on first use) succeed `after` more times, then one fails as if the
+ * device were out of memory -- the call reports MBF_ERR_OOM and frees what it had
+ * taken -- and the hook turns itself off.  after = -1 turns it off.  Process-wide. */
+mbf_status mbf_debug_fail_alloc(int64_t after);
 
 /* Kernel timing, a measurement aid (no counterpart in the paper; off by default).
  * While enabled, every kernel an apply on this operator launches is bracketed by two

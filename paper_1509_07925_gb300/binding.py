@@ -62,7 +62,8 @@ class OpInfo(C.Structure):
                 ("smem", C.c_int32), ("nnz_stage", C.c_int64 * 32), ("nnz_leaf_u", C.c_int64),
                 ("tensor_ok", C.c_int32), ("tensor_stages", C.c_int32), ("bytes_tensor", C.c_int64),
                 ("tensor_smem", C.c_int32), ("tensor_slots", C.c_int32),
-                ("tensor_unavailable", C.c_char * 128)]
+                ("tensor_unavailable", C.c_char * 128), ("eps", C.c_double),
+                ("eps_samples", C.c_int32), ("reserved_eps", C.c_int32)]
 
 
 PROFILE_KINDS = 8
@@ -123,12 +124,16 @@ SIGNATURES = {
                                          C.POINTER(BuildOpts), C.POINTER(C.c_void_p)]),
     "mbf_op_destroy": (C.c_int, [C.c_void_p]),
     "mbf_op_info": (C.c_int, [C.c_void_p, C.POINTER(OpInfo)]),
+    "mbf_op_estimate_error": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_uint64,
+                                        C.c_void_p, C.POINTER(C.c_double)]),
     "mbf_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p]),
     "mbf_apply_adjoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32,
                                     C.c_void_p]),
     "mbf_apply_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32,
                                  C.c_void_p]),
     "mbf_op_check": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "mbf_op_debug_stall": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64]),
+    "mbf_debug_fail_alloc": (C.c_int, [C.c_int64]),
     "mbf_apply_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "mbf_op_set_profiling": (C.c_int, [C.c_void_p, C.c_int32]),
     "mbf_op_tune": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(TuneResult)]),
@@ -325,6 +330,15 @@ class Operator:
         _check(lib().mbf_op_info(self._h, C.byref(inf)))
         return inf
 
+    def estimate_error(self, kernel="dft", n_samples=256, seed=1, stream: int = 0) -> float:
+        """Relative error against the direct sum on sampled outputs (mbf_op_estimate_error);
+        kernel: a built-in name or an entry-function address."""
+        fn = builtin_kernel(kernel) if isinstance(kernel, str) else kernel
+        e = C.c_double()
+        _check(lib().mbf_op_estimate_error(self._h, fn, None, n_samples, seed, C.c_void_p(stream),
+                                           C.byref(e)))
+        return e.value
+
     def apply(self, g_ptr: int, u_ptr: int, nrhs: int, precision=MBF_PREC_AUTO, stream: int = 0):
         """u = K_f g on device pointers (complex64, [nrhs][N])."""
         _check(lib().mbf_apply(self._h, C.c_void_p(g_ptr), C.c_void_p(u_ptr), nrhs, precision,
@@ -361,6 +375,10 @@ class Operator:
 
     def check(self, stream: int = 0):
         _check(lib().mbf_op_check(self._h, C.c_void_p(stream)))
+
+    def debug_stall(self, stage: int, wait_ns: int = 0):
+        """Failure-detection test hook (mbf_op_debug_stall); stage=-1, wait_ns=0 turn it off."""
+        _check(lib().mbf_op_debug_stall(self._h, stage, wait_ns))
 
     def close(self):
         if self._h:

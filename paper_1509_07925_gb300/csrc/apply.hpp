@@ -26,6 +26,13 @@ struct ApplyArgs {
   int* status;             // 0 = ok; nonzero = a device wait ran out of time (sticky)
   int32_t nrhs, n_pass, n_slots;
   int32_t accumulate;      // 1: out += result (the caller initialised out), 0: out = result
+  // Failure-detection test hook (mbf_op_debug_stall); zero leaves the apply unchanged.
+  // stall_stage1 = 1 + s: the dependency wait of group 0 of stage s (execution order)
+  // waits for one more producer than exists, so that it can only end by running out of
+  // time.  wait_ns > 0: every wait on a dependency counter, the pass barrier or a chunk
+  // gives up after wait_ns instead of kTimeoutNs.
+  uint64_t wait_ns;
+  int32_t stall_stage1, stall_pad_;
   Plan plan;
 };
 

@@ -289,6 +289,7 @@ __device__ __forceinline__ void chunk_axpy_ul(const float* __restrict__ re, cons
 
 template <int NRB, bool ADJ>
 __global__ void __launch_bounds__(Cfg<NRB>::W * 32, 1) bf_apply_simt(const __grid_constant__ ApplyArgs a) {
+  const uint64_t wait_lim = a.wait_ns ? a.wait_ns : kTimeoutNs;
   constexpr int W = Cfg<NRB>::W, D = Cfg<NRB>::D;
   extern __shared__ __align__(1024) uint8_t smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -374,7 +375,7 @@ __global__ void __launch_bounds__(Cfg<NRB>::W * 32, 1) bf_apply_simt(const __gri
       if (!mbar_try(&full[slot], ph)) {
         const uint64_t t0 = gtimer();
         while (!mbar_try(&full[slot], ph)) {
-          if (gtimer() - t0 > kTimeoutNs) {
+          if (gtimer() - t0 > wait_lim) {
             got = 0;
             if (!*abort) set_status(a.status, abort, ST_FULL_TIMEOUT);
             break;
@@ -412,7 +413,7 @@ __global__ void __launch_bounds__(Cfg<NRB>::W * 32, 1) bf_apply_simt(const __gri
           const uint64_t t0 = gtimer();
           while (*reinterpret_cast<volatile unsigned*>(a.barrier) < target) {
             if (*reinterpret_cast<volatile int*>(a.status) != 0) { *abort = 1; break; }
-            if (gtimer() - t0 > kTimeoutNs) { set_status(a.status, abort, ST_BARRIER_TIMEOUT); break; }
+            if (gtimer() - t0 > wait_lim) { set_status(a.status, abort, ST_BARRIER_TIMEOUT); break; }
             __nanosleep(20);
           }
           __threadfence();
@@ -508,11 +509,12 @@ __global__ void __launch_bounds__(Cfg<NRB>::W * 32, 1) bf_apply_simt(const __gri
           // producing groups of the previous stage (each adds 1 per segment)
           if (lane == 0) {
             const unsigned* cp = cnt_in + g;
-            if (ld_acquire(cp) < need) {
+            const unsigned need_g = need + (e + 1 == a.stall_stage1 && g == 0 ? 1u : 0u);
+            if (ld_acquire(cp) < need_g) {
               const uint64_t t0 = gtimer();
-              while (ld_acquire(cp) < need) {
+              while (ld_acquire(cp) < need_g) {
                 if (*abort || *reinterpret_cast<volatile int*>(a.status) != 0) { *abort = 1; break; }
-                if (gtimer() - t0 > kTimeoutNs) { set_status(a.status, abort, ST_DEP_TIMEOUT); break; }
+                if (gtimer() - t0 > wait_lim) { set_status(a.status, abort, ST_DEP_TIMEOUT); break; }
                 __nanosleep(32);
               }
             }

@@ -12,6 +12,14 @@
 //   checksum                        uint64, over every byte before it
 // The file is written under a temporary name and renamed when complete, so a file with
 // the final name is never a partial write.
+//
+// A file written by a build (build_or_load) has a kernel record beside it, `path`.kernel:
+// magic "MBFKERN1", count, dim, then count entries K(x, xi) of the kernel it was built
+// from (natural x index, natural xi index, Re, Im) and a checksum.  Loading the file for
+// a build evaluates the build's entry function at the same points and rejects the file if
+// they differ, so that factors of one kernel are never taken for another with the same
+// grids and trees (a 2-D DFT and a 2-D FIO without polar transform, for instance).
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -246,6 +254,90 @@ FactorSet load_factors(const std::string& path) {
   return fs;
 }
 
+namespace {
+
+constexpr char kKernMagic[8] = {'M', 'B', 'F', 'K', 'E', 'R', 'N', '1'};
+constexpr int kKernEntries = 16;
+
+struct KernelEntry {
+  int64_t x, xi;
+  double re, im;
+};
+
+// The sampled entries: fixed positions in tree order (spread by two primes), the
+// kernel evaluated through the entry function at their grid coordinates (eqs. X, Omega).
+std::vector<KernelEntry> kernel_entries(const mbf_problem_t& prob, const FactorSet& fs, mbf_entry_fn fn, void* ctx) {
+  std::vector<KernelEntry> e;
+  if (!fn || fs.n_out < 1 || fs.n_w < 1) return e;
+  const int d = prob.dim, n = prob.n;
+  for (int k = 0; k < kKernEntries; ++k) {
+    KernelEntry q{};
+    q.x = fs.x_perm[size_t((int64_t(k) * 7919) % fs.n_out)];
+    q.xi = fs.w_perm[size_t((int64_t(k) * 104729 + 3) % fs.n_w)];
+    double x[3], xi[3], out[2];
+    int64_t a = q.x, b = q.xi;
+    for (int t = d - 1; t >= 0; --t) {
+      x[t] = double(a % n) / n;
+      xi[t] = double(b % n) - n / 2;
+      a /= n;
+      b /= n;
+    }
+    fn(x, 1, xi, 1, d, out, ctx);
+    q.re = out[0];
+    q.im = out[1];
+    e.push_back(q);
+  }
+  return e;
+}
+
+void save_kernel_record(const std::string& path, int dim, const std::vector<KernelEntry>& e) {
+  const std::string tmp = path + ".tmp";
+  {
+    File file;
+    file.f = std::fopen(tmp.c_str(), "wb");
+    if (!file.f) fail(MBF_ERR_IO, "cannot create " + tmp);
+    Writer w(file.f, tmp);
+    const int32_t head[2] = {int32_t(e.size()), dim};
+    w.put(kKernMagic, 8);
+    w.put(head, sizeof head);
+    w.put(e.data(), e.size() * sizeof(KernelEntry));
+    const uint64_t sum = w.sum();
+    if (std::fwrite(&sum, 1, 8, file.f) != 8) fail(MBF_ERR_IO, "write failed: " + tmp);
+    const int rc = std::fclose(file.f);
+    file.f = nullptr;
+    if (rc != 0) {
+      std::remove(tmp.c_str());
+      fail(MBF_ERR_IO, "write failed: " + tmp);
+    }
+  }
+  if (std::rename(tmp.c_str(), path.c_str()) != 0) {
+    std::remove(tmp.c_str());
+    fail(MBF_ERR_IO, "cannot rename " + tmp + " to " + path);
+  }
+}
+
+std::vector<KernelEntry> load_kernel_record(const std::string& path) {
+  File file;
+  file.f = std::fopen(path.c_str(), "rb");
+  if (!file.f)
+    fail(MBF_ERR_INVALID, "factor file has no kernel record (" + path +
+                              "): it was not written by a build, so its kernel cannot be checked");
+  Reader r(file.f, path);
+  char magic[8];
+  int32_t head[2];
+  r.get(magic, 8);
+  r.get(head, sizeof head);
+  if (std::memcmp(magic, kKernMagic, 8) != 0 || head[0] < 0 || head[0] > 1024)
+    fail(MBF_ERR_IO, "corrupt kernel record: " + path);
+  std::vector<KernelEntry> e = r.vec<KernelEntry>(head[0]);
+  const uint64_t expect = r.sum();
+  uint64_t stored = 0;
+  if (std::fread(&stored, 1, 8, file.f) != 8 || stored != expect) fail(MBF_ERR_IO, "corrupt kernel record: " + path);
+  return e;
+}
+
+}  // namespace
+
 FactorSet build_or_load(const mbf_problem_t& prob, mbf_entry_fn fn, void* ctx, const mbf_build_opts_t& opts) {
   const char* path = opts.factor_file;
   if (!path || !*path) return build_factors(prob, fn, ctx, opts);
@@ -263,9 +355,18 @@ FactorSet build_or_load(const mbf_problem_t& prob, mbf_entry_fn fn, void* ctx, c
     if (fs.w_perm != wt.perm || fs.w_off != wt.off) fail(MBF_ERR_INVALID, who + "Omega tree or point set");
     for (int l = fs.L / 2; l <= fs.L; ++l)
       if (fs.RU[size_t(l)] > prob.r || fs.RV[size_t(l)] > prob.r) fail(MBF_ERR_INVALID, who + "ranks above r");
+    // and the kernel: the recorded entries against the entry function of this build
+    const std::vector<KernelEntry> rec = load_kernel_record(std::string(path) + ".kernel");
+    const std::vector<KernelEntry> now = kernel_entries(prob, fs, fn, ctx);
+    bool same = rec.size() == now.size();
+    for (size_t k = 0; same && k < rec.size(); ++k)
+      same = rec[k].x == now[k].x && rec[k].xi == now[k].xi &&
+             std::abs(rec[k].re - now[k].re) + std::abs(rec[k].im - now[k].im) <= 1e-9;
+    if (!same) fail(MBF_ERR_INVALID, who + "kernel entries differ from the kernel record");
     return fs;
   }
   FactorSet fs = build_factors(prob, fn, ctx, opts);
+  save_kernel_record(std::string(path) + ".kernel", prob.dim, kernel_entries(prob, fs, fn, ctx));
   save_factors(fs.view(), path);
   return fs;
 }

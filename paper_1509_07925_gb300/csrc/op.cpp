@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -28,11 +29,32 @@ void cuda_check(cudaError_t e, const char* what) {
   if (e != cudaSuccess) fail(MBF_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// Failure-detection test hook (mbf_debug_fail_alloc): while >= 0, the number of device
+// allocations of this file still allowed to succeed; the next one fails as if the
+// device were out of memory.
+std::atomic<int64_t> g_alloc_budget{-1};
+
+template <class T>
+cudaError_t dev_alloc(T** p, size_t bytes) {
+  int64_t k = g_alloc_budget.load();
+  while (k >= 0) {
+    if (g_alloc_budget.compare_exchange_weak(k, k - 1)) {
+      if (k == 0) {
+        *p = nullptr;
+        g_alloc_budget.store(-1);
+        return cudaErrorMemoryAllocation;
+      }
+      break;
+    }
+  }
+  return cudaMalloc(p, bytes);
+}
+
 template <class T>
 T* dev_upload(const std::vector<T>& v, const char* what) {
   T* p = nullptr;
   const size_t bytes = std::max<size_t>(sizeof(T), v.size() * sizeof(T));
-  cudaError_t e = cudaMalloc(&p, bytes);
+  cudaError_t e = dev_alloc(&p, bytes);
   if (e != cudaSuccess) fail(MBF_ERR_OOM, std::string("cudaMalloc ") + what + ": " + cudaGetErrorString(e));
   if (!v.empty()) cuda_check(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice), what);
   return p;
@@ -528,9 +550,9 @@ mbf_op_s* op_create(const mbf_factors_t& f) {
     op->d_w_perm = dev_upload(to32(f.w_perm, std::max<int64_t>(f.n_w, 1)), "w_perm");
     op->d_w_off = dev_upload(to32(f.w_off, nL + 1), "w_off");
     const size_t vbytes = size_t(op->plan.n_stages) * size_t(op->positions) * 4 * sizeof(float2);
-    if (cudaMalloc(&op->d_bufs, vbytes) != cudaSuccess) fail(MBF_ERR_OOM, "cudaMalloc workspace");
-    if (cudaMalloc(&op->d_barrier, 256 + counter_bytes(op->plan)) != cudaSuccess ||
-        cudaMalloc(&op->d_status, 256) != cudaSuccess)
+    if (dev_alloc(&op->d_bufs, vbytes) != cudaSuccess) fail(MBF_ERR_OOM, "cudaMalloc workspace");
+    if (dev_alloc(&op->d_barrier, 256 + counter_bytes(op->plan)) != cudaSuccess ||
+        dev_alloc(&op->d_status, 256) != cudaSuccess)
       fail(MBF_ERR_OOM, "cudaMalloc barrier");
     cuda_check(cudaMemset(op->d_status, 0, 256), "cudaMemset status");
     for (int nrb : {1, 2, 4}) cuda_check(simt_config(nrb, &op->grid, &op->ns[nrb], &op->smem[nrb]), "simt_config");
@@ -663,7 +685,7 @@ void apply_tc(mbf_op_s* op, const float2* g, float2* u, int64_t nrhs, cudaStream
   const int64_t vec_bytes = tc_vec_bytes(op);
   tc_prepare(op);
   if (tf32 && !op->d_tc_arena_tf32) {   // first TF32 apply: convert the tiles (kept, like the split ones)
-    if (cudaMalloc(&op->d_tc_arena_tf32, size_t(op->tc_bytes)) != cudaSuccess) {
+    if (dev_alloc(&op->d_tc_arena_tf32, size_t(op->tc_bytes)) != cudaSuccess) {
       op->d_tc_arena_tf32 = nullptr;
       fail(MBF_ERR_OOM, "cudaMalloc TF32 tiles");
     }
@@ -762,7 +784,7 @@ void apply_tc_adj(mbf_op_s* op, const float2* u, float2* g, int64_t nrhs, cudaSt
   const int64_t vec_bytes = tc_vec_bytes(op);
   tc_prepare(op);
   if (!op->d_tc_arena_adj) {   // first adjoint apply: conjugate-transpose the tiles (kept)
-    if (cudaMalloc(&op->d_tc_arena_adj, size_t(op->tc_bytes)) != cudaSuccess) {
+    if (dev_alloc(&op->d_tc_arena_adj, size_t(op->tc_bytes)) != cudaSuccess) {
       op->d_tc_arena_adj = nullptr;
       fail(MBF_ERR_OOM, "cudaMalloc adjoint tiles");
     }
@@ -894,6 +916,8 @@ void apply_impl(mbf_op_s* op, const void* in, void* out, int64_t nrhs, int32_t p
   a.n_slots = op->ns[nrb];
   a.plan = op->plan;
   a.accumulate = accumulate ? 1 : 0;
+  a.wait_ns = op->dbg_wait_ns;
+  a.stall_stage1 = op->dbg_stall_stage1;
   if (adj && op->n_w < op->n_in && !accumulate)
     cuda_check(cudaMemsetAsync(out, 0, size_t(nrhs) * size_t(op->n_in) * sizeof(float2), st), "cudaMemsetAsync");
   cudaEvent_t e0 = prof_begin(op, st);
@@ -952,11 +976,11 @@ void tc_prepare(mbf_op_s* op) {
   if (op->d_tc_bufs || !op->tc_unavailable.empty()) return;
   const int S = op->tcplan.n_stages;
   const int64_t vec_bytes = tc_vec_bytes(op);
-  if (cudaMalloc(&op->d_tc_bufs, size_t(S + 1) * size_t(vec_bytes)) != cudaSuccess)
+  if (dev_alloc(&op->d_tc_bufs, size_t(S + 1) * size_t(vec_bytes)) != cudaSuccess)
     fail(MBF_ERR_OOM, "cudaMalloc tensor-path workspace");
-  if (cudaMalloc(&op->d_tc_counters, tc_counter_bytes(op->tcplan)) != cudaSuccess)
+  if (dev_alloc(&op->d_tc_counters, tc_counter_bytes(op->tcplan)) != cudaSuccess)
     fail(MBF_ERR_OOM, "cudaMalloc tensor-path counters");
-  if (cudaMalloc(&op->d_tc_gt, size_t(std::max<int64_t>({op->n_w, op->n_out, 1})) * kTcNR * sizeof(float2)) != cudaSuccess)
+  if (dev_alloc(&op->d_tc_gt, size_t(std::max<int64_t>({op->n_w, op->n_out, 1})) * kTcNR * sizeof(float2)) != cudaSuccess)
     fail(MBF_ERR_OOM, "cudaMalloc tensor-path input panel");
 }
 
@@ -1038,7 +1062,25 @@ mbf_status mbf_build_from_entries(const mbf_problem_t* prob, mbf_entry_fn fn, vo
     if (opts) o = *opts;
     FactorSet fs = build_or_load(*prob, fn, ctx, o);
     mbf_factors_t v = fs.view();
-    *out = op_create(v);
+    mbf_op_s* op = op_create(v);
+    fs = FactorSet{};
+    try {
+      // the §3.3 estimator on 256 sampled outputs, kept for mbf_op_info
+      estimate_error(op, fn, ctx, 256, o.seed ^ 0x6570735f65737469ull, nullptr);
+    } catch (...) {
+      op_free(op);
+      throw;
+    }
+    *out = op;
+  });
+}
+
+mbf_status mbf_op_estimate_error(mbf_op_t op, mbf_entry_fn fn, void* ctx, int32_t n_samples, uint64_t seed,
+                                 void* stream, double* eps) {
+  return guard([&] {
+    if (!op) fail(MBF_ERR_INVALID, "NULL operator");
+    const double e = estimate_error(op, fn, ctx, n_samples, seed, static_cast<cudaStream_t>(stream));
+    if (eps) *eps = e;
   });
 }
 
@@ -1075,6 +1117,8 @@ mbf_status mbf_op_info(mbf_op_t op, mbf_op_info_t* info) {
     info->tensor_smem = int(op->tc_smem);
     info->tensor_slots = op->tc_nsa;
     std::snprintf(info->tensor_unavailable, sizeof(info->tensor_unavailable), "%s", op->tc_unavailable.c_str());
+    info->eps = op->eps;
+    info->eps_samples = op->eps_samples;
   });
 }
 
@@ -1141,20 +1185,34 @@ mbf_status mbf_apply_host(mbf_op_t op, const void* g_host, void* u_host, int64_t
       cuda_check(cudaStreamSynchronize(st), "sync");
       cudaFree(op->d_stage_in);
       op->d_stage_in = nullptr;
-      if (cudaMalloc(&op->d_stage_in, in_b) != cudaSuccess) fail(MBF_ERR_OOM, "cudaMalloc staging");
+      if (dev_alloc(&op->d_stage_in, in_b) != cudaSuccess) fail(MBF_ERR_OOM, "cudaMalloc staging");
       op->stage_in_bytes = in_b;
     }
     if (out_b > op->stage_out_bytes) {
       cuda_check(cudaStreamSynchronize(st), "sync");
       cudaFree(op->d_stage_out);
       op->d_stage_out = nullptr;
-      if (cudaMalloc(&op->d_stage_out, out_b) != cudaSuccess) fail(MBF_ERR_OOM, "cudaMalloc staging");
+      if (dev_alloc(&op->d_stage_out, out_b) != cudaSuccess) fail(MBF_ERR_OOM, "cudaMalloc staging");
       op->stage_out_bytes = out_b;
     }
     cuda_check(cudaMemcpyAsync(op->d_stage_in, g_host, in_b, cudaMemcpyHostToDevice, st), "H2D");
     apply_impl(op, op->d_stage_in, op->d_stage_out, nrhs, precision, stream, false);
     cuda_check(cudaMemcpyAsync(u_host, op->d_stage_out, out_b, cudaMemcpyDeviceToHost, st), "D2H");
     cuda_check(cudaStreamSynchronize(st), "sync");
+  });
+}
+
+mbf_status mbf_debug_fail_alloc(int64_t after) {
+  return guard([&] { g_alloc_budget.store(after < 0 ? -1 : after); });
+}
+
+mbf_status mbf_op_debug_stall(mbf_op_t op, int32_t stage, int64_t wait_ns) {
+  return guard([&] {
+    if (!op) fail(MBF_ERR_INVALID, "NULL operator");
+    if (stage >= op->plan.n_stages) fail(MBF_ERR_INVALID, "stall stage beyond the plan");
+    if (wait_ns < 0) fail(MBF_ERR_INVALID, "negative wait limit");
+    op->dbg_stall_stage1 = stage >= 0 ? stage + 1 : 0;
+    op->dbg_wait_ns = uint64_t(wait_ns);
   });
 }
 

@@ -65,6 +65,12 @@ struct mbf_op_s {
   // staging for mbf_apply_host
   float2 *d_stage_in = nullptr, *d_stage_out = nullptr;
   size_t stage_in_bytes = 0, stage_out_bytes = 0;
+  // error estimate against the direct sum (mbf_op_estimate_error; -1 until made)
+  double eps = -1.0;
+  int32_t eps_samples = 0;
+  // failure-detection test hook of the FP32 SIMT apply (mbf_op_debug_stall)
+  int32_t dbg_stall_stage1 = 0;
+  uint64_t dbg_wait_ns = 0;
 };
 
 
@@ -78,4 +84,7 @@ int64_t tc_vec_bytes(const mbf_op_s* op);
 // accumulate adds the result into out (which the caller initialised).
 void apply_dev(mbf_op_s* op, const void* in, void* out, int64_t nrhs, int32_t precision, cudaStream_t st,
                bool adj, int grid, bool accumulate = false);
+// The error estimator of §3.3 (estimate.cpp); keeps the result in op->eps.
+double estimate_error(mbf_op_s* op, mbf_entry_fn fn, void* ctx, int32_t n_samples, uint64_t seed,
+                      cudaStream_t st);
 }  // namespace mbf

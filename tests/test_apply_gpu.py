@@ -133,3 +133,15 @@ def test_library_builder_end_to_end_small(bd):
     ud = D.direct_sum(P.kernel_fio_iso, X, W, g)
     eps = D.rel_err(uf, ud)
     assert D.rel_err(u, ud) <= eps + TOL_SIMT
+
+
+def test_error_estimate_of_an_exact_factorization(bd):
+    """At full rank the factorization is exact (§2.4: every truncation keeps all singular
+    values), so the §3.3 estimate is the FP32 rounding of the apply alone; with every
+    output sampled it equals the relative error against the full direct sum."""
+    hf = bd.HostFactors.build(2, 16, 4, 16, kernel="dft")   # 16-point middle-level nodes
+    op = bd.Operator(hf)
+    assert op.info().eps == -1.0
+    e = op.estimate_error("dft", n_samples=256, seed=3)
+    assert 0 < e <= 1e-5
+    op.close()

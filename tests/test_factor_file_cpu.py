@@ -170,3 +170,20 @@ def test_build_option_rejects_a_checkpoint_of_another_problem(bd, tmp_path):
     with pytest.raises(bd.MbfError) as e:
         bd.HostFactors.build(2, 16, 2, 8, factor_file=q, w_index=idx + 1, **kw)
     assert e.value.code == bd.MBF_ERR_INVALID and "point set" in str(e.value)
+
+
+def test_build_option_rejects_a_checkpoint_of_another_kernel(bd, tmp_path):
+    """A 2-D DFT and a 2-D FIO without polar transform share n, L, trees and ranks; the
+    kernel record written beside the file tells them apart, and a file without one
+    (written by mbf_factors_save, not by a build) is not taken for a build."""
+    p = tmp_path / "k.mbf"
+    bd.HostFactors.build(2, 16, 2, 8, kernel="dft", factor_file=p).close()
+    assert (tmp_path / "k.mbf.kernel").exists()
+    bd.HostFactors.build(2, 16, 2, 8, kernel="dft", factor_file=p).close()   # same kernel: loads
+    with pytest.raises(bd.MbfError) as e:
+        bd.HostFactors.build(2, 16, 2, 8, kernel="fio_iso", factor_file=p)
+    assert e.value.code == bd.MBF_ERR_INVALID and "kernel" in str(e.value)
+    (tmp_path / "k.mbf.kernel").unlink()
+    with pytest.raises(bd.MbfError) as e:
+        bd.HostFactors.build(2, 16, 2, 8, kernel="dft", factor_file=p)
+    assert e.value.code == bd.MBF_ERR_INVALID and "no kernel record" in str(e.value)

@@ -91,3 +91,20 @@ def test_full_size_tensor_adjoint_64_rhs(full):
     assert np.all(np.isfinite(ga))
     errs = [rel(ga[k], gf[k]) for k in range(64)]
     assert max(errs) <= 1e-4, max(errs)
+
+
+def test_library_error_estimate_agrees_with_the_oracle(full):
+    """mbf_op_estimate_error (the §3.3 estimator inside the library: one FP32 apply
+    against FP64 direct sums of the library's entry function on sampled outputs) agrees
+    with the oracle's estimate of the same operator -- its FP64 factor apply against
+    its own direct sum -- within the spread of a 256-point sample (different g and S);
+    the value is kept for mbf_op_info."""
+    op, fs, sb = full
+    e_lib = op.estimate_error(WL.kernel, n_samples=256, seed=11)
+    g = complex_normal(fs.n_in, 1, seed=WL.seed_g)
+    S = sample_outputs(fs.n_out, 256, seed=WL.seed_s)
+    X, W = P.grid_x(WL.n, WL.dim), P.grid_omega(WL.n, WL.dim)
+    e_orc = D.rel_err(sb.apply(g)[:, S], D.direct_sum(P.KERNELS[WL.kernel], X, W, g, rows=S))
+    assert 0.8 < e_lib / e_orc < 1.25, (e_lib, e_orc)
+    inf = op.info()
+    assert inf.eps == e_lib and inf.eps_samples == 256

@@ -8,10 +8,11 @@ that a failure here cannot hide any other test; it also passes on its own in a
 fresh process (every fixture is local to this module).
 
 Checks, through the C ABI: two calls in a row give the same result as mbf_apply
-within the FP32 tolerance of the other GPU tests (relative L2 <= 1e-5), for two
-operators of different size in turn (so the second call sees the first one's
-leftover scratch), and a problem whose workspace exceeds the array is rejected
-with MBF_ERR_INVALID without running.
+and as the CPU oracle's FP64 apply of the same factors, within the FP32 tolerance
+of the other GPU tests (relative L2 <= 1e-5 per RHS), for operators of different
+size in turn (so each call sees the previous one's leftover scratch), and a
+problem whose workspace exceeds the array is rejected with MBF_ERR_INVALID
+without running.
 """
 import ctypes as C
 
@@ -20,7 +21,9 @@ import pytest
 
 from mbf_synth import complex_normal
 
-from gpu_util import import_factors, oracle_case, rel
+from oracle import bf as B
+
+from gpu_util import export_factors, import_factors, oracle_case, rel
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -57,15 +60,17 @@ def _run(bd, fn, op, g, nrhs, n_out):
                                        (("fio_iso", 64, 2, 4, 24, "polar"), 3),
                                        (("dft", 8, 3, 2, 16, "none"), 5)])
 def test_static_apply_matches_apply_twice(bd, case, nrhs):
-    fs, _ = oracle_case(*case)
+    fs, sb = oracle_case(*case)
     op = bd.Operator(import_factors(bd, fs))
     g = complex_normal(fs.n_in, nrhs, seed=21)
     ref = _run(bd, "apply", op, g, nrhs, fs.n_out)
+    exact = sb.apply(np.ascontiguousarray(g, dtype=np.complex64).astype(np.complex128))
     for _ in range(2):
         out = _run(bd, "static", op, g, nrhs, fs.n_out)
         assert np.all(np.isfinite(out))
         for k in range(nrhs):
             assert rel(out[k], ref[k]) <= TOL_SIMT
+            assert rel(out[k], exact[k]) <= TOL_SIMT
     op.close()
 
 
@@ -86,6 +91,10 @@ def test_static_apply_rejects_oversized_workspace(bd):
     assert torch.all(u == 3.0)            # nothing ran
     gh = complex_normal(n, 1, seed=2)
     ref = _run(bd, "apply", op, gh, 1, n)
-    out = _run(bd, "static", op, gh, 1, n)
-    assert rel(out[0], ref[0]) <= TOL_SIMT
+    exact = B.SparseBF(export_factors(hf.arrays())).apply(
+        np.ascontiguousarray(gh, dtype=np.complex64).astype(np.complex128))
+    for _ in range(2):
+        out = _run(bd, "static", op, gh, 1, n)
+        assert rel(out[0], ref[0]) <= TOL_SIMT
+        assert rel(out[0], exact[0]) <= TOL_SIMT
     op.close()
