@@ -49,13 +49,14 @@ enum DeviceStatus : int {
 // Vectors between the tensor-core stages are "split blocks": block P of a level holds
 // the R8 coefficients of one tree-node pair for the kTcNR right-hand sides of a panel
 // as bf16 pairs hi = bf16(x), lo = bf16(x - hi), laid out as the MMA's K-major A
-// operand with the real and imaginary parts stacked on M (rows n and 64 + n):
-//   byte (hl, k, ri, n) = hl R8 256 + (k / 8) 2048 + (8 ri + n / 8) 128 + (n % 8) 16 + (k % 8) 2.
+// operand with the real and imaginary parts of RHS n interleaved on M (rows
+// m = 2 n + ri, ri = 0 real, 1 imaginary):
+//   byte (hl, k, m) = hl R8 256 + (k / 8) 2048 + (m / 8) 128 + (m % 8) 16 + (k % 8) 2.
 // A consumer copies each hi / lo half of a block into shared memory as it is.
 constexpr int kTcNR = 64;   // RHS per tensor-core panel
 MBF_HD int64_t split_block_bytes(int R8) { return int64_t(R8) * kTcNR * 8; }
 // With TF32 operands the same block holds FP32 (TF32-rounded) values instead, byte
-//   (k, ri, n) = (k / 4) 2048 + (8 ri + n / 8) 128 + (n % 8) 16 + (k % 4) 4
+//   (k, m) = (k / 4) 2048 + (m / 8) 128 + (m % 8) 16 + (k % 4) 4
 // (the MMA's K-major A operand for 32-bit types): the same R8 x 512 bytes.
 
 struct TCArgs {

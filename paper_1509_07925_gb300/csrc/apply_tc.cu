@@ -4,11 +4,13 @@
 // Every group product of a G^l / (H^l)^* level, Y = T X with T complex (M_t x K_t) and X
 // complex (K_t x 64), is computed transposed, Y^T = X^T T^T, on split-BF16 operands
 // (T = T_hi + T_lo, X = X_hi + X_lo, products hi*hi + hi*lo + lo*hi, FP32 accumulation).
-// The MMA's A operand stacks the real and imaginary parts of X^T on M (rows n and
-// 64 + n: M = 128), its B operand is one plane of T (N = M_t), so two accumulators
-//     D1 = [X_re^T; X_im^T] T_re^T,     D2 = [X_re^T; X_im^T] T_im^T
-// give Y_re^T = D1[n] - D2[64 + n] and Y_im^T = D2[n] + D1[64 + n].  With the tile's Re
-// and Im planes adjacent, D1 | D2 is one MMA of N = 2 M_t: three MMAs per K = 16.
+// The MMA's A operand interleaves the real and imaginary parts of X^T on M (row 2 n is
+// X_re[:, n], row 2 n + 1 is X_im[:, n]: M = 128), its B operand is one plane of T
+// (N = M_t), so two accumulators
+//     D1 = A T_re^T,     D2 = A T_im^T
+// give Y_re^T[n] = D1[2n] - D2[2n + 1] and Y_im^T[n] = D2[2n] + D1[2n + 1]: the two lanes
+// of an output pair are neighbours in one warp.  With the tile's Re and Im planes
+// adjacent, D1 | D2 is one MMA of N = 2 M_t: three MMAs per K = 16.
 // The vectors between stages are kept as split blocks (apply.hpp), so a group's X is
 // two contiguous runs per input block.
 //
@@ -21,8 +23,8 @@
 //              threads copy its c blocks into a panel buffer with cp.async and drop
 //              the consumed blocks from L2;
 //   warps 4-7, 8-11   epilogue sets, one per accumulator set: read the accumulators
-//              (tcgen05.ld), pair the halves through shared memory, split and store the
-//              group's output blocks, and hand them to
+//              (tcgen05.ld, the next columns' loads in flight), pair the halves by warp
+//              shuffles, split and store the group's output blocks, and hand them to
 //   warp 12    the signal warp, which fences and counts them in for the consumers.
 // The (V^L)^* and U^L leaf products run before and after it (leaf kernels below).
 // Every wait is bounded; on a timeout the status word is set and all roles drain.
@@ -146,18 +148,25 @@ __device__ __forceinline__ bool elect_one() {
   return pred != 0;
 }
 
-// 16 consecutive TMEM columns of this thread's lane (one row of the accumulator).
+// 16 consecutive TMEM columns of this thread's lane (one row of the accumulator),
+// written straight into the 16 FP32 registers (b32 operands take any 32-bit register).
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]), "=f"(v[8]),
+        "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]), "=f"(v[15])
       : "r"(taddr));
-#pragma unroll
-  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// Uses of registers written by tcgen05.ld must not move above the tcgen05.wait::ld that
+// completes them: after the wait, each register passes through an empty asm that the
+// compiler must assume rewrites it (volatile asms keep their order).
+__device__ __forceinline__ void tmem_hold(float (&x)[16], float (&y)[16]) {
+#pragma unroll
+  for (int j = 0; j < 16; ++j) asm volatile("" : "+f"(x[j]));
+#pragma unroll
+  for (int j = 0; j < 16; ++j) asm volatile("" : "+f"(y[j]));
+}
 
 // Two floats -> bf16x2 (round to nearest even), the first in the low half.
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo_half, float hi_half) {
@@ -224,8 +233,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
   const uint32_t x_buf = 2u * uint32_t(a.kpad_max) * 256u;      // hi + lo halves of a panel
   uint8_t* aring = smem;
   uint8_t* xbuf = aring + size_t(nsa) * a_slot;
-  float* xch = reinterpret_cast<float*>(xbuf + size_t(nxb) * x_buf);   // [set][2][kTcChunk][128]
-  uint64_t* afull = reinterpret_cast<uint64_t*>(xch + size_t(nsets) * 2 * kTcChunk * 128);
+  uint64_t* afull = reinterpret_cast<uint64_t*>(xbuf + size_t(nxb) * x_buf);
   uint64_t* aempty = afull + nsa;
   uint64_t* xfull = aempty + nsa;
   uint64_t* xempty = xfull + 2;
@@ -484,15 +492,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
     }
   } else if (warp >= 4 && (warp - 4) / 4 < nsets) {
     // ---------------------------------------------------------------- epilogue sets
+    // TMEM lane tl is row tl of the panel: RHS n = tl / 2, real (ri = 0) or imaginary
+    // (ri = 1) part, so the two halves of a complex output sit in adjacent lanes of one
+    // warp and pair by a shuffle.  Each warp works on its own: the next 16 columns'
+    // loads are in flight while the current ones are paired, split and stored.
     const int set = (warp - 4) >> 2;             // 0: warps 4-7, 1: warps 8-11
     const int quarter = warp & 3;                // TMEM lane quarter this warp may access
-    const int tl = quarter * 32 + lane;          // TMEM lane: n (real part) or 64 + n (imaginary)
-    const int h = tl >> 6, n = tl & 63;
-    const int et = (warp - 4 - 4 * set) * 32 + lane;   // 0..127
-    const int bar_id = 1 + set;
+    const int tl = quarter * 32 + lane;
+    const int ri = tl & 1, n = tl >> 1;
     const uint32_t lane_base = uint32_t(32 * quarter) << 16;
-    float* xs0 = xch + size_t(set) * 2 * kTcChunk * 128;
-    uint32_t chunk_no = 0;
     int j = 0;
     bool ok = true;
     for (int e = 0; e < S && ok; ++e) {
@@ -501,63 +509,76 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
       uint8_t* dst = a.bufs + int64_t(e) * a.buf_stride;
       const int64_t blk = split_block_bytes(st.R8_out);
       const uint32_t half = uint32_t(st.R8_out) * 256u;
+      // pair, split and store the 16 accumulator columns c0 .. c0 + 15 (output rows of
+      // the group) held in v1 (D1) and v2 (D2)
+      auto emit = [&](int g, int c0, const float (&v1)[kTcChunk], const float (&v2)[kTcChunk]) {
+        float y[kTcChunk];
+#pragma unroll
+        for (int q = 0; q < kTcChunk; ++q) {
+          // Y_re = D1[2n] - D2[2n + 1] (ri = 0), Y_im = D2[2n] + D1[2n + 1] (ri = 1)
+          const float pv = __shfl_xor_sync(0xffffffffu, v2[q], 1);
+          y[q] = ri == 0 ? v1[q] - pv : v1[q] + pv;
+        }
+#pragma unroll
+        for (int r8 = 0; r8 < kTcChunk / 8; ++r8) {
+          const int m0 = c0 + 8 * r8;
+          const int t = m0 / st.R8_out, k2 = m0 - t * st.R8_out;
+          const int64_t P = pat_blk(st.out_pat, g, t, st, c);
+          if (last) {
+            float* o = a.y_out + (P * st.R_out + k2) * (2 * kTcNR) + ri * kTcNR + n;
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+              if (k2 + i < st.R_out) o[i * 2 * kTcNR] = y[8 * r8 + i];
+          } else if (TF32) {   // two runs of 4 rows: byte (k / 4) 2048 + (m / 8) 128 + (m % 8) 16
+            uint8_t* o = dst + P * blk + (k2 >> 2) * 2048 + (tl >> 3) * 128 + (tl & 7) * 16;
+            *reinterpret_cast<uint4*>(o) = tf32x4(y + 8 * r8);
+            *reinterpret_cast<uint4*>(o + 2048) = tf32x4(y + 8 * r8 + 4);
+          } else {
+            uint4 hi, lo;
+            split8(y + 8 * r8, hi, lo);
+            uint8_t* o = dst + P * blk + (k2 >> 3) * 2048 + (tl >> 3) * 128 + (tl & 7) * 16;
+            *reinterpret_cast<uint4*>(o) = hi;
+            *reinterpret_cast<uint4*>(o + half) = lo;
+          }
+        }
+      };
       for (int g = blockIdx.x; g < st.n_groups && ok; g += gridDim.x, ++j) {
         if (j % nsets != set) continue;
         const uint32_t du = uint32_t(j / nsets);
-        // wait for the MMAs of this group
-        int got = 1;
-        if (et == 0 && !wait_bar(&dfull[set], du & 1u, abort)) {
-          got = 0;
-          if (!*abort) {
+        // wait for the MMAs of this group (every lane observes the phase)
+        if (!__all_sync(0xffffffffu, wait_bar(&dfull[set], du & 1u, abort))) {
+          if (lane == 0 && !*abort) {
             atomicCAS(a.status, 0, ST_FULL_TIMEOUT);
             *abort = 1;
           }
-        }
-        if (named_sync_or(bar_id, 128, !got || *abort != 0)) {
           ok = false;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t d1 = taddr + uint32_t(set) * set_cols + lane_base, d2 = d1 + uint32_t(st.M_t);
-        for (int c0 = 0; c0 < st.M_t; c0 += kTcChunk, ++chunk_no) {
-          float v1[kTcChunk], v2[kTcChunk];
-          tmem_ld16(d1 + uint32_t(c0), v1);
-          tmem_ld16(d2 + uint32_t(c0), v2);
+        float a1[kTcChunk], a2[kTcChunk], b1[kTcChunk], b2[kTcChunk];
+        tmem_ld16(d1, a1);
+        tmem_ld16(d2, a2);
+        tmem_wait_ld();
+        tmem_hold(a1, a2);
+        for (int c0 = 0; c0 < st.M_t; c0 += 2 * kTcChunk) {
+          const bool more = c0 + kTcChunk < st.M_t;
+          if (more) {
+            tmem_ld16(d1 + uint32_t(c0 + kTcChunk), b1);
+            tmem_ld16(d2 + uint32_t(c0 + kTcChunk), b2);
+          }
+          emit(g, c0, a1, a2);
           tmem_wait_ld();
-          // pair lanes n and 64 + n: Y_re = D1[n] - D2[64 + n] (h = 0), Y_im = D2[n] + D1[64 + n] (h = 1)
-          float* xsb = xs0 + size_t(chunk_no & 1u) * kTcChunk * 128;
-#pragma unroll
-          for (int q = 0; q < kTcChunk; ++q) xsb[q * 128 + tl] = v2[q];
-          named_sync(bar_id, 128);
-          float y[kTcChunk];
-#pragma unroll
-          for (int q = 0; q < kTcChunk; ++q) {
-            const float pv = xsb[q * 128 + (tl ^ 64)];
-            y[q] = h == 0 ? v1[q] - pv : v1[q] + pv;
+          if (!more) break;
+          tmem_hold(b1, b2);
+          const bool more2 = c0 + 2 * kTcChunk < st.M_t;
+          if (more2) {
+            tmem_ld16(d1 + uint32_t(c0 + 2 * kTcChunk), a1);
+            tmem_ld16(d2 + uint32_t(c0 + 2 * kTcChunk), a2);
           }
-          // rows m = c0 .. c0 + 15 of the group's output: two runs of 8 within one block each
-#pragma unroll
-          for (int r8 = 0; r8 < kTcChunk / 8; ++r8) {
-            const int m0 = c0 + 8 * r8;
-            const int t = m0 / st.R8_out, k2 = m0 - t * st.R8_out;
-            const int64_t P = pat_blk(st.out_pat, g, t, st, c);
-            if (last) {
-              float* o = a.y_out + (P * st.R_out + k2) * (2 * kTcNR) + h * kTcNR + n;
-#pragma unroll
-              for (int i = 0; i < 8; ++i)
-                if (k2 + i < st.R_out) o[i * 2 * kTcNR] = y[8 * r8 + i];
-            } else if (TF32) {   // two runs of 4 rows: byte (k / 4) 2048 + (8 h + n / 8) 128 + (n % 8) 16
-              uint8_t* o = dst + P * blk + (k2 >> 2) * 2048 + (8 * h + (n >> 3)) * 128 + (n & 7) * 16;
-              *reinterpret_cast<uint4*>(o) = tf32x4(y + 8 * r8);
-              *reinterpret_cast<uint4*>(o + 2048) = tf32x4(y + 8 * r8 + 4);
-            } else {
-              uint4 hi, lo;
-              split8(y + 8 * r8, hi, lo);
-              uint8_t* o = dst + P * blk + (k2 >> 3) * 2048 + (8 * h + (n >> 3)) * 128 + (n & 7) * 16;
-              *reinterpret_cast<uint4*>(o) = hi;
-              *reinterpret_cast<uint4*>(o + half) = lo;
-            }
-          }
+          emit(g, c0 + kTcChunk, b1, b2);
+          tmem_wait_ld();
+          if (more2) tmem_hold(a1, a2);
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         mbar_arrive(&dempty[set]);
@@ -700,22 +721,25 @@ __device__ __forceinline__ void store_split8(uint8_t* outs, int64_t leaf, int R8
     im[j] = acc[j].y;
     acc[j] = make_float2(0.f, 0.f);
   }
-  if constexpr (TF32) {   // TF32 block: byte (k / 4) 2048 + (8 ri + n / 8) 128 + (n % 8) 16 + (k % 4) 4
-    uint8_t* o = outs + leaf * split_block_bytes(R8) + (k0 >> 2) * 2048 + (n >> 3) * 128 + (n & 7) * 16;
+  // rows m = 2 n (real part) and 2 n + 1 (imaginary part) of the block: adjacent 16-byte
+  // rows of one core matrix
+  const int m = 2 * n;
+  if constexpr (TF32) {   // TF32 block: byte (k / 4) 2048 + (m / 8) 128 + (m % 8) 16 + (k % 4) 4
+    uint8_t* o = outs + leaf * split_block_bytes(R8) + (k0 >> 2) * 2048 + (m >> 3) * 128 + (m & 7) * 16;
     *reinterpret_cast<uint4*>(o) = tc::tf32x4(re);
     *reinterpret_cast<uint4*>(o + 2048) = tc::tf32x4(re + 4);
-    *reinterpret_cast<uint4*>(o + 1024) = tc::tf32x4(im);
-    *reinterpret_cast<uint4*>(o + 2048 + 1024) = tc::tf32x4(im + 4);
+    *reinterpret_cast<uint4*>(o + 16) = tc::tf32x4(im);
+    *reinterpret_cast<uint4*>(o + 2048 + 16) = tc::tf32x4(im + 4);
   } else {
     uint4 rh, rl, ih, il;
     tc::split8(re, rh, rl);
     tc::split8(im, ih, il);
-    uint8_t* o = outs + leaf * split_block_bytes(R8) + (k0 >> 3) * 2048 + (n >> 3) * 128 + (n & 7) * 16;
+    uint8_t* o = outs + leaf * split_block_bytes(R8) + (k0 >> 3) * 2048 + (m >> 3) * 128 + (m & 7) * 16;
     const int64_t half = int64_t(R8) * 256;
-    *reinterpret_cast<uint4*>(o) = rh;                 // Re hi
-    *reinterpret_cast<uint4*>(o + 1024) = ih;          // Im hi
-    *reinterpret_cast<uint4*>(o + half) = rl;          // Re lo
-    *reinterpret_cast<uint4*>(o + half + 1024) = il;   // Im lo
+    *reinterpret_cast<uint4*>(o) = rh;               // Re hi
+    *reinterpret_cast<uint4*>(o + 16) = ih;          // Im hi
+    *reinterpret_cast<uint4*>(o + half) = rl;        // Re lo
+    *reinterpret_cast<uint4*>(o + half + 16) = il;   // Im lo
   }
 }
 
@@ -917,8 +941,9 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_u_kernel(const __grid_const
 // ------------------------------------------------------------------ host side
 
 size_t tc_smem_bytes(int nsa, int nxb, int nsets, int mt_max, int kpad_max) {
+  (void)nsets;
   return size_t(nsa) * 4 * size_t(mt_max) * 32 + size_t(nxb) * 2 * size_t(kpad_max) * 256 +
-         size_t(nsets) * 2 * kTcChunk * 128 * sizeof(float) + (2 * size_t(nsa) + 20) * 8 + 64;
+         (2 * size_t(nsa) + 20) * 8 + 64;
 }
 
 size_t leaf_smem_bytes(int R, int c, bool u_side, int pts_cap) {

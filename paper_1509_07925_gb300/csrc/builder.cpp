@@ -277,6 +277,74 @@ void problem_trees(const mbf_problem_t& prob, Tree& xt, Tree& wt) {
   }
 }
 
+// Shapes of the padded factor set of a problem (the interchange layout of mbf_factors_t):
+// padded rank caps R_h = min(r, max |A^h|, max |B^h|), R_{l+1} = min(r, max |node at l+1|,
+// c R_l) on each side, leaf arrays at the largest leaf, every array zero.
+void layout_factor_set(int d, int L, int64_t r, int64_t N, const Tree& xt, const Tree& wt, FactorSet& fs) {
+  const int c = 1 << d, h = L / 2;
+  auto max_size = [&](const Tree& T, int l) {
+    int64_t mx = 0;
+    for (int64_t i = 0; i < Tree::ipow(c, l); ++i) mx = std::max(mx, T.size(l, i));
+    return mx;
+  };
+  fs.d = d;
+  fs.L = L;
+  fs.n_out = N;
+  fs.n_in = N;
+  fs.n_w = int64_t(wt.perm.size());
+  fs.RU.assign(size_t(L + 1), 0);
+  fs.RV.assign(size_t(L + 1), 0);
+  const int64_t Rh = std::max<int64_t>(1, std::min({r, max_size(xt, h), max_size(wt, L - h)}));
+  fs.RU[size_t(h)] = fs.RV[size_t(h)] = int32_t(Rh);
+  for (int l = h; l < L; ++l) {
+    fs.RU[size_t(l + 1)] = int32_t(std::max<int64_t>(1, std::min({r, max_size(xt, l + 1), c * int64_t(fs.RU[size_t(l)])})));
+    fs.RV[size_t(l + 1)] = int32_t(std::max<int64_t>(1, std::min({r, max_size(wt, l + 1), c * int64_t(fs.RV[size_t(l)])})));
+  }
+  fs.max_leaf_x = int32_t(std::max<int64_t>(1, max_size(xt, L)));
+  fs.max_leaf_w = int32_t(std::max<int64_t>(1, max_size(wt, L)));
+  const int64_t nL = Tree::ipow(c, L);
+  fs.UL.assign(size_t(nL * fs.max_leaf_x * fs.RU[size_t(L)]), cd(0));
+  fs.VL.assign(size_t(nL * fs.max_leaf_w * fs.RV[size_t(L)]), cd(0));
+  fs.G.resize(size_t(L - h));
+  fs.H.resize(size_t(L - h));
+  for (int l = h; l < L; ++l) {
+    fs.G[size_t(l - h)].assign(size_t(nL * c * fs.RU[size_t(l + 1)] * fs.RU[size_t(l)]), cd(0));
+    fs.H[size_t(l - h)].assign(size_t(nL * c * fs.RV[size_t(l + 1)] * fs.RV[size_t(l)]), cd(0));
+  }
+  fs.S.assign(size_t(Tree::ipow(c, 2 * h) * Rh), 0.0);
+  fs.x_perm = xt.perm;
+  fs.x_off = xt.off;
+  fs.w_perm = wt.perm;
+  fs.w_off = wt.off;
+}
+
+// Algorithmic nonzeros of the unpadded factors (§2.5: the apply cost) from the true
+// ranks rank[side][level][node * c^(L - level) + other].
+int64_t factor_nnz(int c, int L, const Tree& xt, const Tree& wt, const std::vector<std::vector<int32_t>>& kU,
+                   const std::vector<std::vector<int32_t>>& kV) {
+  const int h = L / 2;
+  const int64_t nL = Tree::ipow(c, L), nh = Tree::ipow(c, h);
+  int64_t nnz = 0;
+  for (int64_t q = 0; q < nL; ++q) {
+    nnz += (xt.off[size_t(q + 1)] - xt.off[size_t(q)]) * kU[size_t(L)][size_t(q)];
+    nnz += (wt.off[size_t(q + 1)] - wt.off[size_t(q)]) * kV[size_t(L)][size_t(q)];
+  }
+  for (int64_t q = 0; q < nh * nh; ++q) nnz += kU[size_t(h)][size_t(q)];
+  for (int side = 0; side < 2; ++side) {
+    auto& K = side == 0 ? kU : kV;
+    for (int l = h; l < L; ++l) {
+      const int64_t njp = Tree::ipow(c, L - l - 1);
+      for (int64_t node = 0; node < Tree::ipow(c, l); ++node)
+        for (int64_t jp = 0; jp < njp; ++jp) {
+          int64_t kin = 0;
+          for (int tp = 0; tp < c; ++tp) kin += K[size_t(l)][size_t(node * njp * c + c * jp + tp)];
+          for (int t = 0; t < c; ++t) nnz += kin * K[size_t(l + 1)][size_t((c * node + t) * njp + jp)];
+        }
+    }
+  }
+  return nnz;
+}
+
 namespace {
 
 struct Builder {
@@ -441,71 +509,20 @@ struct Builder {
     }
     problem_trees(prob, xt, wt);
 
-    // padded rank caps: R_h = min(r, max |A^h|, max |B^h|); R_{l+1} = min(r, max |node|, c R_l)
-    auto max_size = [&](const Tree& T, int l) {
-      int64_t mx = 0;
-      for (int64_t i = 0; i < ip(c, l); ++i) mx = std::max(mx, T.size(l, i));
-      return mx;
-    };
-    fs.d = d;
-    fs.L = L;
-    fs.n_out = N;
-    fs.n_in = N;
-    fs.n_w = int64_t(wt.perm.size());
-    fs.RU.assign(size_t(L + 1), 0);
-    fs.RV.assign(size_t(L + 1), 0);
-    const int64_t Rh = std::max<int64_t>(1, std::min({r, max_size(xt, h), max_size(wt, L - h)}));
-    fs.RU[size_t(h)] = fs.RV[size_t(h)] = int32_t(Rh);
-    for (int l = h; l < L; ++l) {
-      fs.RU[size_t(l + 1)] = int32_t(std::max<int64_t>(1, std::min({r, max_size(xt, l + 1), c * int64_t(fs.RU[size_t(l)])})));
-      fs.RV[size_t(l + 1)] = int32_t(std::max<int64_t>(1, std::min({r, max_size(wt, l + 1), c * int64_t(fs.RV[size_t(l)])})));
-    }
-    fs.max_leaf_x = int32_t(std::max<int64_t>(1, max_size(xt, L)));
-    fs.max_leaf_w = int32_t(std::max<int64_t>(1, max_size(wt, L)));
-    const int64_t nL = ip(c, L);
-    fs.UL.assign(size_t(nL * fs.max_leaf_x * fs.RU[size_t(L)]), cd(0));
-    fs.VL.assign(size_t(nL * fs.max_leaf_w * fs.RV[size_t(L)]), cd(0));
-    fs.G.resize(size_t(L - h));
-    fs.H.resize(size_t(L - h));
-    for (int l = h; l < L; ++l) {
-      fs.G[size_t(l - h)].assign(size_t(nL * c * fs.RU[size_t(l + 1)] * fs.RU[size_t(l)]), cd(0));
-      fs.H[size_t(l - h)].assign(size_t(nL * c * fs.RV[size_t(l + 1)] * fs.RV[size_t(l)]), cd(0));
-    }
-    fs.S.assign(size_t(ip(c, 2 * h) * Rh), 0.0);
+    layout_factor_set(d, L, r, N, xt, wt, fs);
     kU.assign(size_t(L + 1), {});
     kV.assign(size_t(L + 1), {});
+    const int64_t nL = ip(c, L);
     for (int l = h; l <= L; ++l) {
       kU[size_t(l)].assign(size_t(nL), 0);
       kV[size_t(l)].assign(size_t(nL), 0);
     }
-    fs.x_perm = xt.perm;
-    fs.x_off = xt.off;
-    fs.w_perm = wt.perm;
-    fs.w_off = wt.off;
 
     const int64_t nh = ip(c, h);
     parallel_for(nh, opts.threads, [&](int64_t i) { side_pass(0, i); });
     parallel_for(nh, opts.threads, [&](int64_t j) { side_pass(1, j); });
 
-    // algorithmic nonzeros (§2.5: the apply cost)
-    int64_t nnz = 0;
-    for (int64_t q = 0; q < nL; ++q) {
-      nnz += (xt.off[size_t(q + 1)] - xt.off[size_t(q)]) * kU[size_t(L)][size_t(q)];
-      nnz += (wt.off[size_t(q + 1)] - wt.off[size_t(q)]) * kV[size_t(L)][size_t(q)];
-    }
-    for (int64_t q = 0; q < nh * nh; ++q) nnz += kU[size_t(h)][size_t(q)];
-    for (int side = 0; side < 2; ++side) {
-      auto& K = side == 0 ? kU : kV;
-      for (int l = h; l < L; ++l) {
-        const int64_t njp = ip(c, L - l - 1);
-        for (int64_t node = 0; node < ip(c, l); ++node)
-          for (int64_t jp = 0; jp < njp; ++jp) {
-            int64_t kin = 0;
-            for (int tp = 0; tp < c; ++tp) kin += K[size_t(l)][size_t(node * njp * c + c * jp + tp)];
-            for (int t = 0; t < c; ++t) nnz += kin * K[size_t(l + 1)][size_t((c * node + t) * njp + jp)];
-          }
-      }
-    }
+    const int64_t nnz = factor_nnz(c, L, xt, wt, kU, kV);
     fs.nnz = nnz;
   }
 };
