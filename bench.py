@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--no-serve", action="store_true", help="skip the served-mix experiment")
     p.add_argument("--serve-requests", type=int, default=512)
     p.add_argument("--no-small", action="store_true", help="skip the 2-D DFT n = 64 latency leg")
+    p.add_argument("--factor-file", default=None,
+                   help="multiscale leg: factor files <path>.t<k> to load (or write) instead of building")
     return p.parse_args()
 
 
@@ -375,6 +377,76 @@ def serve_experiment(torch, bd, ops, n_requests, loads=(0.5, 0.8, 1.1)):
     return out
 
 
+MSBF_WORKLOAD = "fio2_msbf_n512_r24_x32"
+
+
+def msbf_bench(args, torch, bd, stream, peak, peak_kind):
+    """The multiscale workload: 2-D isotropic FIO, n = 512, r = 24, 16 x 16 centre,
+    coronas t = 0..4, 32 RHS on the tensor cores (split-BF16x3).  Not a default leg: its
+    host construction takes minutes.  One step = one apply of eq. (f1) (every corona's
+    factorization plus the dense centre) to a 32-RHS panel."""
+    n, r, nrhs = 512, 24, args.nrhs or 32
+    N = n * n
+    t0 = time.time()
+    m = bd.MsBF.build(n, r, kernel="fio_iso", n_center=16, seed=7, factor_file=args.factor_file)
+    t_build = time.time() - t0
+    info = m.info()
+    sp = stream.cuda_stream
+    g = torch.from_numpy(complex_normal(N, nrhs, seed=0).astype(np.complex64)).cuda()
+    u = torch.empty((nrhs, N), dtype=torch.complex64, device="cuda")
+    for _ in range(max(3, args.warmup)):
+        m.apply(g.data_ptr(), u.data_ptr(), nrhs, bd.MBF_PREC_BF16X3, sp)
+    m.check(sp)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        m.apply(g.data_ptr(), u.data_ptr(), nrhs, bd.MBF_PREC_BF16X3, sp)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    m.check(sp)
+    # end to end: pinned host panel in, result out, inside the timed region
+    gh = g.cpu().pin_memory()
+    uh = torch.empty((nrhs, N), dtype=torch.complex64).pin_memory()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for _ in range(max(3, args.steps // 2)):
+        g.copy_(gh, non_blocking=True)
+        m.apply(g.data_ptr(), u.data_ptr(), nrhs, bd.MBF_PREC_BF16X3, sp)
+        uh.copy_(u, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t1) / max(3, args.steps // 2)
+    fac_bytes = info.bytes_algorithmic + 8 * info.n_center_points * N
+    step_bytes = fac_bytes + 16 * N * nrhs
+    achieved = step_bytes / (ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": N * nrhs / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": DTYPES["bf16x3"][0], "dtype_detail": DTYPES["bf16x3"][1],
+        "data": "synthetic",
+        "config": {"workload": MSBF_WORKLOAD, "kernel": "fio_iso", "tree": "multiscale", "n": n, "N": N, "r": r,
+                   "n_center": 16, "coronas": [int(info.part_t[i]) for i in range(info.n_parts)],
+                   "corona_depths": [int(info.part_L[i]) for i in range(info.n_parts)], "nrhs": nrhs,
+                   "precision": "bf16x3", "l2": f"inputs larger than L2: factors {fac_bytes / 1e9:.1f} GB",
+                   "factor_bytes_algorithmic": fac_bytes, "host_build_s": t_build},
+        "roofline": {"bound": "hbm", "kernel": "whole apply (every kernel of the step)", "achieved": achieved,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "peak_kind": f"{peak_kind} hbm_gbs (burst copy)", "algorithmic_bytes_per_launch": step_bytes,
+                     "algorithmic_bytes": "8 B x nonzeros of every corona's factors + 8 B x the dense centre "
+                                          "entries + 8 B in + 8 B out per point and RHS, per step"},
+        "e2e": {"value": N * nrhs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * N * nrhs,
+                "d2h_bytes_per_step": 8 * N * nrhs},
+        "gpu_launches": None, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    m.close()
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -392,6 +464,9 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     buildlib.build()
+    if args.workload == MSBF_WORKLOAD:
+        peak, peak_kind = measured_peaks()
+        return msbf_bench(args, torch, bd, torch.cuda.current_stream(), peak, peak_kind)
     wl = WORKLOADS[args.workload]
     N = wl.N
     hf = build_factors(bd, wl)

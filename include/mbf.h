@@ -46,8 +46,12 @@ typedef enum mbf_status {
 typedef enum mbf_tree_kind {
   MBF_TREE_UNIFORM = 0,  /* Omega tree over the uniform grid (§2.2)                     */
   MBF_TREE_POLAR = 1,    /* Omega tree over the polar image p(xi) in [0,1]^2 (§3.1-3.2)  */
-  MBF_TREE_SQUARE = 2    /* Omega tree over a square holding an explicit point subset,   */
+  MBF_TREE_SQUARE = 2,   /* Omega tree over a square holding an explicit point subset,   */
                          /* e.g. one corona Omega_t of the multiscale split (§4.2)        */
+  MBF_TREE_POINTS = 3    /* explicit non-uniform point sets on both sides (§2.6): the X  */
+                         /* tree over x_pts in [0,1)^dim, the Omega tree over w_pts in   */
+                         /* the square [w_lo, w_lo + w_side)^dim; empty nodes kept as     */
+                         /* zero-point nodes; natural order = the order of the arrays     */
 } mbf_tree_kind;
 
 typedef enum mbf_precision {
@@ -76,6 +80,13 @@ typedef struct mbf_problem {
   const int64_t* w_index;
   double w_lo;
   double w_side;
+  /* MBF_TREE_POINTS only: the point sets themselves (host, row-major [count][dim]):
+   * X points in [0,1)^dim, Omega points (frequencies) in [w_lo, w_lo + w_side)^dim.
+   * n is not used for them; the operator maps vectors of n_w_pts to vectors of n_x_pts. */
+  int64_t n_x_pts;
+  const double* x_pts;
+  int64_t n_w_pts;
+  const double* w_pts;
 } mbf_problem_t;
 
 /* Kernel entry evaluation, Case (ii) of §1.1: fill the m x n block
@@ -212,7 +223,9 @@ mbf_status mbf_op_info(mbf_op_t op, mbf_op_info_t* info);
  * u(x) is summed in FP64 on the host from entries of fn (as for the builder; called from
  * several threads).  The operator must be built on the grids X, Omega of eqs. (X),
  * (Omega) with n^d points.  Allocates two vectors on the device for the call.  The result
- * is written to *eps (if not NULL) and kept for mbf_op_info. */
+ * is written to *eps (if not NULL) and kept for mbf_op_info.  Grid problems only (the
+ * operator keeps no point coordinates): mbf_build_from_entries skips it for
+ * MBF_TREE_POINTS. */
 mbf_status mbf_op_estimate_error(mbf_op_t op, mbf_entry_fn fn, void* ctx, int32_t n_samples,
                                  uint64_t seed, void* stream, double* eps);
 
@@ -338,7 +351,7 @@ mbf_status mbf_msbf_destroy(mbf_msbf_t m);
  * The paper has no counterpart (its applies are single-threaded CPU loops).  Measures,
  * on `stream` with device buffers it allocates and frees itself, (a) the FP32 SIMT apply
  * for 1, 2, 4, 8, 16, 32 and 64 RHS, (b) the tensor-core apply of one 64-RHS panel for
- * every A-tile ring depth that fits shared memory, then keeps the fastest ring depth and
+ * the even A-tile ring depths 2 .. 16 that fit shared memory, then keeps the fastest and
  * sets the RHS count from which MBF_PREC_AUTO takes the tensor cores to the smallest
  * measured count at which one panel is faster than the SIMT apply.  Blocking; the
  * operator must be idle.  The choices stay with the operator until it is destroyed. */
@@ -362,14 +375,21 @@ mbf_status mbf_op_tune(mbf_op_t op, void* stream, mbf_tune_result_t* out);
  *                never blocks: a request that does not fit the staging budget
  *                (2 nrhs max(n_in, n_out) 8 bytes reserved until it completes) or the
  *                queue returns MBF_ERR_BUSY.
- *   worker       continuous batching: whenever a slot is free it takes the oldest queued
- *                request whose operator is idle, coalesces the queued requests on the
- *                same operator (FIFO, up to max_batch_rhs RHS) into one apply through
- *                staging buffers, and launches the batch on the slot's stream -- as one
- *                captured CUDA graph when use_graphs is set.  Batches of different
- *                operators overlap on the device; while others are running or waiting a
- *                batch's persistent kernels get a 1 / max_inflight share of the SMs.
- *                The precision is MBF_PREC_AUTO for the coalesced RHS count.
+ *   worker       continuous batching: whenever a slot is free it forms a batch: the
+ *                oldest queued request with the queued requests on the same operator
+ *                (FIFO, up to max_batch_rhs RHS, applied at once through a staging panel)
+ *                is its first group; when more operators are queued than slots are
+ *                free, the oldest requests on other operators add groups the same way,
+ *                spreading the queued operators over the free slots, at most
+ *                max_batch_ops per batch.  The batch is launched on
+ *                the slot's stream, its groups in parallel branches -- as one captured
+ *                CUDA graph (one graph launch for requests of several operators and RHS
+ *                counts) when use_graphs is set.  A group borrows a workspace of its
+ *                operator for the batch (the operator's own one when free, else one of a
+ *                pool the operator keeps, allocated on first need), so batches overlap on
+ *                the device, of one operator or of several; while others are running or waiting a batch's
+ *                persistent kernels share 1 / max_inflight of the SMs among its groups.
+ *                The precision is MBF_PREC_AUTO for each group's RHS count.
  *   mbf_poll     state and timestamps of a ticket; a ticket is forgotten after the poll
  *                that reports DONE or ERROR (later polls: MBF_ERR_NOT_FOUND).
  * An operator used by a server must not be applied by the caller at the same time. */
@@ -379,6 +399,8 @@ typedef struct mbf_server_opts {
   int32_t max_batch_rhs;        /* RHS coalesced into one apply (0: 64)                */
   int32_t max_queue;            /* queued requests (0: 4096)                           */
   int32_t use_graphs;           /* 1: each batch is one CUDA graph launch              */
+  int32_t max_batch_ops;        /* operators (groups) per batch (0: 4, <= 8)           */
+  int32_t reserved_opts;
 } mbf_server_opts_t;
 typedef int64_t mbf_ticket_t;
 enum { MBF_REQ_QUEUED = 0, MBF_REQ_RUNNING = 1, MBF_REQ_DONE = 2, MBF_REQ_ERROR = 3 };
@@ -393,6 +415,9 @@ typedef struct mbf_server_stats {
   int64_t submitted, completed, failed, rejected_busy;
   int64_t batches, coalesced_requests, graph_launches, graph_instantiations;
   int32_t max_batch_requests, max_concurrent_batches;
+  int64_t mixed_batches;        /* batches that held requests of more than one operator */
+  int32_t max_batch_ops;        /* most operators in one batch                          */
+  int32_t reserved_stats;
 } mbf_server_stats_t;
 mbf_status mbf_server_create(const mbf_server_opts_t* opts, mbf_server_t* out);
 mbf_status mbf_submit(mbf_server_t s, mbf_op_t op, const void* g, void* u, int64_t nrhs,

@@ -284,3 +284,58 @@ class SparseBF:
         for F in fac[-2::-1]:
             D = F @ D
         return np.asarray(D)
+
+
+class BlockBF:
+    """The same product of eq. (gbf) applied level by level on the padded arrays, without
+    assembling sparse matrices: memory of one level at a time, for factor sets too large
+    for `SparseBF` (test infrastructure; equal to `SparseBF` to rounding, pinned).
+
+    Vector of level l on the X side: [c^l, c^(L-l), R_l] indexed (i, j, k) as the columns
+    of U^l; on the Omega side [c^l, c^(L-l), R_l] indexed (j, i, k) as the columns of V^l.
+      (V^L)^*:   y[j, 0, k]       = sum_a conj(V^L[j, a, k]) g[w_perm[w_off[j] + a]]
+      (H^l)^*:   y_l[j, c ip + tp, k] = sum_{t, k2} conj(H^l[j, ip, t, k2, tp, k]) y_{l+1}[c j + t, ip, k2]
+      M^h:       w[i, j, k]       = S[i, j, k] y_h[j, i, k]
+      G^l:       w_{l+1}[c i + t, jp, k2] = sum_{tp, k} G^l[i, jp, t, k2, tp, k] w_l[i, c jp + tp, k]
+      U^L:       u[x_perm[x_off[i] + a]] = sum_k U^L[i, a, k] w[i, 0, k]
+    (the index conventions of `FactorSet`, eqs. RSh2 / VF, lowrank1, expression-U)."""
+
+    def __init__(self, fs: FactorSet):
+        self.fs = fs
+
+    @staticmethod
+    def _gather_index(perm, off, mx):
+        sizes = np.diff(off)
+        a = np.arange(mx)[None, :]
+        valid = a < sizes[:, None]
+        idx = np.where(valid, off[:-1, None] + a, 0)
+        return np.where(valid, perm[np.minimum(idx, max(perm.shape[0] - 1, 0))], 0), valid
+
+    def apply(self, g: np.ndarray) -> np.ndarray:
+        fs = self.fs
+        c, L, h = fs.c, fs.L, fs.h
+        nL = c ** L
+        g = np.atleast_2d(g)
+        nr = g.shape[0]
+        gt = np.ascontiguousarray(g.T)                              # [n_in, nrhs]
+        gi, gv = self._gather_index(fs.w_perm, fs.w_off, fs.VL.shape[1])
+        leaf_in = gt[gi] * gv[..., None]                            # [nL, mx, nrhs]
+        y = np.matmul(np.conj(fs.VL).transpose(0, 2, 1), leaf_in)   # [nL, R_L, nrhs]
+        for l in range(L - 1, h - 1, -1):
+            A = fs.H[l - h]                                         # [c^l, c^(L-l-1), c, R2, c, R1]
+            ni, njp, _, R2, _, R1 = A.shape
+            yl = y.reshape(ni, c, njp, R2, nr).transpose(0, 2, 1, 3, 4).reshape(ni * njp, c * R2, nr)
+            Ah = np.conj(A).reshape(ni * njp, c * R2, c * R1).transpose(0, 2, 1)
+            y = np.matmul(Ah, yl).reshape(ni, njp * c, R1, nr)     # (j, c ip + tp, k)
+        w = fs.S[..., None] * y.transpose(1, 0, 2, 3)               # [c^h, c^h, R_h, nrhs]
+        for l in range(h, L):
+            A = fs.G[l - h]
+            ni, njp, _, R2, _, R1 = A.shape
+            wl = w.reshape(ni * njp, c * R1, nr)                    # (i, jp), (tp, k)
+            out = np.matmul(A.reshape(ni * njp, c * R2, c * R1), wl).reshape(ni, njp, c, R2, nr)
+            w = out.transpose(0, 2, 1, 3, 4).reshape(ni * c, njp, R2, nr)
+        up = np.matmul(fs.UL, w.reshape(nL, -1, nr))                # [nL, mx, nrhs]
+        xi, xv = self._gather_index(fs.x_perm, fs.x_off, fs.UL.shape[1])
+        u = np.zeros((fs.n_out, nr), dtype=np.complex128)
+        u[xi[xv]] = up[xv]
+        return u.T

@@ -17,7 +17,7 @@ LIBPATH = os.path.join(_HERE, "_lib", "libmbf.so")
 
 MBF_OK, MBF_ERR_INVALID, MBF_ERR_OOM, MBF_ERR_CUDA, MBF_ERR_BUSY, MBF_ERR_TIMEOUT, MBF_ERR_IO, \
     MBF_ERR_NOT_FOUND = range(8)
-MBF_TREE_UNIFORM, MBF_TREE_POLAR, MBF_TREE_SQUARE = 0, 1, 2
+MBF_TREE_UNIFORM, MBF_TREE_POLAR, MBF_TREE_SQUARE, MBF_TREE_POINTS = 0, 1, 2, 3
 MBF_PREC_AUTO, MBF_PREC_FP32_SIMT, MBF_PREC_TF32, MBF_PREC_BF16X3 = 0, 1, 2, 3
 
 _STATUS_NAMES = {0: "MBF_OK", 1: "MBF_ERR_INVALID", 2: "MBF_ERR_OOM", 3: "MBF_ERR_CUDA",
@@ -33,7 +33,9 @@ class MbfError(RuntimeError):
 class Problem(C.Structure):
     _fields_ = [("dim", C.c_int32), ("n", C.c_int32), ("L", C.c_int32), ("r", C.c_int32),
                 ("tree", C.c_int32), ("reserved0", C.c_int32), ("n_w", C.c_int64),
-                ("w_index", C.POINTER(C.c_int64)), ("w_lo", C.c_double), ("w_side", C.c_double)]
+                ("w_index", C.POINTER(C.c_int64)), ("w_lo", C.c_double), ("w_side", C.c_double),
+                ("n_x_pts", C.c_int64), ("x_pts", C.POINTER(C.c_double)), ("n_w_pts", C.c_int64),
+                ("w_pts", C.POINTER(C.c_double))]
 
 
 class BuildOpts(C.Structure):
@@ -77,7 +79,8 @@ class TuneResult(C.Structure):
 
 class ServerOpts(C.Structure):
     _fields_ = [("staging_budget_bytes", C.c_int64), ("max_inflight", C.c_int32),
-                ("max_batch_rhs", C.c_int32), ("max_queue", C.c_int32), ("use_graphs", C.c_int32)]
+                ("max_batch_rhs", C.c_int32), ("max_queue", C.c_int32), ("use_graphs", C.c_int32),
+                ("max_batch_ops", C.c_int32), ("reserved_opts", C.c_int32)]
 
 
 class RequestStatus(C.Structure):
@@ -90,7 +93,8 @@ class ServerStats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
                 ("rejected_busy", C.c_int64), ("batches", C.c_int64), ("coalesced_requests", C.c_int64),
                 ("graph_launches", C.c_int64), ("graph_instantiations", C.c_int64),
-                ("max_batch_requests", C.c_int32), ("max_concurrent_batches", C.c_int32)]
+                ("max_batch_requests", C.c_int32), ("max_concurrent_batches", C.c_int32),
+                ("mixed_batches", C.c_int64), ("max_batch_ops", C.c_int32), ("reserved_stats", C.c_int32)]
 
 
 MBF_REQ_QUEUED, MBF_REQ_RUNNING, MBF_REQ_DONE, MBF_REQ_ERROR = 0, 1, 2, 3
@@ -210,11 +214,20 @@ class HostFactors:
     @classmethod
     def build(cls, dim, n, L, r, tree=MBF_TREE_UNIFORM, kernel="dft", seed=7, threads=0,
               w_index=None, w_lo=0.0, w_side=0.0, sample_factor=3, max_rounds=3, tol=1e-14,
-              factor_file=None):
+              factor_file=None, x_pts=None, w_pts=None):
         """Host FP64 construction (mbf_build_factors); with factor_file, loaded from that
-        file if it exists, else built and written there."""
+        file if it exists, else built and written there.  tree=MBF_TREE_POINTS takes explicit
+        point sets x_pts [n_x][dim] in [0,1)^dim and w_pts [n_w][dim] in the square
+        [w_lo, w_lo + w_side)^dim (§2.6)."""
         self = cls()
         prob = Problem(dim=dim, n=n, L=L, r=r, tree=tree)
+        if x_pts is not None:
+            xp = np.ascontiguousarray(x_pts, dtype=np.float64).reshape(-1, dim)
+            wp = np.ascontiguousarray(w_pts, dtype=np.float64).reshape(-1, dim)
+            self._keep.extend([xp, wp])
+            prob.n_x_pts, prob.x_pts = xp.shape[0], _ptr(xp, C.c_double)
+            prob.n_w_pts, prob.w_pts = wp.shape[0], _ptr(wp, C.c_double)
+            prob.w_lo, prob.w_side = w_lo, w_side
         if w_index is not None:
             wi = np.ascontiguousarray(w_index, dtype=np.int64)
             self._keep.append(wi)
@@ -396,8 +409,9 @@ class Server:
     """Serving loop (mbf_server_t): continuous batching of applies on resident operators."""
 
     def __init__(self, staging_budget_bytes: int = 0, max_inflight: int = 0, max_batch_rhs: int = 0,
-                 max_queue: int = 0, use_graphs: bool = True):
-        o = ServerOpts(staging_budget_bytes, max_inflight, max_batch_rhs, max_queue, 1 if use_graphs else 0)
+                 max_queue: int = 0, use_graphs: bool = True, max_batch_ops: int = 0):
+        o = ServerOpts(staging_budget_bytes, max_inflight, max_batch_rhs, max_queue, 1 if use_graphs else 0,
+                       max_batch_ops)
         self._h = C.c_void_p()
         _check(lib().mbf_server_create(C.byref(o), C.byref(self._h)))
 

@@ -97,7 +97,7 @@ void apply_static_impl(mbf_op_s* op, const void* g, void* u, int64_t nrhs, void*
   a.counters = a.barrier + kBarrierBytes / sizeof(unsigned);
   a.bufs = reinterpret_cast<float2*>(base + sync_bytes);     // one vector per stage
   a.buf_stride = op->positions * nrb;
-  a.status = op->d_status;
+  a.status = op->ws.status;
   a.nrhs = int32_t(nrhs);
   a.n_pass = int32_t((nrhs + nrb - 1) / nrb);
   a.n_slots = op->ns[nrb];

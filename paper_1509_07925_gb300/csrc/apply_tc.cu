@@ -19,13 +19,13 @@
 //              4 planes), into a ring of shared-memory slots (full/empty mbarriers);
 //   warp 1     allocates TMEM; runs the MMA loop (warp-uniform operands), one elected
 //              lane issuing the MMAs into an accumulator set and the commits;
-//   warps 2-3  thread 0 waits for a group's inputs (dependency counters); the 64
-//              threads copy its c blocks into a panel buffer with cp.async and drop
-//              the consumed blocks from L2;
+//   warp 2     one lane waits for a group's inputs (dependency counters) and bulk-
+//              copies its c blocks into a panel buffer (complete_tx on its mbarrier);
 //   warps 4-7, 8-11   epilogue sets, one per accumulator set: read the accumulators
-//              (tcgen05.ld, the next columns' loads in flight), pair the halves by warp
+//              (tcgen05.ld, 32 columns of each half a round), pair the halves by warp
 //              shuffles, split and store the group's output blocks, and hand them to
-//   warp 12    the signal warp, which fences and counts them in for the consumers.
+//   warp 12    the signal warp, which fences and counts them in for the consumers;
+//   warps 3, 13  drop each group's consumed input blocks from L2 once its MMAs are done.
 // The (V^L)^* and U^L leaf products run before and after it (leaf kernels below).
 // Every wait is bounded; on a timeout the status word is set and all roles drain.
 #include <cuda_runtime.h>
@@ -157,15 +157,27 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
         "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]), "=f"(v[15])
       : "r"(taddr));
 }
+// 32 consecutive TMEM columns of this thread's lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]), "=f"(v[8]),
+        "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]), "=f"(v[15]), "=f"(v[16]),
+        "=f"(v[17]), "=f"(v[18]), "=f"(v[19]), "=f"(v[20]), "=f"(v[21]), "=f"(v[22]), "=f"(v[23]), "=f"(v[24]),
+        "=f"(v[25]), "=f"(v[26]), "=f"(v[27]), "=f"(v[28]), "=f"(v[29]), "=f"(v[30]), "=f"(v[31])
+      : "r"(taddr));
+}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 // Uses of registers written by tcgen05.ld must not move above the tcgen05.wait::ld that
 // completes them: after the wait, each register passes through an empty asm that the
 // compiler must assume rewrites it (volatile asms keep their order).
-__device__ __forceinline__ void tmem_hold(float (&x)[16], float (&y)[16]) {
+template <int K>
+__device__ __forceinline__ void tmem_hold(float (&x)[K], float (&y)[K]) {
 #pragma unroll
-  for (int j = 0; j < 16; ++j) asm volatile("" : "+f"(x[j]));
+  for (int j = 0; j < K; ++j) asm volatile("" : "+f"(x[j]));
 #pragma unroll
-  for (int j = 0; j < 16; ++j) asm volatile("" : "+f"(y[j]));
+  for (int j = 0; j < K; ++j) asm volatile("" : "+f"(y[j]));
 }
 
 // Two floats -> bf16x2 (round to nearest even), the first in the low half.
@@ -219,7 +231,7 @@ __device__ __forceinline__ bool wait_bar(uint64_t* b, uint32_t ph, volatile int*
 
 }  // namespace tc
 
-constexpr int kTcThreads = 416;   // 13 warps (roles above)
+constexpr int kTcThreads = 448;   // 14 warps (roles above)
 constexpr int kTcChunk = 16;   // accumulator columns per epilogue step
 
 // TF32: the vectors between stages are TF32 blocks (apply.hpp) and the tiles two FP32
@@ -252,7 +264,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
       mbar_init(&aempty[i], 1);
     }
     for (int s = 0; s < 2; ++s) {
-      mbar_init(&xfull[s], 64);
+      mbar_init(&xfull[s], 1);
       mbar_init(&xempty[s], 1);
       mbar_init(&dfull[s], 1);
       mbar_init(&dempty[s], 128);
@@ -311,74 +323,88 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
       while (!mbar_try(&afull[slot], ph) && gtimer() - t1 < kTimeoutNs) {
       }
     }
-  } else if (warp == 2 || warp == 3) {
+  } else if (warp == 2) {
     // ---------------------------------------------------------------- X panels
-    // The 64 threads of warps 2-3 copy a group's c input blocks with 16-byte cp.async
-    // (the load/store path, so that the panels do not queue behind the tile stream's
-    // bulk copies), wait for their own copies, make them visible to the tensor cores
-    // and arrive on xfull.  Thread 0 first waits for the buffer and the inputs.  Each
-    // block is read by exactly one group, so once it sits in shared memory its lines
-    // are dropped from L2 without a write-back.
-    const int xt = tid - 64;
-    int j = 0;
-    bool ok = true;
-    for (int e = 0; e < S && ok; ++e) {
-      const TCStage& st = plan.st[e];
-      const uint8_t* src = e == 0 ? a.x_in : a.bufs + int64_t(e - 1) * a.buf_stride;
-      const unsigned* cnt_in = a.counters + int64_t(e) * st.n_groups;
-      // split-BF16: hi and lo halves of each block go to the two halves of the panel
-      // buffer; TF32: each block is one run
-      const uint32_t half = TF32 ? uint32_t(st.R8_in) * 512u : uint32_t(st.R8_in) * 256u;
-      const uint32_t xhalf = uint32_t(st.K_pad) * 256u;     // hi or lo half of the panel buffer
-      const int64_t blk = split_block_bytes(st.R8_in);
-      const int pieces = int(half >> 4);                      // 16-byte pieces of one part
-      constexpr int kParts = TF32 ? 1 : 2;
-      for (int g = blockIdx.x; g < st.n_groups && ok; g += gridDim.x, ++j) {
-        const int xs = j % nxb;
-        const uint32_t xu = uint32_t(j / nxb);
-        int fail = 0;
-        if (xt == 0) {
-          fail = !wait_bar(&xempty[xs], (xu & 1u) ^ 1u, abort);
+    // One lane waits for a group's panel buffer and its c input blocks (dependency
+    // counters), then issues one bulk copy per block half (split-BF16: the hi halves of
+    // the c blocks side by side, then the lo halves; TF32: one run per block) that
+    // complete on the buffer's xfull barrier.  The consumed blocks are dropped from L2
+    // later, by the signal warp, once the group's MMAs are done.
+    if (lane == 0) {
+      int j = 0;
+      bool ok = true;
+      for (int e = 0; e < S && ok; ++e) {
+        const TCStage& st = plan.st[e];
+        const uint8_t* src = e == 0 ? a.x_in : a.bufs + int64_t(e - 1) * a.buf_stride;
+        const unsigned* cnt_in = a.counters + int64_t(e) * st.n_groups;
+        const uint32_t half = TF32 ? uint32_t(st.R8_in) * 512u : uint32_t(st.R8_in) * 256u;
+        const uint32_t xhalf = uint32_t(st.K_pad) * 256u;     // hi or lo half of the panel buffer
+        const int64_t blk = split_block_bytes(st.R8_in);
+        constexpr int kParts = TF32 ? 1 : 2;
+        for (int g = blockIdx.x; g < st.n_groups && ok; g += gridDim.x, ++j) {
+          const int xs = j % nxb;
+          const uint32_t xu = uint32_t(j / nxb);
+          bool fail = !wait_bar(&xempty[xs], (xu & 1u) ^ 1u, abort);
           // all c input blocks written by the previous stage
           if (!fail && e > 0) {
             const unsigned* cp = cnt_in + g;
             const uint64_t t0 = gtimer();
             while (ld_acquire(cp) < unsigned(c)) {
               if (*abort || *reinterpret_cast<volatile int*>(a.status) != 0) {
-                fail = 1;
+                fail = true;
                 break;
               }
               if (gtimer() - t0 > kTimeoutNs) {
                 atomicCAS(a.status, 0, ST_DEP_TIMEOUT);
-                fail = 1;
+                fail = true;
                 break;
               }
               __nanosleep(32);
             }
           }
-          if (fail) *abort = 1;
+          if (fail) {
+            *abort = 1;
+            ok = false;
+            break;
+          }
+          uint8_t* xb = xbuf + size_t(xs) * x_buf;
+          mbar_expect_tx(&xfull[xs], uint32_t(kParts * c) * half);
+          for (int t = 0; t < c; ++t) {
+            const uint8_t* sb = src + int64_t(pat_blk(st.in_pat, g, t, st, c)) * blk;
+            for (int hl = 0; hl < kParts; ++hl)
+              bulk_g2s(xb + uint32_t(hl) * xhalf + uint32_t(t) * half, sb + int64_t(hl) * half, half, &xfull[xs]);
+          }
         }
-        if (named_sync_or(3, 64, fail != 0)) {
+      }
+      // wait (bounded) for the copies of the last groups still in flight
+      for (int q = (j > nxb ? j - nxb : 0); q < j; ++q) {
+        const uint64_t t1 = gtimer();
+        while (!mbar_try(&xfull[q % nxb], uint32_t(q / nxb) & 1u) && gtimer() - t1 < kTimeoutNs) {
+        }
+      }
+    }
+  } else if (warp == 3 || warp == 13) {
+    // ---------------------------------------------------------------- L2 discards
+    // Once a group's MMAs are done (its panel buffer's xempty phase), its c input blocks
+    // are neither in shared memory nor read again: their lines are dropped from L2
+    // without a write-back.  Each discard takes a while, so two warps share them.
+    const int dt = (warp == 3 ? 0 : 32) + lane;
+    int j = 0;
+    bool ok = true;
+    for (int e = 0; e < S && ok; ++e) {
+      const TCStage& st = plan.st[e];
+      const uint8_t* src = e == 0 ? a.x_in : a.bufs + int64_t(e - 1) * a.buf_stride;
+      const int64_t blk = split_block_bytes(st.R8_in);
+      for (int g = blockIdx.x; g < st.n_groups && ok; g += gridDim.x, ++j) {
+        const int xs = j % nxb;
+        const uint32_t xu = uint32_t(j / nxb);
+        if (!__all_sync(0xffffffffu, wait_bar(&xempty[xs], xu & 1u, abort))) {
           ok = false;
           break;
         }
-        const uint32_t xb = sa(xbuf + size_t(xs) * x_buf);
         for (int t = 0; t < c; ++t) {
           const uint8_t* sb = src + int64_t(pat_blk(st.in_pat, g, t, st, c)) * blk;
-#pragma unroll 4
-          for (int q = xt; q < kParts * pieces; q += 64) {
-            const int hl = q >= pieces, pq = q - hl * pieces;
-            cp_async16(xb + uint32_t(hl) * xhalf + uint32_t(t) * half + uint32_t(pq) * 16u,
-                       sb + int64_t(hl) * half + int64_t(pq) * 16);
-          }
-        }
-        cp_async_wait_all();
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive(&xfull[xs]);
-        named_sync(3, 64);          // every thread's copies of the blocks have landed
-        for (int t = 0; t < c; ++t) {
-          const uint8_t* sb = src + int64_t(pat_blk(st.in_pat, g, t, st, c)) * blk;
-          for (int64_t q = xt; q < (blk >> 7); q += 64) l2_discard(sb + (q << 7));
+          for (int64_t q = dt; q < (blk >> 7); q += 64) l2_discard(sb + (q << 7));
         }
       }
     }
@@ -494,8 +520,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
     // ---------------------------------------------------------------- epilogue sets
     // TMEM lane tl is row tl of the panel: RHS n = tl / 2, real (ri = 0) or imaginary
     // (ri = 1) part, so the two halves of a complex output sit in adjacent lanes of one
-    // warp and pair by a shuffle.  Each warp works on its own: the next 16 columns'
-    // loads are in flight while the current ones are paired, split and stored.
+    // warp and pair by a shuffle.  Each warp works on its own.
     const int set = (warp - 4) >> 2;             // 0: warps 4-7, 1: warps 8-11
     const int quarter = warp & 3;                // TMEM lane quarter this warp may access
     const int tl = quarter * 32 + lane;
@@ -511,7 +536,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
       const uint32_t half = uint32_t(st.R8_out) * 256u;
       // pair, split and store the 16 accumulator columns c0 .. c0 + 15 (output rows of
       // the group) held in v1 (D1) and v2 (D2)
-      auto emit = [&](int g, int c0, const float (&v1)[kTcChunk], const float (&v2)[kTcChunk]) {
+      auto emit = [&](int g, int c0, const float* v1, const float* v2) {
         float y[kTcChunk];
 #pragma unroll
         for (int q = 0; q < kTcChunk; ++q) {
@@ -556,32 +581,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t d1 = taddr + uint32_t(set) * set_cols + lane_base, d2 = d1 + uint32_t(st.M_t);
-        float a1[kTcChunk], a2[kTcChunk], b1[kTcChunk], b2[kTcChunk];
-        tmem_ld16(d1, a1);
-        tmem_ld16(d2, a2);
-        tmem_wait_ld();
-        tmem_hold(a1, a2);
-        for (int c0 = 0; c0 < st.M_t; c0 += 2 * kTcChunk) {
-          const bool more = c0 + kTcChunk < st.M_t;
-          if (more) {
-            tmem_ld16(d1 + uint32_t(c0 + kTcChunk), b1);
-            tmem_ld16(d2 + uint32_t(c0 + kTcChunk), b2);
-          }
-          emit(g, c0, a1, a2);
+        // 32 columns of D1 and of D2 a round (M_t is a multiple of 32); the accumulator set
+        // is released to the MMA warp as soon as its last columns are in registers
+        for (int c0 = 0; c0 < st.M_t; c0 += 32) {
+          float v1[32], v2[32];
+          tmem_ld32(d1 + uint32_t(c0), v1);
+          tmem_ld32(d2 + uint32_t(c0), v2);
           tmem_wait_ld();
-          if (!more) break;
-          tmem_hold(b1, b2);
-          const bool more2 = c0 + 2 * kTcChunk < st.M_t;
-          if (more2) {
-            tmem_ld16(d1 + uint32_t(c0 + 2 * kTcChunk), a1);
-            tmem_ld16(d2 + uint32_t(c0 + 2 * kTcChunk), a2);
+          tmem_hold(v1, v2);
+          if (c0 + 32 >= st.M_t) {
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(&dempty[set]);
           }
-          emit(g, c0 + kTcChunk, b1, b2);
-          tmem_wait_ld();
-          if (more2) tmem_hold(a1, a2);
+          emit(g, c0, v1, v2);
+          emit(g, c0 + kTcChunk, v1 + kTcChunk, v2 + kTcChunk);
         }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        mbar_arrive(&dempty[set]);
         // hand the written blocks to the signal warp (which counts them in for the next
         // stage off this set's path); first make sure it took the set's previous group,
         // so that the two never get a full phase apart
@@ -755,7 +769,10 @@ __device__ __forceinline__ void store_split8(uint8_t* outs, int64_t leaf, int R8
 // One CTA per leaf bounds a CTA's work by the largest leaf, not the largest group (a
 // ragged tree puts several times the mean number of points into some groups).  The
 // panel rows are read by this CTA alone and never again: their L2 lines are discarded
-// rather than written back.  Empty leaves give zero blocks.
+// rather than written back.  With `gather` the rows come straight from g in natural
+// order through the tree permutation instead (no panel, no permute kernel): device
+// buffers take this route; page-locked host buffers keep the panel, read row by row.
+// Empty leaves give zero blocks.
 __device__ __forceinline__ void leaf_v_point(float2 (&acc)[8], const float2* vrow, float2 x) {
   const float4* vp = reinterpret_cast<const float4*>(vrow);
 #pragma unroll
@@ -778,10 +795,13 @@ __global__ void __launch_bounds__(kTcNR * kLeafMaxR8 / 8) leaf_v_kernel(const __
   using tc::l2_discard;
   constexpr int NR = kTcNR;
   extern __shared__ __align__(16) float2 lsm[];
+  __shared__ int nat[kLeafPts];            // gather: natural indices of the round's points
   const int j = blockIdx.x, c = a.c, g = j / c, R = a.R, R8 = a.R8, cap = a.pts_cap;
   const int tid = threadIdx.x, nth = int(blockDim.x), n = tid % NR, k0 = 8 * (tid / NR);
-  float2* xs = lsm;                        // [cap][NR]: the round's panel rows
-  float2* vs = lsm + cap * NR;             // [cap][R8]: conj V, zero for k >= R
+  // a gathered row is written one RHS per thread: padded to NR + 1 entries against bank conflicts
+  const int xstride = a.gather ? NR + 1 : NR;
+  float2* xs = lsm;                        // [cap][xstride]: the round's panel rows
+  float2* vs = lsm + cap * xstride;        // [cap][R8]: conj V, zero for k >= R
   const int pg = __ldg(a.off + c * g), p0 = __ldg(a.off + j), np = __ldg(a.off + j + 1) - p0;
   float2 acc[8];
 #pragma unroll
@@ -794,7 +814,28 @@ __global__ void __launch_bounds__(kTcNR * kLeafMaxR8 / 8) leaf_v_kernel(const __
       const int nb = min(cap, np - b0);
       if (b0 > 0) __syncthreads();         // previous round's shared reads done
       const float2* src = a.vec + int64_t(p0 + b0) * NR;
-      for (int q = tid; q < nb * (NR / 2); q += nth) cp_async16(sa(xs) + uint32_t(q) * 16u, src + 2 * q);
+      if (a.gather) {
+        // the round's points straight from g in natural order: thread q reads RHS
+        // q / nb of point q % nb, so that a warp's loads fall on a few nearby rows
+        for (int q = tid; q < nb; q += nth) nat[q] = __ldg(a.perm + p0 + b0 + q);
+        __syncthreads();
+        for (int q0 = tid; q0 < nb * NR; q0 += 4 * nth) {        // 4 loads in flight per thread
+          float2 v[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int q = q0 + u * nth, nn = q / nb, b = q - nn * nb, rhs = a.rhs0 + nn;
+            v[u] = (q < nb * NR && rhs < a.nrhs) ? __ldg(a.vec + int64_t(rhs) * a.len_vec + nat[b])
+                                                 : make_float2(0.f, 0.f);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int q = q0 + u * nth, nn = q / nb, b = q - nn * nb;
+            if (q < nb * NR) xs[b * xstride + nn] = v[u];
+          }
+        }
+      } else {
+        for (int q = tid; q < nb * (NR / 2); q += nth) cp_async16(sa(xs) + uint32_t(q) * 16u, src + 2 * q);
+      }
       for (int b1 = bq; b1 < nb; b1 += 8 * bstep) {             // 8 loads in flight per thread
         float2 v[8];
 #pragma unroll
@@ -816,22 +857,27 @@ __global__ void __launch_bounds__(kTcNR * kLeafMaxR8 / 8) leaf_v_kernel(const __
       }
       cp_async_wait_all();
       __syncthreads();
-      const char* lines = reinterpret_cast<const char*>(src);
-      for (int q = tid; q < nb * (NR * int(sizeof(float2)) / 128); q += nth) l2_discard(lines + 128 * q);
+      if (!a.gather) {   // the panel rows are read by this CTA alone and never again
+        const char* lines = reinterpret_cast<const char*>(src);
+        for (int q = tid; q < nb * (NR * int(sizeof(float2)) / 128); q += nth) l2_discard(lines + 128 * q);
+      }
 #pragma unroll 4
-      for (int b = 0; b < nb; ++b) leaf_v_point(acc, vs + b * R8 + k0, xs[b * NR + n]);
+      for (int b = 0; b < nb; ++b) leaf_v_point(acc, vs + b * R8 + k0, xs[b * xstride + n]);
     }
   }
   store_split8<TF32>(a.outs, j, R8, n, k0, acc);
 }
 
-// U^L for a panel, one CTA per group g (leaves i = c g + t):
+// U^L for a panel, one CTA per group g (leaves i = c g + t) or, with leaf_split, one
+// CTA per leaf:
 //   u[rhs0 + n][x_perm(b)] (+)= sum_k U^L_i[b][k] w[i R + k][n]
 // for the points b of leaf i.  The group's item is stored by columns (line = k, entry =
-// point of the group); the coefficient rows of the group's c leaves are c R contiguous
-// rows of 64 real then 64 imaginary parts, staged whole in shared memory.  Thread
+// point of the group); the coefficient rows of the CTA's leaves (R contiguous rows of
+// 64 real then 64 imaginary parts per leaf) are staged whole in shared memory.  Thread
 // (b, nq) computes point b of the round for the 16 RHS n = 16 nq + 0..15, so that a
-// warp stores 32 consecutive points of one RHS row.
+// warp stores 32 consecutive points of one RHS row.  One CTA per leaf bounds a CTA's
+// work by the largest leaf when a ragged tree puts several times the mean number of
+// points into some groups.
 // XPOSE (the adjoint's V^L leaf products): the group's item is a (V^L)^* item (line =
 // point, entry = k, conj V), read transposed and conjugated.
 template <bool XPOSE>
@@ -839,19 +885,23 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_u_kernel(const __grid_const
   constexpr int NR = kTcNR, NQ = kLeafThreads / kLeafPts, MN = NR / NQ;
   extern __shared__ __align__(16) float2 lsm[];
   __shared__ int lend[kLeafMaxC + 1];
-  const int g = blockIdx.x, c = a.c, R = a.R;
+  const int c = a.c, R = a.R;
+  const int g = a.leaf_split ? int(blockIdx.x) / c : int(blockIdx.x);
+  const int t0 = a.leaf_split ? int(blockIdx.x) - g * c : 0, nl = a.leaf_split ? 1 : c;   // leaves t0 .. t0 + nl - 1
   const int tid = threadIdx.x;
-  const int pg = a.off[c * g], np = a.off[c * g + c] - pg;
+  const int pg = a.off[c * g];
+  const int pb = a.off[c * g + t0] - pg, np = a.off[c * g + t0 + nl] - pg - pb;   // points, group-relative
   if (np == 0) return;
   if (tid <= c) lend[tid] = a.off[c * g + tid] - pg;
   const Item it = a.items[a.item_base + int64_t(g) * a.item_stride];
   const uint8_t* ibase = a.arena + size_t(it.off128) * 128;
-  float* ws = reinterpret_cast<float*>(lsm);                       // [c R][2 NR]
-  float2* us = reinterpret_cast<float2*>(ws + size_t(c) * R * 2 * NR);   // [R][kLeafPts]
+  float* ws = reinterpret_cast<float*>(lsm);                        // [nl R][2 NR]
+  float2* us = reinterpret_cast<float2*>(ws + size_t(nl) * R * 2 * NR);   // [R][kLeafPts]
+  const float* rows_g = a.wl + (int64_t(c) * g + t0) * R * 2 * NR;     // the CTA's leaves' rows
   {
-    const float4* src = reinterpret_cast<const float4*>(a.wl + int64_t(c) * g * R * 2 * NR);
+    const float4* src = reinterpret_cast<const float4*>(rows_g);
     float4* dst = reinterpret_cast<float4*>(ws);
-    const int nq4 = c * R * (2 * NR / 4);
+    const int nq4 = nl * R * (2 * NR / 4);
     for (int q0 = tid; q0 < nq4; q0 += 8 * kLeafThreads) {      // 8 loads in flight per thread
       float4 v[8];
 #pragma unroll
@@ -864,10 +914,10 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_u_kernel(const __grid_const
   }
   const int bb = tid % kLeafPts, nq = tid / kLeafPts;
   __syncthreads();
-  {   // the group's rows are read by this CTA alone and never again: drop them from L2
+  {   // the rows are read by this CTA alone and never again: drop them from L2
     using tc::l2_discard;
-    const char* rows = reinterpret_cast<const char*>(a.wl + int64_t(c) * g * R * 2 * NR);
-    for (int q = tid; q < c * R * (2 * NR * int(sizeof(float)) / 128); q += kLeafThreads) l2_discard(rows + 128 * q);
+    const char* rows = reinterpret_cast<const char*>(rows_g);
+    for (int q = tid; q < nl * R * (2 * NR * int(sizeof(float)) / 128); q += kLeafThreads) l2_discard(rows + 128 * q);
   }
   for (int b0 = 0; b0 < np; b0 += kLeafPts) {
     const int nb = min(kLeafPts, np - b0);
@@ -879,10 +929,10 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_u_kernel(const __grid_const
         const int q = q0 + u * kLeafThreads, k = q / nb, b = q - k * nb;
         if (q < R * nb) {
           if (XPOSE) {
-            const float2 e = item_entry(ibase, it, b0 + b, k);
+            const float2 e = item_entry(ibase, it, pb + b0 + b, k);
             v[u] = make_float2(e.x, -e.y);
           } else {
-            v[u] = item_entry(ibase, it, k, b0 + b);
+            v[u] = item_entry(ibase, it, k, pb + b0 + b);
           }
         } else {
           v[u] = make_float2(0.f, 0.f);
@@ -896,10 +946,10 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_u_kernel(const __grid_const
     }
     __syncthreads();
     if (bb < nb) {
-      const int p = b0 + bb;
-      int t = 0;
-      while (t + 1 < c && p >= lend[t + 1]) ++t;
-      const float* wr = ws + size_t(t) * R * 2 * NR + MN * nq;
+      const int p = pb + b0 + bb;                 // group-relative point
+      int t = t0;
+      while (t + 1 < t0 + nl && p >= lend[t + 1]) ++t;
+      const float* wr = ws + size_t(t - t0) * R * 2 * NR + MN * nq;
       float2 acc[MN];
 #pragma unroll
       for (int j = 0; j < MN; ++j) acc[j] = make_float2(0.f, 0.f);
@@ -949,7 +999,7 @@ size_t tc_smem_bytes(int nsa, int nxb, int nsets, int mt_max, int kpad_max) {
 size_t leaf_smem_bytes(int R, int c, bool u_side, int pts_cap) {
   const int R8 = (R + 7) & ~7;
   return u_side ? size_t(c) * R * 2 * kTcNR * sizeof(float) + size_t(R) * kLeafPts * sizeof(float2)
-                : sizeof(float2) * size_t(pts_cap) * (kTcNR + R8);
+                : sizeof(float2) * size_t(pts_cap) * (kTcNR + 1 + R8);
 }
 
 int leaf_pts_cap(int64_t max_leaf_points) {
@@ -1060,14 +1110,15 @@ cudaError_t launch_permute_in(const LeafArgs& a, cudaStream_t stream) {
 }
 
 cudaError_t launch_leaf(const LeafArgs& a, bool u_side, int n_groups, cudaStream_t stream, bool tf32, bool xpose) {
-  const size_t smem = u_side ? leaf_smem_bytes(a.R, a.c, true) : sizeof(float2) * size_t(a.pts_cap) * (kTcNR + a.R8);
+  const size_t smem = u_side ? leaf_smem_bytes(a.R, a.leaf_split ? 1 : a.c, true)
+                             : sizeof(float2) * size_t(a.pts_cap) * (kTcNR + (a.gather ? 1 : 0) + a.R8);
   void (*kern)(LeafArgs) =
       u_side ? (xpose ? leaf_u_kernel<true> : leaf_u_kernel<false>)
              : (tf32 ? (xpose ? leaf_v_kernel<true, true> : leaf_v_kernel<true, false>)
                      : (xpose ? leaf_v_kernel<false, true> : leaf_v_kernel<false, false>));
   // U^L: a CTA per group; (V^L)^*: a CTA per leaf, one thread per RHS column and group of 8 rows
   const int threads = u_side ? kLeafThreads : kTcNR * (a.R8 / 8);
-  const int64_t blocks = u_side ? int64_t(n_groups) : int64_t(n_groups) * a.c;
+  const int64_t blocks = (u_side && !a.leaf_split) ? int64_t(n_groups) : int64_t(n_groups) * a.c;
   if (!u_side && (a.pts_cap < 8 || a.pts_cap > kLeafPts || a.pts_cap % 8 != 0)) return cudaErrorInvalidValue;
   if (blocks <= 0) return cudaSuccess;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));

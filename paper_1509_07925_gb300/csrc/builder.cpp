@@ -249,14 +249,30 @@ void parallel_for(int64_t count, int threads, F&& fn) {
 void problem_trees(const mbf_problem_t& prob, Tree& xt, Tree& wt) {
   const int d = prob.dim, n = prob.n, L = prob.L;
   if (d != 2 && d != 3) fail(MBF_ERR_INVALID, "dim must be 2 or 3");
-  if (n < 2 || (n & (n - 1)) != 0) fail(MBF_ERR_INVALID, "n must be a power of two");
   if (L < 2 || (L % 2) != 0) fail(MBF_ERR_INVALID, "L must be even and >= 2");
-  xt = tree_uniform(n, d, L);
+  if (prob.tree != MBF_TREE_POINTS) {
+    if (n < 2 || (n & (n - 1)) != 0) fail(MBF_ERR_INVALID, "n must be a power of two");
+    xt = tree_uniform(n, d, L);
+  }
   if (prob.tree == MBF_TREE_UNIFORM) {
     wt = tree_uniform(n, d, L);
   } else if (prob.tree == MBF_TREE_POLAR) {
     if (d != 2) fail(MBF_ERR_INVALID, "polar tree needs dim 2");
     wt = tree_polar(n, L);
+  } else if (prob.tree == MBF_TREE_POINTS) {
+    if (!prob.x_pts || !prob.w_pts || prob.n_x_pts <= 0 || prob.n_w_pts <= 0)
+      fail(MBF_ERR_INVALID, "explicit point sets need x_pts and w_pts");
+    if (!(prob.w_side > 0)) fail(MBF_ERR_INVALID, "explicit point sets need w_side > 0");
+    std::vector<double> xp(prob.x_pts, prob.x_pts + prob.n_x_pts * d), wp(prob.w_pts, prob.w_pts + prob.n_w_pts * d);
+    for (double v : xp)
+      if (!(v >= 0.0 && v < 1.0)) fail(MBF_ERR_INVALID, "x_pts outside [0,1)^dim");
+    for (double v : wp)
+      if (!(v >= prob.w_lo && v < prob.w_lo + prob.w_side)) fail(MBF_ERR_INVALID, "w_pts outside the square");
+    std::vector<int64_t> xi(size_t(prob.n_x_pts)), wi(size_t(prob.n_w_pts));
+    for (int64_t q = 0; q < prob.n_x_pts; ++q) xi[size_t(q)] = q;
+    for (int64_t q = 0; q < prob.n_w_pts; ++q) wi[size_t(q)] = q;
+    xt = tree_square(xp, xi, d, 0.0, 1.0, L);
+    wt = tree_square(wp, wi, d, prob.w_lo, prob.w_side, L);
   } else if (prob.tree == MBF_TREE_SQUARE) {
     if (!prob.w_index || prob.n_w <= 0) fail(MBF_ERR_INVALID, "square tree needs w_index");
     if (!(prob.w_side > 0)) fail(MBF_ERR_INVALID, "square tree needs w_side > 0");
@@ -280,7 +296,8 @@ void problem_trees(const mbf_problem_t& prob, Tree& xt, Tree& wt) {
 // Shapes of the padded factor set of a problem (the interchange layout of mbf_factors_t):
 // padded rank caps R_h = min(r, max |A^h|, max |B^h|), R_{l+1} = min(r, max |node at l+1|,
 // c R_l) on each side, leaf arrays at the largest leaf, every array zero.
-void layout_factor_set(int d, int L, int64_t r, int64_t N, const Tree& xt, const Tree& wt, FactorSet& fs) {
+void layout_factor_set(int d, int L, int64_t r, int64_t N_out, int64_t N_in, const Tree& xt, const Tree& wt,
+                       FactorSet& fs) {
   const int c = 1 << d, h = L / 2;
   auto max_size = [&](const Tree& T, int l) {
     int64_t mx = 0;
@@ -289,8 +306,8 @@ void layout_factor_set(int d, int L, int64_t r, int64_t N, const Tree& xt, const
   };
   fs.d = d;
   fs.L = L;
-  fs.n_out = N;
-  fs.n_in = N;
+  fs.n_out = N_out;
+  fs.n_in = N_in;
   fs.n_w = int64_t(wt.perm.size());
   fs.RU.assign(size_t(L + 1), 0);
   fs.RV.assign(size_t(L + 1), 0);
@@ -484,7 +501,8 @@ struct Builder {
     c = 1 << d;
     h = L / 2;
     if (d != 2 && d != 3) fail(MBF_ERR_INVALID, "dim must be 2 or 3");
-    if (n < 2 || (n & (n - 1)) != 0) fail(MBF_ERR_INVALID, "n must be a power of two");
+    if (prob.tree != MBF_TREE_POINTS && (n < 2 || (n & (n - 1)) != 0))
+      fail(MBF_ERR_INVALID, "n must be a power of two");
     if (L < 2 || (L % 2) != 0) fail(MBF_ERR_INVALID, "L must be even and >= 2");
     if (r < 1) fail(MBF_ERR_INVALID, "r must be >= 1");
     if (!fn) fail(MBF_ERR_INVALID, "entry function is NULL");
@@ -494,22 +512,34 @@ struct Builder {
     if (opts.threads <= 0) opts.threads = int(std::max(1u, std::thread::hardware_concurrency()));
     gram_cut = std::max(opts.tol * opts.tol, 1e-13);
 
-    int64_t N = 1;
-    for (int k = 0; k < d; ++k) N *= n;
-    xcoord.resize(size_t(N * d));
-    wcoord.resize(size_t(N * d));
-    for (int64_t p = 0; p < N; ++p) {
-      int64_t q = p;
-      for (int k = d - 1; k >= 0; --k) {
-        const int64_t digit = q % n;
-        q /= n;
-        xcoord[size_t(p * d + k)] = double(digit) / double(n);
-        wcoord[size_t(p * d + k)] = double(digit) - double(n / 2);
+    int64_t N_out = 0, N_in = 0;
+    if (prob.tree == MBF_TREE_POINTS) {
+      // explicit point sets (§2.6): coordinates as given, natural order = array order
+      N_out = prob.n_x_pts;
+      N_in = prob.n_w_pts;
+      if (prob.x_pts && prob.w_pts && N_out > 0 && N_in > 0) {
+        xcoord.assign(prob.x_pts, prob.x_pts + N_out * d);
+        wcoord.assign(prob.w_pts, prob.w_pts + N_in * d);
+      }
+    } else {
+      int64_t N = 1;
+      for (int k = 0; k < d; ++k) N *= n;
+      N_out = N_in = N;
+      xcoord.resize(size_t(N * d));
+      wcoord.resize(size_t(N * d));
+      for (int64_t p = 0; p < N; ++p) {
+        int64_t q = p;
+        for (int k = d - 1; k >= 0; --k) {
+          const int64_t digit = q % n;
+          q /= n;
+          xcoord[size_t(p * d + k)] = double(digit) / double(n);
+          wcoord[size_t(p * d + k)] = double(digit) - double(n / 2);
+        }
       }
     }
     problem_trees(prob, xt, wt);
 
-    layout_factor_set(d, L, r, N, xt, wt, fs);
+    layout_factor_set(d, L, r, N_out, N_in, xt, wt, fs);
     kU.assign(size_t(L + 1), {});
     kV.assign(size_t(L + 1), {});
     const int64_t nL = ip(c, L);

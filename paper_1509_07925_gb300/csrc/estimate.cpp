@@ -88,7 +88,7 @@ double estimate_error(mbf_op_s* op, mbf_entry_fn fn, void* ctx, int32_t n_sample
   cudaFree(dg);
   cudaFree(du);
   int status = 0;
-  check(cudaMemcpy(&status, op->d_status, sizeof(int), cudaMemcpyDeviceToHost), "read status");
+  check(cudaMemcpy(&status, op->ws.status, sizeof(int), cudaMemcpyDeviceToHost), "read status");
   if (status != 0) fail(MBF_ERR_TIMEOUT, "estimate: a device wait of the apply gave up");
 
   // S: n_samples distinct outputs (partial Fisher-Yates on a counter-based stream)

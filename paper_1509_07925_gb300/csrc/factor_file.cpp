@@ -275,12 +275,19 @@ std::vector<KernelEntry> kernel_entries(const mbf_problem_t& prob, const FactorS
     q.x = fs.x_perm[size_t((int64_t(k) * 7919) % fs.n_out)];
     q.xi = fs.w_perm[size_t((int64_t(k) * 104729 + 3) % fs.n_w)];
     double x[3], xi[3], out[2];
-    int64_t a = q.x, b = q.xi;
-    for (int t = d - 1; t >= 0; --t) {
-      x[t] = double(a % n) / n;
-      xi[t] = double(b % n) - n / 2;
-      a /= n;
-      b /= n;
+    if (prob.tree == MBF_TREE_POINTS) {
+      for (int t = 0; t < d; ++t) {
+        x[t] = prob.x_pts[q.x * d + t];
+        xi[t] = prob.w_pts[q.xi * d + t];
+      }
+    } else {
+      int64_t a = q.x, b = q.xi;
+      for (int t = d - 1; t >= 0; --t) {
+        x[t] = double(a % n) / n;
+        xi[t] = double(b % n) - n / 2;
+        a /= n;
+        b /= n;
+      }
     }
     fn(x, 1, xi, 1, d, out, ctx);
     q.re = out[0];
@@ -350,7 +357,8 @@ FactorSet build_or_load(const mbf_problem_t& prob, mbf_entry_fn fn, void* ctx, c
     problem_trees(prob, xt, wt);
     const std::string who = std::string("factor file ") + path + " was built for another problem: ";
     if (fs.d != prob.dim || fs.L != prob.L) fail(MBF_ERR_INVALID, who + "dim or L");
-    if (fs.x_perm != xt.perm || fs.x_off != xt.off || fs.n_in != Tree::ipow(prob.n, prob.dim))
+    const int64_t n_in = prob.tree == MBF_TREE_POINTS ? prob.n_w_pts : Tree::ipow(prob.n, prob.dim);
+    if (fs.x_perm != xt.perm || fs.x_off != xt.off || fs.n_in != n_in)
       fail(MBF_ERR_INVALID, who + "X tree or grid size");
     if (fs.w_perm != wt.perm || fs.w_off != wt.off) fail(MBF_ERR_INVALID, who + "Omega tree or point set");
     for (int l = fs.L / 2; l <= fs.L; ++l)

@@ -100,11 +100,9 @@ FactorSet build_factors(const mbf_problem_t& prob, mbf_entry_fn fn, void* ctx,
                         const mbf_build_opts_t& opts);
 // Padded factor-set shapes (ranks capped per level, zero arrays) and the algorithmic
 // nonzeros from true ranks rank[level][node * c^(L - level) + other] (builder.cpp).
-void layout_factor_set(int d, int L, int64_t r, int64_t N, const Tree& xt, const Tree& wt, FactorSet& fs);
+void layout_factor_set(int d, int L, int64_t r, int64_t N_out, int64_t N_in, const Tree& xt, const Tree& wt,
+                       FactorSet& fs);
 int64_t factor_nnz(int c, int L, const Tree& xt, const Tree& wt, const std::vector<std::vector<int32_t>>& kU,
                    const std::vector<std::vector<int32_t>>& kV);
-// Construction on the current CUDA device (build_gpu.cu) for a built-in kernel:
-// 0 = DFT, 1 = isotropic FIO, 2 = Example-1 FIO.  Same factor set layout.
-FactorSet build_factors_gpu(const mbf_problem_t& prob, int kernel_id, const mbf_build_opts_t& opts);
 
 }  // namespace mbf

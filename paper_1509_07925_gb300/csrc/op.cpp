@@ -482,36 +482,38 @@ void op_free(mbf_op_s* op) {
   int prev = 0;
   cudaGetDevice(&prev);
   cudaSetDevice(op->device);
+  for (Workspace* w : op->ws_pool) {
+    ws_free(*w);
+    delete w;
+  }
   cudaFree(op->d_arena);
   cudaFree(op->d_items);
   cudaFree(op->d_x_perm);
   cudaFree(op->d_x_off);
   cudaFree(op->d_w_perm);
   cudaFree(op->d_w_off);
-  cudaFree(op->d_bufs);
-  cudaFree(op->d_barrier);
-  cudaFree(op->d_status);
+  ws_free(op->ws);
   cudaFree(op->d_stage_in);
   cudaFree(op->d_stage_out);
   cudaFree(op->d_tc_arena);
   cudaFree(op->d_tc_arena_tf32);
   cudaFree(op->d_tc_arena_adj);
   cudaFree(op->d_x_inv);
-  cudaFree(op->d_tc_bufs);
   for (auto& r : op->prof_pending) {
     cudaEventDestroy(r.e0);
     cudaEventDestroy(r.e1);
   }
-  cudaFree(op->d_tc_counters);
-  cudaFree(op->d_tc_gt);
   cudaFree(op->d_w_inv);
   cudaSetDevice(prev);
   delete op;
 }
 
+std::atomic<uint64_t> g_op_serial{0};
+
 mbf_op_s* op_create(const mbf_factors_t& f) {
   validate_factors(f);
   auto* op = new mbf_op_s();
+  op->serial = ++g_op_serial;
   try {
     op->d = f.dim;
     op->c = 1 << f.dim;
@@ -545,16 +547,25 @@ mbf_op_s* op_create(const mbf_factors_t& f) {
       op->leaf_pts_x = std::max(op->leaf_pts_x, f.x_off[q + 1] - f.x_off[q]);
       op->leaf_pts_w = std::max(op->leaf_pts_w, f.w_off[q + 1] - f.w_off[q]);
     }
+    // a tree whose largest group of c leaves holds more than twice the mean of the
+    // non-empty groups gets one CTA per leaf in the leaf kernels of its U^L side
+    auto ragged = [&](const int64_t* off) {
+      int64_t mx = 0, tot = 0, ne = 0;
+      for (int64_t gq = 0; gq < nL / op->c; ++gq) {
+        const int64_t np = off[(gq + 1) * op->c] - off[gq * op->c];
+        mx = std::max(mx, np);
+        tot += np;
+        ne += np > 0;
+      }
+      return ne > 0 && mx * ne > 2 * tot;
+    };
+    op->split_x = ragged(f.x_off) ? 1 : 0;
+    op->split_w = ragged(f.w_off) ? 1 : 0;
     op->d_x_perm = dev_upload(to32(f.x_perm, f.n_out), "x_perm");
     op->d_x_off = dev_upload(to32(f.x_off, nL + 1), "x_off");
     op->d_w_perm = dev_upload(to32(f.w_perm, std::max<int64_t>(f.n_w, 1)), "w_perm");
     op->d_w_off = dev_upload(to32(f.w_off, nL + 1), "w_off");
-    const size_t vbytes = size_t(op->plan.n_stages) * size_t(op->positions) * 4 * sizeof(float2);
-    if (dev_alloc(&op->d_bufs, vbytes) != cudaSuccess) fail(MBF_ERR_OOM, "cudaMalloc workspace");
-    if (dev_alloc(&op->d_barrier, 256 + counter_bytes(op->plan)) != cudaSuccess ||
-        dev_alloc(&op->d_status, 256) != cudaSuccess)
-      fail(MBF_ERR_OOM, "cudaMalloc barrier");
-    cuda_check(cudaMemset(op->d_status, 0, 256), "cudaMemset status");
+    ws_init(op, op->ws);
     for (int nrb : {1, 2, 4}) cuda_check(simt_config(nrb, &op->grid, &op->ns[nrb], &op->smem[nrb]), "simt_config");
     cuda_check(cudaDeviceGetAttribute(&op->sms, cudaDevAttrMultiProcessorCount, op->device), "attr");
     // tensor-core tiles (the multi-RHS path); an operator whose tiles do not fit keeps
@@ -582,7 +593,7 @@ mbf_op_s* op_create(const mbf_factors_t& f) {
         if (smem(2) > size_t(optin)) nxb = 1;
         if (smem(2) > size_t(optin)) fail(MBF_ERR_INVALID, "tiles too large for the tensor path");
         nsa = 2;
-        while (nsa < 8 && smem(nsa + 1) <= size_t(optin)) ++nsa;
+        while (nsa < 16 && smem(nsa + 1) <= size_t(optin)) ++nsa;
         sm = std::max(smem(nsa), size_t(optin) / 2 + 1024);
       };
       config(op->tc_mt_max, op->tc_kpad_max, op->tc_nsets, op->tc_nxb, op->tc_nsa, op->tc_smem);
@@ -677,13 +688,13 @@ void prof_collect(mbf_op_s* op) {
 // Tensor-core apply, per panel of 64 RHS: permute the panel into Omega-tree order, the
 // (V^L)^* leaf kernel, the persistent tcgen05 kernel over the G / H levels, the U^L leaf
 // kernel (which scatters u to natural order).
-void apply_tc(mbf_op_s* op, const float2* g, float2* u, int64_t nrhs, cudaStream_t st, int grid, bool accumulate,
-              bool tf32) {
+void apply_tc(mbf_op_s* op, Workspace& w, const float2* g, float2* u, int64_t nrhs, cudaStream_t st, int grid, bool accumulate,
+              bool host_io, bool tf32) {
   if (!op->tc_unavailable.empty()) fail(MBF_ERR_INVALID, "tensor path unavailable: " + op->tc_unavailable);
   const TCPlan& tp = op->tcplan;
   const int S = tp.n_stages;
   const int64_t vec_bytes = tc_vec_bytes(op);
-  tc_prepare(op);
+  ws_prepare_tc(op, w);
   if (tf32 && !op->d_tc_arena_tf32) {   // first TF32 apply: convert the tiles (kept, like the split ones)
     if (dev_alloc(&op->d_tc_arena_tf32, size_t(op->tc_bytes)) != cudaSuccess) {
       op->d_tc_arena_tf32 = nullptr;
@@ -700,29 +711,38 @@ void apply_tc(mbf_op_s* op, const float2* g, float2* u, int64_t nrhs, cudaStream
   if (grid > 0) sms = std::min(sms, grid);
   const Stage& leaf_st = op->plan.st[0];
   const Stage& last_st = op->plan.st[op->plan.n_stages - 1];
-  uint8_t* yl = op->d_tc_bufs;                       // level-L input of the main stages
+  uint8_t* yl = w.tc_bufs;                       // level-L input of the main stages
   uint8_t* bufs = yl + vec_bytes;                    // main stage e < S - 1 writes bufs + e * vec_bytes
   float* ylast = reinterpret_cast<float*>(yl + int64_t(S) * vec_bytes);   // last main stage
   for (int64_t r0 = 0; r0 < nrhs; r0 += kTcNR) {
-    // g -> panel in tree order
-    LeafArgs pa{};
-    pa.perm = op->d_w_inv;
-    pa.vec = g;
-    pa.outp = op->d_tc_gt;
-    pa.len_vec = op->n_in;
-    pa.nrhs = int32_t(nrhs);
-    pa.rhs0 = int32_t(r0);
-    cudaEvent_t e0 = prof_begin(op, st);
-    cuda_check(launch_permute_in(pa, st), "panel permute launch");
-    prof_end(op, PK_PERMUTE, e0, st);
-    // (V^L)^*: panel -> yl
+    // page-locked host input: g -> panel in tree order first (rows read across the
+    // host link as 16-byte runs); device input: gathered by the leaf kernel itself
+    cudaEvent_t e0 = nullptr;
+    if (host_io) {
+      LeafArgs pa{};
+      pa.perm = op->d_w_inv;
+      pa.vec = g;
+      pa.outp = w.tc_gt;
+      pa.len_vec = op->n_in;
+      pa.nrhs = int32_t(nrhs);
+      pa.rhs0 = int32_t(r0);
+      e0 = prof_begin(op, st);
+      cuda_check(launch_permute_in(pa, st), "panel permute launch");
+      prof_end(op, PK_PERMUTE, e0, st);
+    }
+    // (V^L)^*: panel (or g) -> yl
     LeafArgs la{};
     la.arena = op->d_arena;
     la.items = op->d_items;
     la.item_base = leaf_st.item_base;
     la.item_stride = leaf_st.n_items;
     la.off = op->d_w_off;
-    la.vec = op->d_tc_gt;
+    la.vec = host_io ? w.tc_gt : g;
+    la.gather = host_io ? 0 : 1;
+    la.perm = op->d_w_perm;
+    la.len_vec = op->n_in;
+    la.nrhs = int32_t(nrhs);
+    la.rhs0 = int32_t(r0);
     la.outs = yl;
     la.c = op->c;
     la.R = op->RV[size_t(op->L)];
@@ -738,8 +758,8 @@ void apply_tc(mbf_op_s* op, const float2* g, float2* u, int64_t nrhs, cudaStream
     ta.bufs = bufs;
     ta.y_out = ylast;
     ta.buf_stride = vec_bytes;
-    ta.counters = op->d_tc_counters;
-    ta.status = op->d_status;
+    ta.counters = w.tc_counters;
+    ta.status = w.status;
     ta.nsa = op->tc_nsa;
     ta.nxb = op->tc_nxb;
     ta.nsets = op->tc_nsets;
@@ -765,6 +785,7 @@ void apply_tc(mbf_op_s* op, const float2* g, float2* u, int64_t nrhs, cudaStream
     lu.c = op->c;
     lu.R = op->RU[size_t(op->L)];
     lu.accumulate = accumulate ? 1 : 0;
+    lu.leaf_split = op->split_x;
     e0 = prof_begin(op, st);
     cuda_check(launch_leaf(lu, true, last_st.n_groups, st), "leaf U^L launch");
     prof_end(op, PK_LEAF_U, e0, st);
@@ -775,14 +796,15 @@ void apply_tc(mbf_op_s* op, const float2* g, float2* u, int64_t nrhs, cudaStream
 // order, the U^* leaf products (from the U^L items), the persistent tcgen05 kernel over
 // the reversed levels with conjugate-transposed tiles, the V^L leaf products (from the
 // (V^L)^* items) scattered to natural Omega order.
-void apply_tc_adj(mbf_op_s* op, const float2* u, float2* g, int64_t nrhs, cudaStream_t st, int grid, bool accumulate) {
+void apply_tc_adj(mbf_op_s* op, Workspace& w, const float2* u, float2* g, int64_t nrhs, cudaStream_t st, int grid,
+                  bool accumulate, bool host_io) {
   if (!op->tc_unavailable.empty()) fail(MBF_ERR_INVALID, "tensor path unavailable: " + op->tc_unavailable);
   if (!op->tc_adj_unavailable.empty()) fail(MBF_ERR_INVALID, "tensor adjoint unavailable: " + op->tc_adj_unavailable);
   const TCPlan& fp = op->tcplan;
   const TCPlan& ap = op->tcplan_adj;
   const int S = ap.n_stages;
   const int64_t vec_bytes = tc_vec_bytes(op);
-  tc_prepare(op);
+  ws_prepare_tc(op, w);
   if (!op->d_tc_arena_adj) {   // first adjoint apply: conjugate-transpose the tiles (kept)
     if (dev_alloc(&op->d_tc_arena_adj, size_t(op->tc_bytes)) != cudaSuccess) {
       op->d_tc_arena_adj = nullptr;
@@ -801,29 +823,37 @@ void apply_tc_adj(mbf_op_s* op, const float2* u, float2* g, int64_t nrhs, cudaSt
   if (grid > 0) sms = std::min(sms, grid);
   const Stage& leaf_st = op->plan.st[0];                        // (V^L)^* items
   const Stage& last_st = op->plan.st[op->plan.n_stages - 1];    // U^L items (item 1)
-  uint8_t* yl = op->d_tc_bufs;
+  uint8_t* yl = w.tc_bufs;
   uint8_t* bufs = yl + vec_bytes;
   float* ylast = reinterpret_cast<float*>(yl + int64_t(S) * vec_bytes);
   for (int64_t r0 = 0; r0 < nrhs; r0 += kTcNR) {
-    // u -> panel in X-tree order
-    LeafArgs pa{};
-    pa.perm = op->d_x_inv;
-    pa.vec = u;
-    pa.outp = op->d_tc_gt;
-    pa.len_vec = op->n_out;
-    pa.nrhs = int32_t(nrhs);
-    pa.rhs0 = int32_t(r0);
-    cudaEvent_t e0 = prof_begin(op, st);
-    cuda_check(launch_permute_in(pa, st), "panel permute launch");
-    prof_end(op, PK_PERMUTE, e0, st);
-    // (U^L)^*: panel -> yl (X-leaf blocks)
+    // u -> panel in X-tree order (page-locked host input), or gathered by the leaf kernel
+    cudaEvent_t e0 = nullptr;
+    if (host_io) {
+      LeafArgs pa{};
+      pa.perm = op->d_x_inv;
+      pa.vec = u;
+      pa.outp = w.tc_gt;
+      pa.len_vec = op->n_out;
+      pa.nrhs = int32_t(nrhs);
+      pa.rhs0 = int32_t(r0);
+      e0 = prof_begin(op, st);
+      cuda_check(launch_permute_in(pa, st), "panel permute launch");
+      prof_end(op, PK_PERMUTE, e0, st);
+    }
+    // (U^L)^*: panel (or u) -> yl (X-leaf blocks)
     LeafArgs la{};
     la.arena = op->d_arena;
     la.items = op->d_items;
     la.item_base = last_st.item_base + 1;
     la.item_stride = last_st.n_items;
     la.off = op->d_x_off;
-    la.vec = op->d_tc_gt;
+    la.vec = host_io ? w.tc_gt : u;
+    la.gather = host_io ? 0 : 1;
+    la.perm = op->d_x_perm;
+    la.len_vec = op->n_out;
+    la.nrhs = int32_t(nrhs);
+    la.rhs0 = int32_t(r0);
     la.outs = yl;
     la.c = op->c;
     la.R = op->RU[size_t(op->L)];
@@ -839,8 +869,8 @@ void apply_tc_adj(mbf_op_s* op, const float2* u, float2* g, int64_t nrhs, cudaSt
     ta.bufs = bufs;
     ta.y_out = ylast;
     ta.buf_stride = vec_bytes;
-    ta.counters = op->d_tc_counters;
-    ta.status = op->d_status;
+    ta.counters = w.tc_counters;
+    ta.status = w.status;
     ta.nsa = op->tca_nsa;
     ta.nxb = op->tca_nxb;
     ta.nsets = op->tca_nsets;
@@ -866,6 +896,7 @@ void apply_tc_adj(mbf_op_s* op, const float2* u, float2* g, int64_t nrhs, cudaSt
     lv.c = op->c;
     lv.R = op->RV[size_t(op->L)];
     lv.accumulate = accumulate ? 1 : 0;
+    lv.leaf_split = op->split_w;
     e0 = prof_begin(op, st);
     cuda_check(launch_leaf(lv, true, leaf_st.n_groups, st, false, true), "leaf V^L launch");
     prof_end(op, PK_LEAF_U, e0, st);
@@ -873,8 +904,9 @@ void apply_tc_adj(mbf_op_s* op, const float2* u, float2* g, int64_t nrhs, cudaSt
 }
 
 void apply_impl(mbf_op_s* op, const void* in, void* out, int64_t nrhs, int32_t precision, void* stream,
-                bool adj, int grid = 0, bool accumulate = false) {
+                bool adj, int grid = 0, bool accumulate = false, Workspace* ws = nullptr, bool host_io = false) {
   if (!op) fail(MBF_ERR_INVALID, "operator is NULL");
+  Workspace& w = ws ? *ws : op->ws;
   if (nrhs < 0) fail(MBF_ERR_INVALID, "nrhs < 0");
   if (nrhs == 0) return;
   if ((!in || !out)) fail(MBF_ERR_INVALID, "NULL vector");
@@ -886,10 +918,11 @@ void apply_impl(mbf_op_s* op, const void* in, void* out, int64_t nrhs, int32_t p
   if (uses_tensor(op, nrhs, precision, adj)) {
     if (adj) {
       if (precision == MBF_PREC_TF32) fail(MBF_ERR_INVALID, "TF32 operands apply the forward operator only");
-      apply_tc_adj(op, static_cast<const float2*>(in), static_cast<float2*>(out), nrhs, st, grid, accumulate);
+      apply_tc_adj(op, w, static_cast<const float2*>(in), static_cast<float2*>(out), nrhs, st, grid, accumulate,
+                   host_io);
       return;
     }
-    apply_tc(op, static_cast<const float2*>(in), static_cast<float2*>(out), nrhs, st, grid, accumulate,
+    apply_tc(op, w, static_cast<const float2*>(in), static_cast<float2*>(out), nrhs, st, grid, accumulate, host_io,
              precision == MBF_PREC_TF32);
     return;
   }
@@ -906,11 +939,11 @@ void apply_impl(mbf_op_s* op, const void* in, void* out, int64_t nrhs, int32_t p
   a.out = static_cast<float2*>(out);
   a.in_len = adj ? op->n_out : op->n_in;
   a.out_len = adj ? op->n_in : op->n_out;
-  a.bufs = op->d_bufs;
+  a.bufs = w.bufs;
   a.buf_stride = op->positions * nrb;
-  a.barrier = op->d_barrier;
-  a.counters = op->d_barrier + 64;
-  a.status = op->d_status;
+  a.barrier = w.barrier;
+  a.counters = w.barrier + 64;
+  a.status = w.status;
   a.nrhs = int32_t(nrhs);
   a.n_pass = int32_t((nrhs + nrb - 1) / nrb);
   a.n_slots = op->ns[nrb];
@@ -971,22 +1004,91 @@ int64_t tc_vec_bytes(const mbf_op_s* op) {
   return Tree::ipow(op->c, op->L) * split_block_bytes(r8max);
 }
 
-// Allocate the tensor-path workspace (first use), so that later applies allocate nothing.
-void tc_prepare(mbf_op_s* op) {
-  if (op->d_tc_bufs || !op->tc_unavailable.empty()) return;
+// Workspaces.  The SIMT parts at operator creation; the tensor path's on its first use
+// (or through tc_prepare / the server before a capture), so later applies allocate
+// nothing.
+void ws_init(const mbf_op_s* op, Workspace& w) {
+  const size_t vbytes = size_t(op->plan.n_stages) * size_t(op->positions) * 4 * sizeof(float2);
+  if (dev_alloc(&w.bufs, vbytes) != cudaSuccess) fail(MBF_ERR_OOM, "cudaMalloc workspace");
+  if (dev_alloc(&w.barrier, 256 + counter_bytes(op->plan)) != cudaSuccess || dev_alloc(&w.status, 256) != cudaSuccess)
+    fail(MBF_ERR_OOM, "cudaMalloc barrier");
+  cuda_check(cudaMemset(w.status, 0, 256), "cudaMemset status");
+}
+
+void ws_prepare_tc(const mbf_op_s* op, Workspace& w) {
+  if (w.tc_bufs || !op->tc_unavailable.empty()) return;
   const int S = op->tcplan.n_stages;
   const int64_t vec_bytes = tc_vec_bytes(op);
-  if (dev_alloc(&op->d_tc_bufs, size_t(S + 1) * size_t(vec_bytes)) != cudaSuccess)
+  if (dev_alloc(&w.tc_bufs, size_t(S + 1) * size_t(vec_bytes)) != cudaSuccess)
     fail(MBF_ERR_OOM, "cudaMalloc tensor-path workspace");
-  if (dev_alloc(&op->d_tc_counters, tc_counter_bytes(op->tcplan)) != cudaSuccess)
+  if (dev_alloc(&w.tc_counters, tc_counter_bytes(op->tcplan)) != cudaSuccess)
     fail(MBF_ERR_OOM, "cudaMalloc tensor-path counters");
-  if (dev_alloc(&op->d_tc_gt, size_t(std::max<int64_t>({op->n_w, op->n_out, 1})) * kTcNR * sizeof(float2)) != cudaSuccess)
+  if (dev_alloc(&w.tc_gt, size_t(std::max<int64_t>({op->n_w, op->n_out, 1})) * kTcNR * sizeof(float2)) != cudaSuccess)
     fail(MBF_ERR_OOM, "cudaMalloc tensor-path input panel");
 }
 
+void ws_free(Workspace& w) {
+  cudaFree(w.bufs);
+  cudaFree(w.barrier);
+  cudaFree(w.status);
+  cudaFree(w.tc_bufs);
+  cudaFree(w.tc_counters);
+  cudaFree(w.tc_gt);
+  w = Workspace{};
+}
+
+void tc_prepare(mbf_op_s* op) { ws_prepare_tc(op, op->ws); }
+
+Workspace* ws_acquire(mbf_op_s* op, bool tensor) {
+  std::lock_guard<std::mutex> lk(op->ws_mu);
+  Workspace* w = nullptr;
+  if (!op->ws_own_lent) {
+    op->ws_own_lent = true;
+    w = &op->ws;
+  } else {
+    for (size_t k = 0; k < op->ws_pool.size() && !w; ++k)
+      if (!op->ws_pool_lent[k]) {
+        op->ws_pool_lent[k] = true;
+        w = op->ws_pool[k];
+      }
+    if (!w) {
+      auto* nw = new Workspace();
+      try {
+        ws_init(op, *nw);
+      } catch (...) {
+        ws_free(*nw);
+        delete nw;
+        throw;
+      }
+      op->ws_pool.push_back(nw);
+      op->ws_pool_lent.push_back(true);
+      w = nw;
+    }
+  }
+  try {
+    if (tensor) ws_prepare_tc(op, *w);
+  } catch (...) {
+    if (w == &op->ws) op->ws_own_lent = false;
+    for (size_t k = 0; k < op->ws_pool.size(); ++k)
+      if (op->ws_pool[k] == w) op->ws_pool_lent[k] = false;
+    throw;
+  }
+  return w;
+}
+
+void ws_release(mbf_op_s* op, Workspace* w) {
+  std::lock_guard<std::mutex> lk(op->ws_mu);
+  if (w == &op->ws) {
+    op->ws_own_lent = false;
+    return;
+  }
+  for (size_t k = 0; k < op->ws_pool.size(); ++k)
+    if (op->ws_pool[k] == w) op->ws_pool_lent[k] = false;
+}
+
 void apply_dev(mbf_op_s* op, const void* in, void* out, int64_t nrhs, int32_t precision, cudaStream_t st,
-               bool adj, int grid, bool accumulate) {
-  apply_impl(op, in, out, nrhs, precision, st, adj, grid, accumulate);
+               bool adj, int grid, bool accumulate, Workspace* ws) {
+  apply_impl(op, in, out, nrhs, precision, st, adj, grid, accumulate, ws);
 }
 
 }  // namespace mbf
@@ -1065,8 +1167,8 @@ mbf_status mbf_build_from_entries(const mbf_problem_t* prob, mbf_entry_fn fn, vo
     mbf_op_s* op = op_create(v);
     fs = FactorSet{};
     try {
-      // the §3.3 estimator on 256 sampled outputs, kept for mbf_op_info
-      estimate_error(op, fn, ctx, 256, o.seed ^ 0x6570735f65737469ull, nullptr);
+      // the §3.3 estimator on 256 sampled outputs, kept for mbf_op_info (grid problems)
+      if (prob->tree != MBF_TREE_POINTS) estimate_error(op, fn, ctx, 256, o.seed ^ 0x6570735f65737469ull, nullptr);
     } catch (...) {
       op_free(op);
       throw;
@@ -1175,7 +1277,7 @@ mbf_status mbf_apply_host(mbf_op_t op, const void* g_host, void* u_host, int64_t
       cudaPointerAttributes ag{}, au{};
       if (cudaPointerGetAttributes(&ag, g_host) == cudaSuccess && cudaPointerGetAttributes(&au, u_host) == cudaSuccess &&
           ag.type == cudaMemoryTypeHost && au.type == cudaMemoryTypeHost && ag.devicePointer && au.devicePointer) {
-        apply_impl(op, ag.devicePointer, au.devicePointer, nrhs, precision, stream, false);
+        apply_impl(op, ag.devicePointer, au.devicePointer, nrhs, precision, stream, false, 0, false, nullptr, true);
         cuda_check(cudaStreamSynchronize(st), "sync");
         return;
       }
@@ -1221,9 +1323,9 @@ mbf_status mbf_op_check(mbf_op_t op, void* stream) {
     if (!op) fail(MBF_ERR_INVALID, "NULL operator");
     cuda_check(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)), "cudaStreamSynchronize");
     int st = 0;
-    cuda_check(cudaMemcpy(&st, op->d_status, sizeof(int), cudaMemcpyDeviceToHost), "read status");
+    cuda_check(cudaMemcpy(&st, op->ws.status, sizeof(int), cudaMemcpyDeviceToHost), "read status");
     if (st != ST_OK) {
-      cuda_check(cudaMemset(op->d_status, 0, sizeof(int)), "clear status");
+      cuda_check(cudaMemset(op->ws.status, 0, sizeof(int)), "clear status");
       static const char* names[] = {"ok", "grid barrier", "full mbarrier", "empty mbarrier", "bad item",
                                     "dependency counter"};
       fail(MBF_ERR_TIMEOUT, std::string("device wait gave up: ") + (st >= 0 && st <= 5 ? names[st] : "unknown"));

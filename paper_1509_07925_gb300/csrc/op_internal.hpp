@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -13,7 +14,24 @@ struct mbf_factors_s {
   mbf::FactorSet fs;
 };
 
+namespace mbf {
+// Scratch of one apply in flight: the SIMT kernel's coefficient vectors, grid-barrier
+// word and dependency counters, the status word its waits report to, and the tensor
+// path's vectors, counters and tree-ordered input panel (allocated on first tensor
+// use).  An operator owns one; the server owns one per (slot, operator), so that
+// batches of one operator can run at the same time.
+struct Workspace {
+  float2* bufs = nullptr;          // one coefficient vector per stage, 4 RHS wide
+  unsigned* barrier = nullptr;     // barrier word, then (256 bytes on) the dependency counters
+  int* status = nullptr;
+  uint8_t* tc_bufs = nullptr;      // S_main + 1 vectors of c^L blocks x R8 x 64 entries (8 bytes each)
+  unsigned* tc_counters = nullptr;
+  float2* tc_gt = nullptr;         // input panel in Omega-tree order [n_w][64]
+};
+}  // namespace mbf
+
 struct mbf_op_s {
+  uint64_t serial = 0;              // unique per operator created in this process
   int device = 0;
   int d = 2, c = 4, L = 0, h = 0;
   int64_t n_out = 0, n_in = 0, n_w = 0;
@@ -25,9 +43,8 @@ struct mbf_op_s {
   mbf::Item* d_items = nullptr;
   int32_t *d_x_perm = nullptr, *d_x_off = nullptr, *d_w_perm = nullptr, *d_w_off = nullptr;
   int64_t leaf_pts_x = 0, leaf_pts_w = 0;   // points of the largest X / Omega leaf
-  float2* d_bufs = nullptr;         // one coefficient vector per stage, 4 RHS wide
-  unsigned* d_barrier = nullptr;    // barrier word, then (256 bytes on) the dependency counters
-  int* d_status = nullptr;
+  int32_t split_x = 0, split_w = 0;         // U^L-side leaf kernels: one CTA per leaf (ragged tree)
+  mbf::Workspace ws;                // the scratch of the operator's own applies
   int grid = 0, ns[5] = {0, 0, 0, 0, 0};
   size_t smem[5] = {0, 0, 0, 0, 0};
   // tensor-core path: arena of split-bf16 tiles of the main stages, its plan, and the
@@ -38,9 +55,6 @@ struct mbf_op_s {
   int64_t tc_bytes = 0;
   int tc_mt_max = 16, tc_kpad_max = 16, tc_nsa = 2, tc_nxb = 2, tc_nsets = 2;
   size_t tc_smem = 0;
-  uint8_t* d_tc_bufs = nullptr;       // S_main + 1 vectors of c^L blocks x R8 x 64 entries (8 bytes each)
-  unsigned* d_tc_counters = nullptr;
-  float2* d_tc_gt = nullptr;          // input panel in Omega-tree order [n_w][64]
   int32_t* d_w_inv = nullptr;         // natural Omega index -> tree position (-1: not in the tree)
   std::string tc_unavailable;         // why the tensor path cannot run for this operator ("" if it can)
   std::string simt_unavailable;       // why the FP32 SIMT path cannot (leaves beyond its limits; "" if it can)
@@ -71,6 +85,12 @@ struct mbf_op_s {
   // failure-detection test hook of the FP32 SIMT apply (mbf_op_debug_stall)
   int32_t dbg_stall_stage1 = 0;
   uint64_t dbg_wait_ns = 0;
+  // workspaces lent to concurrent batches (the server): the operator's own one first,
+  // then further ones, allocated on first need and kept until the operator is destroyed
+  std::mutex ws_mu;
+  bool ws_own_lent = false;
+  std::vector<mbf::Workspace*> ws_pool;
+  std::vector<bool> ws_pool_lent;
 };
 
 
@@ -79,11 +99,22 @@ void set_last_error(const std::string& m);
 // Internal entry points shared with the server and the tuner.  All throw mbf::Error.
 bool uses_tensor(const mbf_op_s* op, int64_t nrhs, int32_t precision, bool adj);
 void tc_prepare(mbf_op_s* op);
+// Allocate a workspace for `op` (its SIMT parts; ws_prepare_tc adds the tensor path's,
+// once) and free one.  Throw mbf::Error (MBF_ERR_OOM) on a failed allocation.
+void ws_init(const mbf_op_s* op, Workspace& w);
+void ws_prepare_tc(const mbf_op_s* op, Workspace& w);
+void ws_free(Workspace& w);
+// Borrow a workspace of `op` for one apply in flight (its own one if free, else one of its
+// pool, allocated if every one is lent; with the tensor path's parts when `tensor`), and
+// give it back.  Thread safe.
+Workspace* ws_acquire(mbf_op_s* op, bool tensor);
+void ws_release(mbf_op_s* op, Workspace* w);
 int64_t tc_vec_bytes(const mbf_op_s* op);
 // Apply on the device; grid > 0 caps the persistent kernels' CTA count (an SM share);
 // accumulate adds the result into out (which the caller initialised).
+// ws: the workspace to use (nullptr: the operator's own).
 void apply_dev(mbf_op_s* op, const void* in, void* out, int64_t nrhs, int32_t precision, cudaStream_t st,
-               bool adj, int grid, bool accumulate = false);
+               bool adj, int grid, bool accumulate = false, Workspace* ws = nullptr);
 // The error estimator of §3.3 (estimate.cpp); keeps the result in op->eps.
 double estimate_error(mbf_op_s* op, mbf_entry_fn fn, void* ctx, int32_t n_samples, uint64_t seed,
                       cudaStream_t st);

@@ -2,15 +2,21 @@
 // no counterpart).  A worker thread owns the CUDA work; mbf_submit / mbf_poll only
 // touch the queue under the server's mutex.
 //
-// Per batch: the oldest queued request whose operator is idle, plus the queued
-// requests on the same operator in FIFO order up to max_batch_rhs RHS.  One request
-// runs in place; several are gathered into a staging panel (device-to-device copies),
-// applied once, and scattered back.  With use_graphs the batch's copies and kernels
-// are captured into one CUDA graph; an executable graph is kept per batch shape
-// (operator, request RHS counts, SM share) and updated in place for new buffers.
+// Per batch (one slot = one stream): the oldest queued request and the queued requests
+// on its operator in FIFO order up to max_batch_rhs RHS form the batch's first group;
+// when more operators are queued than slots are free, the oldest requests on other
+// operators add further groups the same way, up to max_batch_ops operators.  A group of one request runs in place; several are gathered
+// into a staging panel (device-to-device copies), applied once, and scattered back.
+// Each group borrows a workspace of its operator for the batch (the operator's own one
+// when free, else one of its pool, allocated once and kept by the operator), so batches
+// of one operator in different slots run at the same time.  With use_graphs the whole batch --
+// every group's copies and kernels, in parallel branches -- is captured into one CUDA
+// graph and started by one graph launch; an executable graph is kept per batch shape
+// (operators, request RHS counts, SM shares) and updated in place for new buffers.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -42,12 +48,21 @@ struct Request {
   mbf_request_status_t st{};
 };
 
-struct Batch {
-  int slot = -1;
+// One operator's share of a batch.
+struct Group {
   mbf_op_s* op = nullptr;
   std::vector<mbf_ticket_t> ids;
+  std::vector<Request*> rq;
   int64_t rhs = 0;
-  void* stage = nullptr;   // [rhs][n_in] then [rhs][n_out]
+  void* stage = nullptr;       // [rhs][n_in] then [rhs][n_out]
+  mbf::Workspace* ws = nullptr;   // borrowed from the operator for the batch
+};
+
+constexpr int kMaxGroups = 8;   // operators per batch at most
+
+struct Batch {
+  int slot = -1;
+  std::vector<Group> groups;   // empty: the slot is free
   cudaEvent_t done = nullptr;
 };
 
@@ -69,10 +84,13 @@ struct mbf_server_s {
   mbf_ticket_t next_id = 1;
   int64_t reserved = 0;
   bool stop = false;
-  std::vector<cudaStream_t> streams;
-  std::vector<int*> status_host;   // pinned: copy of the operator's status word per slot
-  std::vector<Batch> slots;        // slot i busy iff slots[i].op != nullptr
-  std::set<mbf_op_s*> busy_ops;
+  std::vector<cudaStream_t> streams;                 // per slot
+  std::vector<std::vector<cudaStream_t>> aux;        // per slot: branch streams of a batch
+  std::vector<cudaEvent_t> fork_ev;                  // per slot
+  std::vector<std::vector<cudaEvent_t>> join_ev;     // per slot and branch
+  std::vector<int*> status_host;   // pinned: [slot][group] copies of the groups' status words
+  std::vector<Batch> slots;
+
   std::map<std::string, GraphEntry> graphs;
   uint64_t use_clock = 0;
   mbf_server_stats_t stats{};
@@ -84,29 +102,29 @@ struct mbf_server_s {
   }
   int inflight() const {
     int n = 0;
-    for (const auto& b : slots) n += b.op != nullptr;
+    for (const auto& b : slots) n += !b.groups.empty();
     return n;
   }
 
-  // Copies, apply and scatter of one batch on stream st (captured or not).
-  void enqueue_batch(const Batch& b, const std::vector<Request*>& rq, int grid, cudaStream_t st) {
-    mbf_op_s* op = b.op;
-    if (rq.size() == 1) {
-      mbf::apply_dev(op, rq[0]->g, rq[0]->u, rq[0]->nrhs, MBF_PREC_AUTO, st, false, grid);
+  // Copies and apply of one group on stream st (captured or not).
+  void enqueue_group(const Group& gr, int grid, cudaStream_t st) {
+    mbf_op_s* op = gr.op;
+    if (gr.rq.size() == 1) {
+      mbf::apply_dev(op, gr.rq[0]->g, gr.rq[0]->u, gr.rq[0]->nrhs, MBF_PREC_AUTO, st, false, grid, false, gr.ws);
       return;
     }
-    auto* in = static_cast<float2*>(b.stage);
-    float2* out = in + b.rhs * op->n_in;
+    auto* in = static_cast<float2*>(gr.stage);
+    float2* out = in + gr.rhs * op->n_in;
     int64_t r0 = 0;
-    for (Request* r : rq) {
+    for (Request* r : gr.rq) {
       cuda_ok(cudaMemcpyAsync(in + r0 * op->n_in, r->g, size_t(r->nrhs * op->n_in) * sizeof(float2),
                               cudaMemcpyDeviceToDevice, st),
               "gather copy");
       r0 += r->nrhs;
     }
-    mbf::apply_dev(op, in, out, b.rhs, MBF_PREC_AUTO, st, false, grid);
+    mbf::apply_dev(op, in, out, gr.rhs, MBF_PREC_AUTO, st, false, grid, false, gr.ws);
     r0 = 0;
-    for (Request* r : rq) {
+    for (Request* r : gr.rq) {
       cuda_ok(cudaMemcpyAsync(r->u, out + r0 * op->n_out, size_t(r->nrhs * op->n_out) * sizeof(float2),
                               cudaMemcpyDeviceToDevice, st),
               "scatter copy");
@@ -114,21 +132,40 @@ struct mbf_server_s {
     }
   }
 
+  // All groups of a batch: group 0 on the slot's stream, the others on branch streams
+  // forked from it and joined back into it.
+  void enqueue_batch(const Batch& b, int grid, cudaStream_t st) {
+    const size_t ng = b.groups.size();
+    const int gg = grid > 0 ? std::max(1, grid / int(ng)) : (ng > 1 ? std::max(1, sms / int(ng)) : 0);
+    if (ng > 1) cuda_ok(cudaEventRecord(fork_ev[size_t(b.slot)], st), "fork");
+    for (size_t k = 1; k < ng; ++k) {
+      cudaStream_t as = aux[size_t(b.slot)][k - 1];
+      cuda_ok(cudaStreamWaitEvent(as, fork_ev[size_t(b.slot)], 0), "fork wait");
+      enqueue_group(b.groups[k], gg, as);
+      cuda_ok(cudaEventRecord(join_ev[size_t(b.slot)][k - 1], as), "join");
+    }
+    enqueue_group(b.groups[0], gg, st);
+    for (size_t k = 1; k < ng; ++k) cuda_ok(cudaStreamWaitEvent(st, join_ev[size_t(b.slot)][k - 1], 0), "join wait");
+  }
+
   // Launch a batch on its slot (worker thread, lock not held).
-  void launch(Batch& b, const std::vector<Request*>& rq, int grid) {
+  void launch(Batch& b, int grid) {
     cudaStream_t st = streams[size_t(b.slot)];
-    mbf_op_s* op = b.op;
-    if (mbf::uses_tensor(op, b.rhs, MBF_PREC_AUTO, false)) mbf::tc_prepare(op);   // no allocation in capture
-    if (rq.size() > 1)
-      cuda_ok(cudaMallocAsync(&b.stage, size_t(b.rhs * (op->n_in + op->n_out)) * sizeof(float2), st),
-              "staging allocation");
+    std::string key = std::to_string(grid);
+    for (Group& gr : b.groups) {
+      // no allocation inside the capture: workspaces and staging first
+      gr.ws = mbf::ws_acquire(gr.op, mbf::uses_tensor(gr.op, gr.rhs, MBF_PREC_AUTO, false));
+      if (gr.rq.size() > 1)
+        cuda_ok(cudaMallocAsync(&gr.stage, size_t(gr.rhs * (gr.op->n_in + gr.op->n_out)) * sizeof(float2), st),
+                "staging allocation");
+      key += "|" + std::to_string(gr.op->serial);
+      for (Request* r : gr.rq) key += "/" + std::to_string(r->nrhs);
+    }
     if (opts.use_graphs) {
-      std::string key = std::to_string(reinterpret_cast<uintptr_t>(op)) + "/" + std::to_string(grid);
-      for (Request* r : rq) key += "/" + std::to_string(r->nrhs);
       cuda_ok(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
       cudaGraph_t graph = nullptr;
       try {
-        enqueue_batch(b, rq, grid, st);
+        enqueue_batch(b, grid, st);
       } catch (...) {
         cudaStreamEndCapture(st, &graph);
         if (graph) cudaGraphDestroy(graph);
@@ -167,13 +204,31 @@ struct mbf_server_s {
         graphs.erase(lru);
       }
     } else {
-      enqueue_batch(b, rq, grid, st);
+      enqueue_batch(b, grid, st);
     }
-    if (b.stage) cuda_ok(cudaFreeAsync(b.stage, st), "staging free");
-    b.stage = nullptr;
-    cuda_ok(cudaMemcpyAsync(status_host[size_t(b.slot)], op->d_status, sizeof(int), cudaMemcpyDeviceToHost, st),
-            "status copy");
+    for (size_t k = 0; k < b.groups.size(); ++k) {
+      Group& gr = b.groups[k];
+      if (gr.stage) cuda_ok(cudaFreeAsync(gr.stage, st), "staging free");
+      gr.stage = nullptr;
+      cuda_ok(cudaMemcpyAsync(status_host[size_t(b.slot)] + k, gr.ws->status, sizeof(int), cudaMemcpyDeviceToHost, st),
+              "status copy");
+    }
     cuda_ok(cudaEventRecord(b.done, st), "event record");
+  }
+
+  // Fail every request of group gr with err at time t (lock held).
+  void fail_group(Group& gr, int32_t err, double t) {
+    for (mbf_ticket_t id : gr.ids) {
+      auto it = reqs.find(id);
+      if (it == reqs.end()) continue;
+      Request& r = it->second;
+      r.st.state = MBF_REQ_ERROR;
+      r.st.error = err;
+      r.st.t_done = t;
+      reserved -= r.reserved;
+      r.reserved = 0;
+      ++stats.failed;
+    }
   }
 
   // Worker: retire finished batches, start new ones, sleep briefly while work is out.
@@ -185,80 +240,109 @@ struct mbf_server_s {
       // 1. completions
       for (size_t i = 0; i < slots.size(); ++i) {
         Batch& b = slots[i];
-        if (!b.op) continue;
+        if (b.groups.empty()) continue;
         const cudaError_t q = cudaEventQuery(b.done);
         if (q == cudaErrorNotReady) continue;
-        int dev_status = *status_host[i];
-        int32_t err = MBF_OK;
-        if (q != cudaSuccess) {
-          err = MBF_ERR_CUDA;
-          mbf::set_last_error(std::string("batch failed: ") + cudaGetErrorString(q));
-        } else if (dev_status != 0) {
-          err = MBF_ERR_TIMEOUT;
-          cudaMemsetAsync(b.op->d_status, 0, sizeof(int), streams[i]);
-          cudaStreamSynchronize(streams[i]);
-        }
         const double t = now();
-        for (mbf_ticket_t id : b.ids) {
-          auto it = reqs.find(id);
-          if (it == reqs.end()) continue;
-          Request& r = it->second;
-          r.st.state = err == MBF_OK ? MBF_REQ_DONE : MBF_REQ_ERROR;
-          r.st.error = err;
-          r.st.t_done = t;
-          reserved -= r.reserved;
-          r.reserved = 0;
-          if (err == MBF_OK) ++stats.completed;
-          else ++stats.failed;
+        for (size_t k = 0; k < b.groups.size(); ++k) {
+          Group& gr = b.groups[k];
+          int32_t err = MBF_OK;
+          if (q != cudaSuccess) {
+            err = MBF_ERR_CUDA;
+            mbf::set_last_error(std::string("batch failed: ") + cudaGetErrorString(q));
+          } else if (status_host[i][k] != 0) {
+            // a device wait of this group's apply gave up: its requests fail, its
+            // workspace's status word is cleared for the next batch
+            err = MBF_ERR_TIMEOUT;
+            cudaMemsetAsync(gr.ws->status, 0, sizeof(int), streams[i]);
+            cudaStreamSynchronize(streams[i]);
+            status_host[i][k] = 0;
+          }
+          if (err != MBF_OK) {
+            mbf::ws_release(gr.op, gr.ws);
+            fail_group(gr, err, t);
+            continue;
+          }
+          mbf::ws_release(gr.op, gr.ws);
+          for (mbf_ticket_t id : gr.ids) {
+            auto it = reqs.find(id);
+            if (it == reqs.end()) continue;
+            Request& r = it->second;
+            r.st.state = MBF_REQ_DONE;
+            r.st.error = MBF_OK;
+            r.st.t_done = t;
+            reserved -= r.reserved;
+            r.reserved = 0;
+            ++stats.completed;
+          }
         }
-        busy_ops.erase(b.op);
-        b.op = nullptr;
-        b.ids.clear();
+        b.groups.clear();
         progress = true;
       }
       // 2. dispatch
       for (size_t i = 0; i < slots.size(); ++i) {
-        if (slots[i].op) continue;
-        auto qi = queue.begin();
-        while (qi != queue.end() && busy_ops.count(reqs[*qi].op)) ++qi;
-        if (qi == queue.end()) break;
-        mbf_op_s* op = reqs[*qi].op;
+        if (!slots[i].groups.empty() || queue.empty()) continue;
         Batch& b = slots[i];
         b.slot = int(i);
-        b.op = op;
-        b.rhs = 0;
-        std::vector<Request*> rq;
-        for (auto it = qi; it != queue.end();) {
-          Request& r = reqs[*it];
-          if (r.op == op && (rq.empty() || b.rhs + r.nrhs <= opts.max_batch_rhs)) {
-            b.ids.push_back(*it);
-            rq.push_back(&r);
-            b.rhs += r.nrhs;
-            it = queue.erase(it);
-          } else {
-            ++it;
+        // operators per batch: one while the free slots can take every queued operator
+        // on its own (each then gets a whole SM share), else the queued operators are
+        // spread over the free slots, up to max_batch_ops per batch
+        int free_slots = 0;
+        for (const auto& x : slots) free_slots += x.groups.empty();
+        std::set<mbf_op_s*> qops;
+        for (mbf_ticket_t id : queue) qops.insert(reqs[id].op);
+        const int want = (int(qops.size()) + free_slots - 1) / std::max(1, free_slots);
+        const int max_ops = std::min({kMaxGroups, std::max(1, opts.max_batch_ops), std::max(1, want)});
+        int64_t nreq = 0, nrhs_all = 0;
+        while (int(b.groups.size()) < max_ops) {
+          // the oldest queued request on an operator not yet in the batch opens a group
+          // (a batch holds one group per operator: they share the slot's workspace for
+          // it); that operator's queued requests join it
+          auto qo = queue.begin();
+          while (qo != queue.end() && std::any_of(b.groups.begin(), b.groups.end(),
+                                                  [&](const Group& x) { return x.op == reqs[*qo].op; }))
+            ++qo;
+          if (qo == queue.end()) break;
+          Group gr;
+          gr.op = reqs[*qo].op;
+          for (auto it = qo; it != queue.end();) {
+            Request& r = reqs[*it];
+            if (r.op == gr.op && (gr.rq.empty() || gr.rhs + r.nrhs <= opts.max_batch_rhs)) {
+              gr.ids.push_back(*it);
+              gr.rq.push_back(&r);
+              gr.rhs += r.nrhs;
+              it = queue.erase(it);
+            } else {
+              ++it;
+            }
           }
+          nreq += int64_t(gr.rq.size());
+          nrhs_all += gr.rhs;
+          b.groups.push_back(std::move(gr));
         }
-        busy_ops.insert(op);
         const double t = now();
-        for (Request* r : rq) {
-          r->st.state = MBF_REQ_RUNNING;
-          r->st.t_start = t;
-          r->st.batch_requests = int32_t(rq.size());
-          r->st.batch_rhs = int32_t(b.rhs);
-        }
+        for (Group& gr : b.groups)
+          for (Request* r : gr.rq) {
+            r->st.state = MBF_REQ_RUNNING;
+            r->st.t_start = t;
+            r->st.batch_requests = int32_t(nreq);
+            r->st.batch_rhs = int32_t(nrhs_all);
+          }
         ++stats.batches;
-        if (rq.size() > 1) stats.coalesced_requests += int64_t(rq.size());
-        stats.max_batch_requests = std::max(stats.max_batch_requests, int32_t(rq.size()));
+        if (nreq > 1) stats.coalesced_requests += nreq;
+        if (b.groups.size() > 1) ++stats.mixed_batches;
+        stats.max_batch_requests = std::max(stats.max_batch_requests, int32_t(nreq));
+        stats.max_batch_ops = std::max(stats.max_batch_ops, int32_t(b.groups.size()));
         stats.max_concurrent_batches = std::max(stats.max_concurrent_batches, int32_t(inflight()));
         // SM share: the whole GPU when this batch runs alone, 1 / max_inflight otherwise
+        // (split among the batch's groups)
         const bool shared = inflight() > 1 || !queue.empty();
         const int grid = shared ? std::max(1, sms / opts.max_inflight) : 0;
         lk.unlock();
         int32_t err = MBF_OK;
         std::string msg;
         try {
-          launch(b, rq, grid);
+          launch(b, grid);
         } catch (const Error& e) {
           err = e.code;
           msg = e.what();
@@ -272,21 +356,15 @@ struct mbf_server_s {
         if (err != MBF_OK) {
           // nothing (more) runs for this batch: fail its requests now
           cudaStreamSynchronize(streams[i]);
+          for (auto& as : aux[i]) cudaStreamSynchronize(as);
           cudaGetLastError();
           mbf::set_last_error(msg);
           const double t2 = now();
-          for (mbf_ticket_t id : b.ids) {
-            Request& r = reqs[id];
-            r.st.state = MBF_REQ_ERROR;
-            r.st.error = err;
-            r.st.t_done = t2;
-            reserved -= r.reserved;
-            r.reserved = 0;
-            ++stats.failed;
+          for (Group& gr : b.groups) {
+            if (gr.ws) mbf::ws_release(gr.op, gr.ws);
+            fail_group(gr, err, t2);
           }
-          busy_ops.erase(op);
-          b.op = nullptr;
-          b.ids.clear();
+          b.groups.clear();
         }
         progress = true;
       }
@@ -339,6 +417,11 @@ void server_free(mbf_server_s* s) {
     if (b.done) cudaEventDestroy(b.done);
   for (int* p : s->status_host) cudaFreeHost(p);
   for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
+  for (auto& v : s->aux)
+    for (cudaStream_t st : v) cudaStreamDestroy(st);
+  for (cudaEvent_t e : s->fork_ev) cudaEventDestroy(e);
+  for (auto& v : s->join_ev)
+    for (cudaEvent_t e : v) cudaEventDestroy(e);
   delete s;
 }
 
@@ -357,19 +440,34 @@ mbf_status mbf_server_create(const mbf_server_opts_t* opts, mbf_server_t* out) {
       if (s->opts.max_inflight > 16) fail(MBF_ERR_INVALID, "max_inflight > 16");
       if (s->opts.max_batch_rhs <= 0) s->opts.max_batch_rhs = 64;
       if (s->opts.max_queue <= 0) s->opts.max_queue = 4096;
+      if (s->opts.max_batch_ops <= 0) s->opts.max_batch_ops = 4;
+      if (s->opts.max_batch_ops > kMaxGroups) fail(MBF_ERR_INVALID, "max_batch_ops > 8");
       cuda_ok(cudaGetDevice(&s->device), "cudaGetDevice");
       cuda_ok(cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device), "attr");
       s->t0 = std::chrono::steady_clock::now();
       s->slots.resize(size_t(s->opts.max_inflight));
+      s->aux.resize(size_t(s->opts.max_inflight));
+      s->join_ev.resize(size_t(s->opts.max_inflight));
       for (int i = 0; i < s->opts.max_inflight; ++i) {
         cudaStream_t st = nullptr;
         cuda_ok(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "stream");
         s->streams.push_back(st);
         int* p = nullptr;
-        cuda_ok(cudaMallocHost(&p, sizeof(int)), "pinned status");
-        *p = 0;
+        cuda_ok(cudaMallocHost(&p, sizeof(int) * kMaxGroups), "pinned status");
+        for (int k = 0; k < kMaxGroups; ++k) p[k] = 0;
         s->status_host.push_back(p);
         cuda_ok(cudaEventCreateWithFlags(&s->slots[size_t(i)].done, cudaEventDisableTiming), "event");
+        cudaEvent_t fe = nullptr;
+        cuda_ok(cudaEventCreateWithFlags(&fe, cudaEventDisableTiming), "event");
+        s->fork_ev.push_back(fe);
+        for (int k = 1; k < s->opts.max_batch_ops; ++k) {
+          cudaStream_t as = nullptr;
+          cuda_ok(cudaStreamCreateWithFlags(&as, cudaStreamNonBlocking), "stream");
+          s->aux[size_t(i)].push_back(as);
+          cudaEvent_t je = nullptr;
+          cuda_ok(cudaEventCreateWithFlags(&je, cudaEventDisableTiming), "event");
+          s->join_ev[size_t(i)].push_back(je);
+        }
       }
       s->worker = std::thread([s] { s->run(); });
     } catch (...) {

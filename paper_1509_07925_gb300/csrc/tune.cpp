@@ -79,7 +79,7 @@ extern "C" mbf_status mbf_op_tune(mbf_op_t op, void* stream, mbf_tune_result_t* 
       double best = 1e30;
       int best_nsa = keep_nsa;
       size_t best_smem = keep_smem;
-      for (int nsa = 2; nsa <= 8 && out->n_slots < 8; ++nsa) {
+      for (int nsa = 2; nsa <= 16 && out->n_slots < 8; nsa += 2) {
         const size_t sm = mbf::tc_smem_bytes(nsa, op->tc_nxb, op->tc_nsets, op->tc_mt_max, op->tc_kpad_max);
         if (sm > size_t(optin)) break;
         op->tc_nsa = nsa;
@@ -116,9 +116,9 @@ extern "C" mbf_status mbf_op_tune(mbf_op_t op, void* stream, mbf_tune_result_t* 
     }
     cuda_ok(cudaStreamSynchronize(st), "sync");
     int dev_status = 0;
-    cuda_ok(cudaMemcpy(&dev_status, op->d_status, sizeof(int), cudaMemcpyDeviceToHost), "status");
+    cuda_ok(cudaMemcpy(&dev_status, op->ws.status, sizeof(int), cudaMemcpyDeviceToHost), "status");
     if (dev_status != 0) {
-      cudaMemset(op->d_status, 0, sizeof(int));
+      cudaMemset(op->ws.status, 0, sizeof(int));
       fail(MBF_ERR_TIMEOUT, "a device wait gave up while tuning");
     }
     mbf::set_last_error("");

@@ -205,3 +205,16 @@ def test_bf_error_against_table_2():
     rate_floor = floor[14] / floor[22]
     rate_paper = paper[14] / paper[22]
     assert 1 / 1.5 < rate_floor / rate_paper < 1.5, (rate_floor, rate_paper)
+
+
+@pytest.mark.parametrize("case", [("dft", 16, 2, 4, 8, "none"), ("fio_iso", 32, 2, 4, 12, "polar"),
+                                  ("dft", 8, 3, 2, 16, "none"), ("fio_iso", 64, 2, 6, 6, "polar")])
+def test_block_apply_equals_sparse_apply(case):
+    """The level-by-level apply on the padded arrays (`BlockBF`) and the product of the
+    explicitly assembled sparse factors (`SparseBF`, pinned by the dense-product and
+    exactness tests above) give the same K_f g: two independent readings of eq. (gbf)."""
+    _, _, fs = _make(*case)
+    g = complex_normal(fs.n_in, 3, seed=12)
+    a = B.BlockBF(fs).apply(g)
+    b = B.SparseBF(fs).apply(g)
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()

@@ -107,6 +107,70 @@ def test_mix_matches_oracle_and_alone(bd, ops):
     assert stats.graph_launches == stats.batches     # every batch was one graph launch
 
 
+def test_mixed_operators_in_one_graph_launch(bd, ops):
+    """Requests of several operators and RHS counts queued together go into one batch,
+    one CUDA graph launch with a parallel branch per operator; each result equals the
+    oracle and the same request applied alone.  A single slot is held by a blocker (an
+    operator whose apply is made to wait 300 ms for a producer it lacks, through the
+    failure-detection hook) while the mix is queued behind it."""
+    import time
+    fs0, _ = oracle_case(*OPS[2])
+    blocker = bd.Operator(import_factors(bd, fs0))
+    blocker.debug_stall(1, 300_000_000)
+    srv = bd.Server(max_inflight=1, max_batch_rhs=64, max_batch_ops=4)
+    reqs = [(k, complex_normal(ops[k][1].n_in, nrhs, seed=70 + 4 * k + nrhs))
+            for k in range(len(ops)) for nrhs in (3, 9)]
+    # every buffer exists before the blocker runs (a device synchronize would wait for it)
+    bufs = []
+    for k, g in reqs:
+        gt = torch.from_numpy(g.astype(np.complex64)).cuda()
+        ut = torch.full((g.shape[0], ops[k][1].n_out), float("nan"), dtype=torch.complex64, device="cuda")
+        bufs.append((gt, ut))
+    gb = torch.zeros((1, fs0.n_in), dtype=torch.complex64, device="cuda")
+    ub = torch.empty((1, fs0.n_out), dtype=torch.complex64, device="cuda")
+    torch.cuda.synchronize()
+    tb = srv.submit(blocker, gb.data_ptr(), ub.data_ptr(), 1)
+    t0 = time.time()
+    while srv.poll(tb).state != bd.MBF_REQ_RUNNING:     # the blocker holds the only slot
+        assert time.time() - t0 < 10.0
+    tickets = [srv.submit(ops[k][0], gt.data_ptr(), ut.data_ptr(), g.shape[0])
+               for (k, g), (gt, ut) in zip(reqs, bufs)]
+    sts = _wait(bd, srv, tickets)
+    sts = [sts[t] for t in tickets]
+    stb = _wait(bd, srv, [tb])[tb]
+    stats = srv.stats()
+    srv.close()
+    blocker.close()
+    mix = [ut.cpu().numpy().astype(np.complex128) for _, ut in bufs]
+    assert stb.state == bd.MBF_REQ_ERROR and stb.error == bd.MBF_ERR_TIMEOUT
+    assert stats.mixed_batches >= 1 and stats.max_batch_ops == 4
+    assert stats.graph_launches == stats.batches
+    assert all(st.batch_requests == len(reqs) for st in sts)   # all of them in one batch
+    alone_srv = bd.Server(max_inflight=1)
+    for (k, g), m, st in zip(reqs, mix, sts):
+        assert st.state == bd.MBF_REQ_DONE, st.error
+        ref = ops[k][2].apply(g)
+        assert rel(m, ref) <= TOL, (k, g.shape, rel(m, ref))
+        a, sa = _run(bd, alone_srv, ops, [(k, g)])
+        assert sa[0].batch_requests == 1 and rel(m, a[0]) <= 2 * TOL
+    alone_srv.close()
+
+
+def test_batches_of_one_operator_overlap(bd, ops):
+    """With a workspace per slot and operator, batches of the same operator run at the
+    same time on different slots; every result still equals the oracle."""
+    op, fs, sb = ops[3]
+    srv = bd.Server(max_inflight=4, max_batch_rhs=8)
+    reqs = [(3, complex_normal(fs.n_in, 8, seed=90 + i)) for i in range(16)]
+    res, sts = _run(bd, srv, ops, reqs)
+    stats = srv.stats()
+    srv.close()
+    assert stats.max_concurrent_batches >= 2 and stats.mixed_batches == 0
+    for (k, g), m, st in zip(reqs, res, sts):
+        assert st.state == bd.MBF_REQ_DONE and st.batch_rhs == 8
+        assert rel(m, sb.apply(g)) <= TOL
+
+
 def test_graphs_off_gives_the_same_results(bd, ops):
     reqs = _requests(ops, 16, seed=9)
     a_srv = bd.Server(max_inflight=2, use_graphs=True)
