@@ -161,6 +161,23 @@ typedef struct mbf_op_s* mbf_op_t;            /* device-resident packed operator
 typedef struct mbf_server_s* mbf_server_t;    /* serving loop                           */
 typedef struct mbf_msbf_s* mbf_msbf_t;        /* multiscale factorization (§4)          */
 
+/* Products with the operator, Case (i) of §1.1: out = K in (adjoint = 0) or out = K^* in
+ * (adjoint = 1) for nrhs vectors; host, complex FP64 interleaved, laid out [nrhs][len]
+ * in natural order (in: n_in, out: n_out for K; the reverse for K^*).  Called from one
+ * host thread at a time. */
+typedef void (*mbf_apply_fn)(const double* in, double* out, int64_t nrhs, int32_t adjoint, void* ctx);
+
+/* Build the FP64 factors of an operator known only through products with K and K^*
+ * (Case (i) of §1.1; PBF-m / MBF-m of §3.3, §4.3): the middle level by the SVD via
+ * random matrix-vector multiplication (§2.1) of every block K^h_{i,j}, from K applied
+ * to the zero-padded Gaussian matrices C^P_j (r + 8 columns per Omega node j) and K^*
+ * to R^P_i (§2.3); the recursion as for mbf_build_factors.  prob as for
+ * mbf_build_factors (uniform or polar Omega tree, or explicit point sets); opts.seed
+ * seeds the Gaussian matrices; the factor_file option is not used.  2 c^h (r + 8)
+ * products in all, in calls of at most 256 vectors. */
+mbf_status mbf_build_from_applies(const mbf_problem_t* prob, mbf_apply_fn fn, void* ctx,
+                                  const mbf_build_opts_t* opts, mbf_factors_h* out);
+
 /* Build the FP64 factors on the host (§2.3-2.4, Case (ii)); threads per opts.
  * The builder keeps O(N log N) memory by recomputing each middle-level block for the
  * V side instead of storing U^h, V^h (§2.5, interleaved construction). */

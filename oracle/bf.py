@@ -24,7 +24,7 @@ from dataclasses import dataclass, field
 import numpy as np
 import scipy.sparse as sp
 
-from .lowrank import TOL, forms, svd_sampling, truncated_svd
+from .lowrank import TOL, _orth, forms, svd_sampling, truncated_svd
 
 
 @dataclass
@@ -114,7 +114,62 @@ def build(kernel, X: np.ndarray, W: np.ndarray, xtree, wtree, r: int, seed: int 
                                      factor=factor, tol=tol)
             U, Sd, V = forms(U0, s, V0, 1)
             Ucur[i, j], S[i, j], Vcur[j, i] = U, Sd, V
+    return _recursive(X.shape[0], W.shape[0], xtree, wtree, r, tol, Ucur, Vcur, S)
 
+
+def build_from_applies(apply_K, apply_Kh, n_out: int, n_in: int, xtree, wtree, r: int,
+                       seed: int = 7, k: int = 8, tol: float = TOL) -> FactorSet:
+    """Construct the BF of an operator known only through products with K and K^*
+    (Case (i) of §2.3).  apply_K(V) = K V for V of shape [n_in, m], apply_Kh(V) = K^* V.
+
+    For each Omega node j a Gaussian C_j (|B_j| x (r + k)) is zero-padded to C^P_j and
+    K C^P_j gives K^h_{i,j} C_j for every i; for each X node i, R_i padded to R^P_i gives
+    (K^h_{i,j})^* R_i for every j.  Each block is then factored by the SVD via random
+    matrix-vector multiplication (§2.1): Q_col, Q_row from pivoted QRs of the two products
+    (first r columns), M = (R_i^* Q_col)^+ (R_i^* K^h_{i,j} C_j) (Q_row^* C_j)^+, and the SVD
+    of M; R_i^* K^h_{i,j} C_j is read off as ((K^h_{i,j})^* R_i)^* C_j."""
+    d, L = xtree.d, xtree.L
+    assert wtree.L == L and wtree.d == d and L % 2 == 0 and L >= 2
+    c, h = 2 ** d, L // 2
+    p = r + k
+    rng = np.random.default_rng([seed, 1])
+    C, KC = {}, {}
+    for j in range(c ** h):
+        cols = wtree.node_points(L - h, j)
+        C[j] = (rng.standard_normal((cols.size, p)) + 1j * rng.standard_normal((cols.size, p))) / np.sqrt(2)
+        CP = np.zeros((n_in, p), dtype=np.complex128)
+        CP[cols] = C[j]
+        KC[j] = apply_K(CP)
+    R, KhR = {}, {}
+    for i in range(c ** h):
+        rows = xtree.node_points(h, i)
+        R[i] = (rng.standard_normal((rows.size, p)) + 1j * rng.standard_normal((rows.size, p))) / np.sqrt(2)
+        RP = np.zeros((n_out, p), dtype=np.complex128)
+        RP[rows] = R[i]
+        KhR[i] = apply_Kh(RP)
+    Ucur, Vcur, S = {}, {}, {}
+    for i in range(c ** h):
+        rows = xtree.node_points(h, i)
+        for j in range(c ** h):
+            cols = wtree.node_points(L - h, j)
+            Y, Wm = KC[j][rows], KhR[i][cols]
+            if rows.size == 0 or cols.size == 0:
+                U0, s, V0 = truncated_svd(np.zeros((rows.size, cols.size), complex), r, tol)
+            else:
+                Qc, Qr = _orth(Y)[:, :r], _orth(Wm)[:, :r]
+                M = np.linalg.pinv(R[i].conj().T @ Qc) @ (Wm.conj().T @ C[j]) @ np.linalg.pinv(Qr.conj().T @ C[j])
+                Um, s, Vm = truncated_svd(M, r, tol)
+                U0, V0 = Qc @ Um, Qr @ Vm
+            U, Sd, V = forms(U0, s, V0, 1)
+            Ucur[i, j], S[i, j], Vcur[j, i] = U, Sd, V
+    return _recursive(n_out, n_in, xtree, wtree, r, tol, Ucur, Vcur, S)
+
+
+def _recursive(n_out, n_in, xtree, wtree, r, tol, Ucur, Vcur, S) -> FactorSet:
+    """§2.4: the recursive factorization of the middle-level factors and the assembly of
+    the padded factor set."""
+    d, L = xtree.d, xtree.L
+    c, h = 2 ** d, L // 2
     kU = {h: np.array([[Ucur[i, j].shape[1] for j in range(c ** h)] for i in range(c ** h)])}
     kV = {h: np.array([[Vcur[j, i].shape[1] for i in range(c ** h)] for j in range(c ** h)])}
 
@@ -180,7 +235,7 @@ def build(kernel, X: np.ndarray, W: np.ndarray, xtree, wtree, r: int, seed: int 
     for (i, j), Sd in S.items():
         Sarr[i, j, :Sd.shape[0]] = Sd
 
-    return FactorSet(d=d, L=L, n_out=X.shape[0], n_in=W.shape[0],
+    return FactorSet(d=d, L=L, n_out=n_out, n_in=n_in,
                      x_perm=xtree.perm, x_off=xtree.off, w_perm=wtree.perm, w_off=wtree.off,
                      RU=RU, RV=RV, UL=leaf_array(Ucur, xtree, RU[L]),
                      VL=leaf_array(Vcur, wtree, RV[L]),

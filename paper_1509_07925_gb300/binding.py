@@ -114,11 +114,14 @@ class Profile(C.Structure):
 
 ENTRY_FN = C.CFUNCTYPE(None, C.POINTER(C.c_double), C.c_int64, C.POINTER(C.c_double), C.c_int64,
                        C.c_int32, C.POINTER(C.c_double), C.c_void_p)
+APPLY_FN = C.CFUNCTYPE(None, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int64, C.c_int32, C.c_void_p)
 
 # name -> (restype, argtypes); every entry point declared in include/mbf.h
 SIGNATURES = {
     "mbf_build_factors": (C.c_int, [C.POINTER(Problem), C.c_void_p, C.c_void_p, C.POINTER(BuildOpts),
                                     C.POINTER(C.c_void_p)]),
+    "mbf_build_from_applies": (C.c_int, [C.POINTER(Problem), C.c_void_p, C.c_void_p, C.POINTER(BuildOpts),
+                                         C.POINTER(C.c_void_p)]),
     "mbf_factors_view": (C.c_int, [C.c_void_p, C.POINTER(Factors)]),
     "mbf_factors_destroy": (C.c_int, [C.c_void_p]),
     "mbf_factors_save": (C.c_int, [C.POINTER(Factors), C.c_char_p]),
@@ -237,6 +240,41 @@ class HostFactors:
         fn = builtin_kernel(kernel) if isinstance(kernel, str) else kernel
         h = C.c_void_p()
         _check(lib().mbf_build_factors(C.byref(prob), fn, None, C.byref(opts), C.byref(h)))
+        self._handle = h
+        _check(lib().mbf_factors_view(h, C.byref(self.view)))
+        return self
+
+    @classmethod
+    def build_from_applies(cls, dim, n, L, r, apply, n_out, n_in, tree=MBF_TREE_UNIFORM, seed=7, threads=0,
+                           tol=1e-14, x_pts=None, w_pts=None, w_lo=0.0, w_side=0.0):
+        """Case (i) construction (mbf_build_from_applies): `apply(v, adjoint)` takes a complex
+        [nrhs, n_in] array (n_out for the adjoint) and returns K v (or K^* v), [nrhs, n_out]."""
+        self = cls()
+        prob = Problem(dim=dim, n=n, L=L, r=r, tree=tree)
+        if x_pts is not None:
+            xp = np.ascontiguousarray(x_pts, dtype=np.float64).reshape(-1, dim)
+            wp = np.ascontiguousarray(w_pts, dtype=np.float64).reshape(-1, dim)
+            self._keep.extend([xp, wp])
+            prob.n_x_pts, prob.x_pts = xp.shape[0], _ptr(xp, C.c_double)
+            prob.n_w_pts, prob.w_pts = wp.shape[0], _ptr(wp, C.c_double)
+            prob.w_lo, prob.w_side = w_lo, w_side
+        opts = BuildOpts(seed=seed, sample_factor=3, max_rounds=3, tol=tol, threads=threads, factor_file=None)
+        errors = []
+
+        def cb(pin, pout, nrhs, adjoint, _ctx):
+            try:
+                li, lo = (n_out, n_in) if adjoint else (n_in, n_out)
+                v = np.ctypeslib.as_array(pin, shape=(2 * nrhs * li,)).view(np.complex128).reshape(nrhs, li)
+                res = np.ascontiguousarray(apply(v.copy(), bool(adjoint)), dtype=np.complex128).reshape(nrhs, lo)
+                np.ctypeslib.as_array(pout, shape=(2 * nrhs * lo,))[:] = res.view(np.float64).ravel()
+            except Exception as e:   # no exception may cross the C ABI
+                errors.append(e)
+        fn = APPLY_FN(cb)
+        h = C.c_void_p()
+        code = lib().mbf_build_from_applies(C.byref(prob), C.cast(fn, C.c_void_p), None, C.byref(opts), C.byref(h))
+        if errors:
+            raise errors[0]
+        _check(code)
         self._handle = h
         _check(lib().mbf_factors_view(h, C.byref(self.view)))
         return self

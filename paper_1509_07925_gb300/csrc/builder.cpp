@@ -215,6 +215,53 @@ LowRank svd_sampling(const Entries& entries, int64_t m, int64_t n, int64_t r, st
   return out;
 }
 
+// SVD via random matrix-vector multiplication (§2.1, first procedure), from the products
+// Y = Z C (m x p) and W = Z^* R (n x p) with the Gaussian matrices C (n x p), R (m x p):
+// Q_col, Q_row from pivoted QRs of Y and W (first r columns), M = (R^* Q_col)^+ (W^* C)
+// (Q_row^* C)^+ (R^* Z C = W^* C), and the SVD of M, truncated at rank r and tol sigma_1.
+LowRank svd_matvec(const Mat& Y, const Mat& W, const Mat& C, const Mat& R, int64_t r, double tol) {
+  LowRank out;
+  const int64_t m = Y.m, n = W.m;
+  if (m == 0 || n == 0 || r == 0) {
+    out.U = Mat(m, 0);
+    out.V = Mat(n, 0);
+    return out;
+  }
+  Mat Qc, Qr;
+  pivoted_qr(Y, r, 1e-14, &Qc);
+  pivoted_qr(W, r, 1e-14, &Qr);
+  const Mat A1 = matmul_hn(R, Qc);     // R^* Q_col
+  const Mat A2 = matmul_hn(W, C);      // W^* C = R^* Z C
+  const Mat A3 = matmul_hn(Qr, C);     // Q_row^* C
+  const Mat M = matmul(matmul(pinv(A1, 1e-15 * double(A1.m)), A2), pinv(A3, 1e-15 * double(A3.n)));
+  Mat Um, Vm;
+  std::vector<double> sm;
+  svd_small(M, Um, sm, Vm);
+  int64_t k = 0;
+  while (k < int64_t(sm.size()) && k < r && sm[size_t(k)] > tol * sm[0]) ++k;
+  Mat Uk(Um.m, k), Vk(Vm.m, k);
+  for (int64_t q = 0; q < k; ++q) {
+    std::copy(Um.col(q), Um.col(q) + Um.m, Uk.col(q));
+    std::copy(Vm.col(q), Vm.col(q) + Vm.m, Vk.col(q));
+  }
+  out.U = matmul(Qc, Uk);
+  out.V = matmul(Qr, Vk);
+  out.s.assign(sm.begin(), sm.begin() + k);
+  return out;
+}
+
+// Complex Gaussian matrix (a + i b)/sqrt(2), m x p, from a seeded generator.
+Mat gaussian(int64_t m, int64_t p, uint64_t seed) {
+  std::mt19937_64 rng(seed);
+  std::normal_distribution<double> nd(0.0, 1.0);
+  Mat G(m, p);
+  for (int64_t q = 0; q < m * p; ++q) {
+    const double a = nd(rng), b = nd(rng);
+    G.a[size_t(q)] = cd(a, b) / std::sqrt(2.0);
+  }
+  return G;
+}
+
 template <class F>
 void parallel_for(int64_t count, int threads, F&& fn) {
   std::atomic<int64_t> next{0};
@@ -368,6 +415,11 @@ struct Builder {
   const mbf_problem_t& prob;
   mbf_entry_fn fn;
   void* ctx;
+  // Case (i) (§2.3): the operator is known only through products with K and K^*
+  mbf_apply_fn afn = nullptr;
+  int64_t p_over = 8;          // oversampling k of the random products
+  Mat KC;                      // [n_out][c^h p]: K C^P_j for every Omega node j (natural rows)
+  Mat KhR;                     // [n_in][c^h p]: K^* R^P_i for every X node i
   mbf_build_opts_t opts;
   int d, n, L, h, c;
   int64_t r;
@@ -398,9 +450,65 @@ struct Builder {
 
   // Middle-level block K^h_{i,j} (§2.3) by the SVD via random sampling; identical
   // for the U and the V pass because the generator depends on (seed, i, j) only.
+  // Case (i) random matrices: C_j (|B_j| x p) and R_i (|A_i| x p), seeded per node.
+  Mat case1_C(int64_t j) const {
+    return gaussian(wt.size(L - h, j), r + p_over, mix64(opts.seed ^ 0x4331000000000000ULL ^ uint64_t(j)));
+  }
+  Mat case1_R(int64_t i) const {
+    return gaussian(xt.size(h, i), r + p_over, mix64(opts.seed ^ 0x5231000000000000ULL ^ uint64_t(i)));
+  }
+
+  // Case (i): K C^P_j and K^* R^P_i for all nodes through the black box (§2.3), the
+  // zero-padded random matrices applied in chunks of at most 256 vectors.
+  void case1_products() {
+    const int64_t nh = ip(c, h), p = r + p_over;
+    const int64_t n_out = fs.n_out, n_in = fs.n_in;
+    KC = Mat(n_out, nh * p);
+    KhR = Mat(n_in, nh * p);
+    for (int side = 0; side < 2; ++side) {
+      const int64_t len_in = side == 0 ? n_in : n_out, len_out = side == 0 ? n_out : n_in;
+      Mat& dst = side == 0 ? KC : KhR;
+      const int64_t total = nh * p;
+      for (int64_t v0 = 0; v0 < total; v0 += 256) {
+        const int64_t nv = std::min<int64_t>(256, total - v0);
+        std::vector<double> in(size_t(2 * nv * len_in), 0.0), out(size_t(2 * nv * len_out), 0.0);
+        for (int64_t node = v0 / p; node <= (v0 + nv - 1) / p; ++node) {
+          const Mat G = side == 0 ? case1_C(node) : case1_R(node);
+          const Tree& T = side == 0 ? wt : xt;
+          const int lev = side == 0 ? L - h : h;
+          const int64_t b0 = T.begin(lev, node);
+          for (int64_t q = 0; q < p; ++q) {
+            const int64_t v = node * p + q - v0;
+            if (v < 0 || v >= nv) continue;
+            for (int64_t a = 0; a < G.m; ++a) {
+              const int64_t nat = T.perm[size_t(b0 + a)];
+              in[size_t(2 * (v * len_in + nat))] = G(a, q).real();
+              in[size_t(2 * (v * len_in + nat) + 1)] = G(a, q).imag();
+            }
+          }
+        }
+        afn(in.data(), out.data(), nv, side, ctx);
+        for (int64_t v = 0; v < nv; ++v)
+          for (int64_t row = 0; row < len_out; ++row)
+            dst(row, v0 + v) = cd(out[size_t(2 * (v * len_out + row))], out[size_t(2 * (v * len_out + row) + 1)]);
+      }
+    }
+  }
+
   LowRank middle(int64_t i, int64_t j) const {
     const int64_t xb = xt.begin(h, i), xe = xt.end(h, i);
     const int64_t wb = wt.begin(L - h, j), we = wt.end(L - h, j);
+    if (afn) {
+      // Case (i): Y = K^h_{i,j} C_j = rows A_i of K C^P_j; W = (K^h_{i,j})^* R_i = rows B_j of
+      // K^* R^P_i (§2.3); then the SVD via random matrix-vector multiplication (§2.1)
+      const int64_t p = r + p_over;
+      Mat Y(xe - xb, p), W(we - wb, p);
+      for (int64_t q = 0; q < p; ++q) {
+        for (int64_t a = 0; a < Y.m; ++a) Y(a, q) = KC(xt.perm[size_t(xb + a)], j * p + q);
+        for (int64_t b = 0; b < W.m; ++b) W(b, q) = KhR(wt.perm[size_t(wb + b)], i * p + q);
+      }
+      return svd_matvec(Y, W, case1_C(j), case1_R(i), r, opts.tol);
+    }
     std::mt19937_64 rng(mix64(opts.seed ^ mix64(uint64_t(i) * 0x10001ULL + uint64_t(j) + 1)));
     auto entries = [&](const std::vector<int64_t>& ri, const std::vector<int64_t>& ci) {
       std::vector<int64_t> xr(ri.size()), wc(ci.size());
@@ -505,7 +613,7 @@ struct Builder {
       fail(MBF_ERR_INVALID, "n must be a power of two");
     if (L < 2 || (L % 2) != 0) fail(MBF_ERR_INVALID, "L must be even and >= 2");
     if (r < 1) fail(MBF_ERR_INVALID, "r must be >= 1");
-    if (!fn) fail(MBF_ERR_INVALID, "entry function is NULL");
+    if (!fn && !afn) fail(MBF_ERR_INVALID, "entry function is NULL");
     if (opts.sample_factor <= 0) opts.sample_factor = 3;
     if (opts.max_rounds <= 0) opts.max_rounds = 3;
     if (!(opts.tol > 0)) opts.tol = 1e-14;
@@ -548,6 +656,7 @@ struct Builder {
       kV[size_t(l)].assign(size_t(nL), 0);
     }
 
+    if (afn) case1_products();
     const int64_t nh = ip(c, h);
     parallel_for(nh, opts.threads, [&](int64_t i) { side_pass(0, i); });
     parallel_for(nh, opts.threads, [&](int64_t j) { side_pass(1, j); });
@@ -562,6 +671,16 @@ struct Builder {
 FactorSet build_factors(const mbf_problem_t& prob, mbf_entry_fn fn, void* ctx,
                         const mbf_build_opts_t& opts) {
   Builder b(prob, fn, ctx, opts);
+  b.run();
+  return std::move(b.fs);
+}
+
+FactorSet build_factors_from_applies(const mbf_problem_t& prob, mbf_apply_fn afn, void* ctx,
+                                     const mbf_build_opts_t& opts) {
+  if (!afn) fail(MBF_ERR_INVALID, "apply function is NULL");
+  if (prob.tree == MBF_TREE_SQUARE) fail(MBF_ERR_INVALID, "construction from applies takes whole grids or point sets");
+  Builder b(prob, nullptr, ctx, opts);
+  b.afn = afn;
   b.run();
   return std::move(b.fs);
 }

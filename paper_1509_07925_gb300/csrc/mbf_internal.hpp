@@ -98,6 +98,9 @@ Mat pinv(const Mat& A, double rcond);
 // ---------------------------------------------------------------- builder
 FactorSet build_factors(const mbf_problem_t& prob, mbf_entry_fn fn, void* ctx,
                         const mbf_build_opts_t& opts);
+// Case (i) of §1.1 / §2.3: the middle level from products with K and K^* only.
+FactorSet build_factors_from_applies(const mbf_problem_t& prob, mbf_apply_fn afn, void* ctx,
+                                     const mbf_build_opts_t& opts);
 // Padded factor-set shapes (ranks capped per level, zero arrays) and the algorithmic
 // nonzeros from true ranks rank[level][node * c^(L - level) + other] (builder.cpp).
 void layout_factor_set(int d, int L, int64_t r, int64_t N_out, int64_t N_in, const Tree& xt, const Tree& wt,

@@ -1117,6 +1117,23 @@ mbf_status mbf_build_factors(const mbf_problem_t* prob, mbf_entry_fn fn, void* c
   });
 }
 
+mbf_status mbf_build_from_applies(const mbf_problem_t* prob, mbf_apply_fn fn, void* ctx,
+                                  const mbf_build_opts_t* opts, mbf_factors_h* out) {
+  return guard([&] {
+    if (!prob || !out) fail(MBF_ERR_INVALID, "NULL argument");
+    mbf_build_opts_t o{};
+    if (opts) o = *opts;
+    auto* h = new mbf_factors_s();
+    try {
+      h->fs = build_factors_from_applies(*prob, fn, ctx, o);
+    } catch (...) {
+      delete h;
+      throw;
+    }
+    *out = h;
+  });
+}
+
 mbf_status mbf_factors_view(mbf_factors_h f, mbf_factors_t* view) {
   return guard([&] {
     if (!f || !view) fail(MBF_ERR_INVALID, "NULL argument");
