@@ -395,17 +395,20 @@ mbf_status mbf_op_tune(mbf_op_t op, void* stream, mbf_tune_result_t* out);
  *   worker       continuous batching: whenever a slot is free it forms a batch: the
  *                oldest queued request with the queued requests on the same operator
  *                (FIFO, up to max_batch_rhs RHS, applied at once through a staging panel)
- *                is its first group; when more operators are queued than slots are
- *                free, the oldest requests on other operators add groups the same way,
- *                spreading the queued operators over the free slots, at most
- *                max_batch_ops per batch.  The batch is launched on
+ *                is its first group.  When requests back up (more queued than
+ *                max_inflight * max_batch_ops) and more operators are queued than slots
+ *                are free, the oldest requests on other operators add groups the same
+ *                way, spreading the queued operators over the free slots, at most
+ *                max_batch_ops per batch, each group's factor traffic at most
+ *                mix_work_pct percent of the first group's.  The batch is launched on
  *                the slot's stream, its groups in parallel branches -- as one captured
  *                CUDA graph (one graph launch for requests of several operators and RHS
  *                counts) when use_graphs is set.  A group borrows a workspace of its
  *                operator for the batch (the operator's own one when free, else one of a
  *                pool the operator keeps, allocated on first need), so batches overlap on
- *                the device, of one operator or of several; while others are running or waiting a batch's
- *                persistent kernels share 1 / max_inflight of the SMs among its groups.
+ *                the device, of one operator or of several.  While others are running or
+ *                waiting, a batch's persistent kernels share 1 / max_inflight of the SMs,
+ *                split among its groups in proportion to their factor traffic.
  *                The precision is MBF_PREC_AUTO for each group's RHS count.
  *   mbf_poll     state and timestamps of a ticket; a ticket is forgotten after the poll
  *                that reports DONE or ERROR (later polls: MBF_ERR_NOT_FOUND).
@@ -417,7 +420,9 @@ typedef struct mbf_server_opts {
   int32_t max_queue;            /* queued requests (0: 4096)                           */
   int32_t use_graphs;           /* 1: each batch is one CUDA graph launch              */
   int32_t max_batch_ops;        /* operators (groups) per batch (0: 4, <= 8)           */
-  int32_t reserved_opts;
+  int32_t mix_work_pct;         /* a further operator joins a batch only if its group's
+                                   factor traffic is <= this percent of the first
+                                   group's (0: 25)                                     */
 } mbf_server_opts_t;
 typedef int64_t mbf_ticket_t;
 enum { MBF_REQ_QUEUED = 0, MBF_REQ_RUNNING = 1, MBF_REQ_DONE = 2, MBF_REQ_ERROR = 3 };

@@ -80,7 +80,7 @@ class TuneResult(C.Structure):
 class ServerOpts(C.Structure):
     _fields_ = [("staging_budget_bytes", C.c_int64), ("max_inflight", C.c_int32),
                 ("max_batch_rhs", C.c_int32), ("max_queue", C.c_int32), ("use_graphs", C.c_int32),
-                ("max_batch_ops", C.c_int32), ("reserved_opts", C.c_int32)]
+                ("max_batch_ops", C.c_int32), ("mix_work_pct", C.c_int32)]
 
 
 class RequestStatus(C.Structure):
@@ -447,9 +447,9 @@ class Server:
     """Serving loop (mbf_server_t): continuous batching of applies on resident operators."""
 
     def __init__(self, staging_budget_bytes: int = 0, max_inflight: int = 0, max_batch_rhs: int = 0,
-                 max_queue: int = 0, use_graphs: bool = True, max_batch_ops: int = 0):
+                 max_queue: int = 0, use_graphs: bool = True, max_batch_ops: int = 0, mix_work_pct: int = 0):
         o = ServerOpts(staging_budget_bytes, max_inflight, max_batch_rhs, max_queue, 1 if use_graphs else 0,
-                       max_batch_ops)
+                       max_batch_ops, mix_work_pct)
         self._h = C.c_void_p()
         _check(lib().mbf_server_create(C.byref(o), C.byref(self._h)))
 

@@ -592,8 +592,8 @@ mbf_op_s* op_create(const mbf_factors_t& f) {
         auto smem = [&](int n) { return tc_smem_bytes(n, nxb, nsets, mt, kp); };
         if (smem(2) > size_t(optin)) nxb = 1;
         if (smem(2) > size_t(optin)) fail(MBF_ERR_INVALID, "tiles too large for the tensor path");
-        nsa = 2;
-        while (nsa < 16 && smem(nsa + 1) <= size_t(optin)) ++nsa;
+        nsa = 2;   // a multiple of the tile stream's producer lanes (2)
+        while (nsa + 2 <= 16 && smem(nsa + 2) <= size_t(optin)) nsa += 2;
         sm = std::max(smem(nsa), size_t(optin) / 2 + 1024);
       };
       config(op->tc_mt_max, op->tc_kpad_max, op->tc_nsets, op->tc_nxb, op->tc_nsa, op->tc_smem);
@@ -747,7 +747,6 @@ void apply_tc(mbf_op_s* op, Workspace& w, const float2* g, float2* u, int64_t nr
     la.c = op->c;
     la.R = op->RV[size_t(op->L)];
     la.R8 = tp.st[0].R8_in;
-    la.pts_cap = leaf_pts_cap(op->leaf_pts_w);
     e0 = prof_begin(op, st);
     cuda_check(launch_leaf(la, false, leaf_st.n_groups, st, tf32), "leaf (V^L)^* launch");
     prof_end(op, PK_LEAF_V, e0, st);
@@ -858,7 +857,6 @@ void apply_tc_adj(mbf_op_s* op, Workspace& w, const float2* u, float2* g, int64_
     la.c = op->c;
     la.R = op->RU[size_t(op->L)];
     la.R8 = ap.st[0].R8_in;
-    la.pts_cap = leaf_pts_cap(op->leaf_pts_x);
     e0 = prof_begin(op, st);
     cuda_check(launch_leaf(la, false, last_st.n_groups, st, false, true), "leaf (U^L)^* launch");
     prof_end(op, PK_LEAF_V, e0, st);

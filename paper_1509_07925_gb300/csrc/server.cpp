@@ -4,8 +4,10 @@
 //
 // Per batch (one slot = one stream): the oldest queued request and the queued requests
 // on its operator in FIFO order up to max_batch_rhs RHS form the batch's first group;
-// when more operators are queued than slots are free, the oldest requests on other
-// operators add further groups the same way, up to max_batch_ops operators.  A group of one request runs in place; several are gathered
+// when requests back up and more operators are queued than slots are free, the oldest
+// requests on other operators add further groups the same way, up to max_batch_ops
+// operators of at most mix_work_pct percent of the first group's factor traffic.  A
+// group of one request runs in place; several are gathered
 // into a staging panel (device-to-device copies), applied once, and scattered back.
 // Each group borrows a workspace of its operator for the batch (the operator's own one
 // when free, else one of its pool, allocated once and kept by the operator), so batches
@@ -132,19 +134,51 @@ struct mbf_server_s {
     }
   }
 
+  // Factor bytes a group streams: the operator's factors once per pass (a 64-RHS panel
+  // on the tensor cores, up to 4 RHS on the SIMT kernel).  The apply is bound by this
+  // traffic, so it sets the group's share of the batch's SMs.
+  static double group_work(const Group& gr) {
+    const mbf_op_s* op = gr.op;
+    if (mbf::uses_tensor(op, gr.rhs, MBF_PREC_AUTO, false))
+      return double(std::max<int64_t>(op->tc_bytes, 1)) * double((gr.rhs + 63) / 64);
+    return 8.0 * double(std::max<int64_t>(op->nnz, 1)) * double((gr.rhs + 3) / 4);
+  }
+
+  // SMs of each group: the batch's share (grid, or the whole GPU when 0) split in
+  // proportion to the groups' factor traffic, at least one each, so that the groups
+  // finish together instead of the largest one running on an even split.
+  std::vector<int> group_grids(const Batch& b, int grid) const {
+    const size_t ng = b.groups.size();
+    if (ng == 1) return {grid};
+    const int share = grid > 0 ? grid : sms;
+    std::vector<double> w(ng);
+    double sum = 0;
+    for (size_t k = 0; k < ng; ++k) sum += (w[k] = group_work(b.groups[k]));
+    std::vector<int> g(ng);
+    int used = 0;
+    size_t big = 0;
+    for (size_t k = 0; k < ng; ++k) {
+      g[k] = std::max(1, int(double(share) * w[k] / sum));
+      used += g[k];
+      if (w[k] > w[big]) big = k;
+    }
+    g[big] = std::max(1, g[big] + share - used);   // the remainder to the largest group
+    return g;
+  }
+
   // All groups of a batch: group 0 on the slot's stream, the others on branch streams
   // forked from it and joined back into it.
   void enqueue_batch(const Batch& b, int grid, cudaStream_t st) {
     const size_t ng = b.groups.size();
-    const int gg = grid > 0 ? std::max(1, grid / int(ng)) : (ng > 1 ? std::max(1, sms / int(ng)) : 0);
+    const std::vector<int> gg = group_grids(b, grid);
     if (ng > 1) cuda_ok(cudaEventRecord(fork_ev[size_t(b.slot)], st), "fork");
     for (size_t k = 1; k < ng; ++k) {
       cudaStream_t as = aux[size_t(b.slot)][k - 1];
       cuda_ok(cudaStreamWaitEvent(as, fork_ev[size_t(b.slot)], 0), "fork wait");
-      enqueue_group(b.groups[k], gg, as);
+      enqueue_group(b.groups[k], gg[k], as);
       cuda_ok(cudaEventRecord(join_ev[size_t(b.slot)][k - 1], as), "join");
     }
-    enqueue_group(b.groups[0], gg, st);
+    enqueue_group(b.groups[0], gg[0], st);
     for (size_t k = 1; k < ng; ++k) cuda_ok(cudaStreamWaitEvent(st, join_ev[size_t(b.slot)][k - 1], 0), "join wait");
   }
 
@@ -284,38 +318,53 @@ struct mbf_server_s {
         if (!slots[i].groups.empty() || queue.empty()) continue;
         Batch& b = slots[i];
         b.slot = int(i);
-        // operators per batch: one while the free slots can take every queued operator
-        // on its own (each then gets a whole SM share), else the queued operators are
-        // spread over the free slots, up to max_batch_ops per batch
+        // operators per batch: one unless requests back up (more queued than the slots
+        // take as batches of max_batch_ops requests each) and the free slots cannot take
+        // every queued operator on its own; then the queued operators are spread over the
+        // free slots, up to max_batch_ops per batch.  Below that backlog a request of a
+        // small operator is not held back by a larger operator's group.
         int free_slots = 0;
         for (const auto& x : slots) free_slots += x.groups.empty();
         std::set<mbf_op_s*> qops;
         for (mbf_ticket_t id : queue) qops.insert(reqs[id].op);
-        const int want = (int(qops.size()) + free_slots - 1) / std::max(1, free_slots);
+        const bool backlog = int64_t(queue.size()) > int64_t(opts.max_inflight) * opts.max_batch_ops;
+        const int want = backlog ? (int(qops.size()) + free_slots - 1) / std::max(1, free_slots) : 1;
         const int max_ops = std::min({kMaxGroups, std::max(1, opts.max_batch_ops), std::max(1, want)});
         int64_t nreq = 0, nrhs_all = 0;
+        std::set<mbf_op_s*> passed;   // operators left out of this batch by the work ratio
+        double work0 = 0;
         while (int(b.groups.size()) < max_ops) {
-          // the oldest queued request on an operator not yet in the batch opens a group
-          // (a batch holds one group per operator: they share the slot's workspace for
-          // it); that operator's queued requests join it
+          // the oldest queued request on an operator not yet in (or passed over for) the
+          // batch opens a group (a batch holds one group per operator: they share the
+          // slot's workspace for it); that operator's queued requests join it
           auto qo = queue.begin();
-          while (qo != queue.end() && std::any_of(b.groups.begin(), b.groups.end(),
-                                                  [&](const Group& x) { return x.op == reqs[*qo].op; }))
+          while (qo != queue.end() && (passed.count(reqs[*qo].op) ||
+                                       std::any_of(b.groups.begin(), b.groups.end(),
+                                                   [&](const Group& x) { return x.op == reqs[*qo].op; })))
             ++qo;
           if (qo == queue.end()) break;
           Group gr;
           gr.op = reqs[*qo].op;
-          for (auto it = qo; it != queue.end();) {
+          std::vector<size_t> take;   // queue positions of the group's requests
+          for (auto it = qo; it != queue.end(); ++it) {
             Request& r = reqs[*it];
             if (r.op == gr.op && (gr.rq.empty() || gr.rhs + r.nrhs <= opts.max_batch_rhs)) {
               gr.ids.push_back(*it);
               gr.rq.push_back(&r);
               gr.rhs += r.nrhs;
-              it = queue.erase(it);
-            } else {
-              ++it;
+              take.push_back(size_t(it - queue.begin()));
             }
           }
+          // a further operator joins only if its factor traffic is at most mix_work_pct
+          // percent of the first group's: the batch ends with its longest group
+          const double wk = group_work(gr);
+          if (b.groups.empty()) {
+            work0 = wk;
+          } else if (wk * 100.0 > double(opts.mix_work_pct) * work0) {
+            passed.insert(gr.op);
+            continue;
+          }
+          for (auto t = take.rbegin(); t != take.rend(); ++t) queue.erase(queue.begin() + std::ptrdiff_t(*t));
           nreq += int64_t(gr.rq.size());
           nrhs_all += gr.rhs;
           b.groups.push_back(std::move(gr));
@@ -335,7 +384,7 @@ struct mbf_server_s {
         stats.max_batch_ops = std::max(stats.max_batch_ops, int32_t(b.groups.size()));
         stats.max_concurrent_batches = std::max(stats.max_concurrent_batches, int32_t(inflight()));
         // SM share: the whole GPU when this batch runs alone, 1 / max_inflight otherwise
-        // (split among the batch's groups)
+        // (split among the batch's groups in proportion to their factor traffic)
         const bool shared = inflight() > 1 || !queue.empty();
         const int grid = shared ? std::max(1, sms / opts.max_inflight) : 0;
         lk.unlock();
@@ -442,6 +491,8 @@ mbf_status mbf_server_create(const mbf_server_opts_t* opts, mbf_server_t* out) {
       if (s->opts.max_queue <= 0) s->opts.max_queue = 4096;
       if (s->opts.max_batch_ops <= 0) s->opts.max_batch_ops = 4;
       if (s->opts.max_batch_ops > kMaxGroups) fail(MBF_ERR_INVALID, "max_batch_ops > 8");
+      if (s->opts.mix_work_pct < 0) fail(MBF_ERR_INVALID, "mix_work_pct < 0");
+      if (s->opts.mix_work_pct == 0) s->opts.mix_work_pct = 25;
       cuda_ok(cudaGetDevice(&s->device), "cudaGetDevice");
       cuda_ok(cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device), "attr");
       s->t0 = std::chrono::steady_clock::now();

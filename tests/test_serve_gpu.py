@@ -117,7 +117,7 @@ def test_mixed_operators_in_one_graph_launch(bd, ops):
     fs0, _ = oracle_case(*OPS[2])
     blocker = bd.Operator(import_factors(bd, fs0))
     blocker.debug_stall(1, 300_000_000)
-    srv = bd.Server(max_inflight=1, max_batch_rhs=64, max_batch_ops=4)
+    srv = bd.Server(max_inflight=1, max_batch_rhs=64, max_batch_ops=4, mix_work_pct=100000)
     reqs = [(k, complex_normal(ops[k][1].n_in, nrhs, seed=70 + 4 * k + nrhs))
             for k in range(len(ops)) for nrhs in (3, 9)]
     # every buffer exists before the blocker runs (a device synchronize would wait for it)
@@ -154,6 +154,61 @@ def test_mixed_operators_in_one_graph_launch(bd, ops):
         a, sa = _run(bd, alone_srv, ops, [(k, g)])
         assert sa[0].batch_requests == 1 and rel(m, a[0]) <= 2 * TOL
     alone_srv.close()
+
+
+def _queue_behind_blocker(bd, srv, ops, order, seed):
+    """Hold the server's only slot with a stalled blocker, queue requests on the
+    operators `order` (in that order, two RHS each) behind it, and wait for all."""
+    import time
+    fs0, _ = oracle_case(*OPS[2])
+    blocker = bd.Operator(import_factors(bd, fs0))
+    blocker.debug_stall(1, 200_000_000)
+    reqs = [(k, complex_normal(ops[k][1].n_in, 2, seed=seed + i)) for i, k in enumerate(order)]
+    bufs = []
+    for k, g in reqs:
+        bufs.append((torch.from_numpy(g.astype(np.complex64)).cuda(),
+                     torch.empty((2, ops[k][1].n_out), dtype=torch.complex64, device="cuda")))
+    gb = torch.zeros((1, fs0.n_in), dtype=torch.complex64, device="cuda")
+    ub = torch.empty((1, fs0.n_out), dtype=torch.complex64, device="cuda")
+    torch.cuda.synchronize()
+    tb = srv.submit(blocker, gb.data_ptr(), ub.data_ptr(), 1)
+    t0 = time.time()
+    while srv.poll(tb).state != bd.MBF_REQ_RUNNING:
+        assert time.time() - t0 < 10.0
+    tickets = [srv.submit(ops[k][0], gt.data_ptr(), ut.data_ptr(), 2) for (k, _), (gt, ut) in zip(reqs, bufs)]
+    sts = _wait(bd, srv, tickets)
+    _wait(bd, srv, [tb])
+    blocker.close()
+    for (k, g), (_, ut), t in zip(reqs, bufs, tickets):
+        assert sts[t].state == bd.MBF_REQ_DONE
+        assert rel(ut.cpu().numpy().astype(np.complex128), ops[k][2].apply(g)) <= TOL
+    return [sts[t] for t in tickets]
+
+
+def test_batch_policy_work_ratio_and_backlog(bd, ops):
+    """Default policy: under a backlog (6 queued > 1 slot x 4 operators per batch) a
+    further operator joins a batch only if its factor traffic is at most 25 % of the
+    first group's.  A small operator queued first keeps a larger one out of its batch;
+    a larger one queued first takes the small one along (one mixed batch).  Without a
+    backlog (3 queued) no batch is mixed."""
+    small, big = 0, 3          # 2-D DFT n = 16 (256 points), polar FIO n = 64 (4096 points)
+    srv = bd.Server(max_inflight=1, max_batch_rhs=64, max_batch_ops=4)
+    sts = _queue_behind_blocker(bd, srv, ops, [small] * 3 + [big] * 3, seed=300)
+    stats = srv.stats()
+    srv.close()
+    assert stats.mixed_batches == 0
+    assert all(st.batch_requests == 3 for st in sts)
+    srv = bd.Server(max_inflight=1, max_batch_rhs=64, max_batch_ops=4)
+    sts = _queue_behind_blocker(bd, srv, ops, [big] * 3 + [small] * 3, seed=310)
+    stats = srv.stats()
+    srv.close()
+    assert stats.mixed_batches == 1
+    assert all(st.batch_requests == 6 for st in sts)
+    srv = bd.Server(max_inflight=1, max_batch_rhs=64, max_batch_ops=4)
+    sts = _queue_behind_blocker(bd, srv, ops, [big, small, small], seed=320)
+    stats = srv.stats()
+    srv.close()
+    assert stats.mixed_batches == 0
 
 
 def test_batches_of_one_operator_overlap(bd, ops):
