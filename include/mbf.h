@@ -212,7 +212,9 @@ typedef struct mbf_op_info {
   int32_t dim, L, c, n_stages;
   int64_t n_out, n_in;
   int32_t RU[32], RV[32];
-  int64_t nnz_algorithmic;      /* nonzeros of the unpadded factors (the §2.5 apply cost) */
+  int64_t nnz_algorithmic;      /* nonzeros of the unpadded factors (the §2.5 apply cost):
+                                   mbf_factors_t.nnz, or when that is 0 the nonzero
+                                   entries the packer stored                             */
   int64_t bytes_algorithmic;    /* 8 * nnz_algorithmic (complex64)                        */
   int64_t bytes_packed;         /* device bytes of the packed tiles incl. padding         */
   int64_t bytes_stage[32];      /* packed bytes streamed by each forward stage            */

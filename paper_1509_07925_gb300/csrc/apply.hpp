@@ -87,6 +87,7 @@ struct LeafArgs {
   int32_t nrhs, rhs0, c, R;
   int32_t R8, item_stride;
   int32_t accumulate;       // U^L: 1 adds into u
+  int32_t pts_cap;          // (V^L)^*: points staged per round (leaf_pts_cap of the largest leaf)
   int32_t leaf_split;       // U^L side: 1 = one CTA per leaf (ragged trees), 0 = one per group
   int32_t gather;           // (V^L)^* side: 1 = vec is [nrhs][len_vec] in natural order, read through
                             // perm (tree position -> natural index); 0 = the tree-ordered panel
@@ -103,8 +104,11 @@ size_t counter_bytes(const Plan& plan);
 // tensor-core path (apply_tc.cu)
 size_t tc_smem_bytes(int nsa, int nxb, int nsets, int mt_max, int kpad_max);
 size_t tc_counter_bytes(const TCPlan& plan);
-// Dynamic shared memory of a leaf kernel.
-size_t leaf_smem_bytes(int R, int c, bool u_side);
+// Dynamic shared memory of a leaf kernel; the (V^L)^* side stages pts_cap points a round.
+size_t leaf_smem_bytes(int R, int c, bool u_side, int pts_cap = 64);
+// Points per round of the (V^L)^* leaf kernel for leaves of at most max_leaf_points
+// points: rounded up to 8, within [8, 64].
+int leaf_pts_cap(int64_t max_leaf_points);
 bool leaf_fits(int R8, int c);   // leaf kernels: R8 <= 64, c <= 8
 // tf32: TF32 tiles and vectors (kind::tf32 MMAs), else split-BF16x3.
 cudaError_t launch_apply_tc(const TCArgs& a, int grid, size_t smem, cudaStream_t stream, bool tf32);

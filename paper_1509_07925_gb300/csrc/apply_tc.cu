@@ -15,12 +15,13 @@
 // two contiguous runs per input block.
 //
 // Warp roles in a CTA (one per SM, persistent, cooperative):
-//   warp 0     one lane streams each group's tile, chunk by chunk (K = 16 columns,
+//   warp 0     two lanes stream each group's tile, chunk by chunk (K = 16 columns,
 //              4 planes), into a ring of shared-memory slots (full/empty mbarriers);
 //   warp 1     allocates TMEM; runs the MMA loop (warp-uniform operands), one elected
 //              lane issuing the MMAs into an accumulator set and the commits;
-//   warp 2     one lane waits for a group's inputs (dependency counters) and bulk-
-//              copies its c blocks into a panel buffer (complete_tx on its mbarrier);
+//   warp 2     lane 0 waits for a group's inputs (dependency counters), then one lane
+//              per block half bulk-copies the c blocks into a panel buffer
+//              (complete_tx on its mbarrier);
 //   warps 4-7, 8-11   epilogue sets, one per accumulator set: read the accumulators
 //              (tcgen05.ld, 32 columns of each half a round), pair the halves by warp
 //              shuffles, split and store the group's output blocks, and hand them to
@@ -141,12 +142,6 @@ __device__ __forceinline__ bool named_sync_or(int id, int n, bool v) {
   return r != 0;
 }
 
-// One lane of the (converged) warp: true in exactly one lane.
-__device__ __forceinline__ bool elect_one() {
-  uint32_t pred = 0;
-  asm volatile("{\n .reg .pred P;\n elect.sync _|P, 0xffffffff;\n selp.u32 %0, 1, 0, P;\n}\n" : "=r"(pred));
-  return pred != 0;
-}
 
 // 16 consecutive TMEM columns of this thread's lane (one row of the accumulator),
 // written straight into the 16 FP32 registers (b32 operands take any 32-bit register).
@@ -197,6 +192,13 @@ __device__ __forceinline__ void split8(const float* y, uint4& hi, uint4& lo) {
   }
   hi = make_uint4(h[0], h[1], h[2], h[3]);
   lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// One lane of the (converged) warp: true in exactly one lane.
+__device__ __forceinline__ bool elect_one() {
+  uint32_t pred = 0;
+  asm volatile("{\n .reg .pred P;\n elect.sync _|P, 0xffffffff;\n selp.u32 %0, 1, 0, P;\n}\n" : "=r"(pred));
+  return pred != 0;
 }
 
 // Block index (tree-node pair of the level) of segment t of group g under a pattern.
@@ -661,7 +663,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
 
 // ------------------------------------------------------------------ leaf kernels
 // U^L: one CTA per group (its c leaves), the group's points staged kLeafPts at a time;
-// (V^L)^*: one CTA per leaf, its points in rounds of 16 on warp-level MMAs.
+// (V^L)^*: one CTA per leaf, its points staged up to LeafArgs::pts_cap at a time.
 constexpr int kLeafThreads = 256;
 constexpr int kLeafPts = 64;        // points staged per round (= kTcNR)
 constexpr int kLeafMaxR8 = 64;      // largest leaf rank (rounded up to 8) of the tensor path
@@ -735,240 +737,148 @@ __global__ void __launch_bounds__(kLeafThreads) permute_in_kernel(const __grid_c
   }
 }
 
-// (V^L)^* for a panel of 64 RHS, one CTA of kLeafVThreads threads per leaf j (of group
+// Rows k0 .. k0 + 7 of column n of split block `leaf` from 8 accumulators: byte
+// (hl, k, ri, n) as in apply.hpp, so 8 consecutive k are one 16-byte run per plane.
+template <bool TF32>
+__device__ __forceinline__ void store_split8(uint8_t* outs, int64_t leaf, int R8, int n, int k0, float2 (&acc)[8]) {
+  float re[8], im[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    re[j] = acc[j].x;
+    im[j] = acc[j].y;
+    acc[j] = make_float2(0.f, 0.f);
+  }
+  // rows m = 2 n (real part) and 2 n + 1 (imaginary part) of the block: adjacent 16-byte
+  // rows of one core matrix
+  const int m = 2 * n;
+  if constexpr (TF32) {   // TF32 block: byte (k / 4) 2048 + (m / 8) 128 + (m % 8) 16 + (k % 4) 4
+    uint8_t* o = outs + leaf * split_block_bytes(R8) + (k0 >> 2) * 2048 + (m >> 3) * 128 + (m & 7) * 16;
+    *reinterpret_cast<uint4*>(o) = tc::tf32x4(re);
+    *reinterpret_cast<uint4*>(o + 2048) = tc::tf32x4(re + 4);
+    *reinterpret_cast<uint4*>(o + 16) = tc::tf32x4(im);
+    *reinterpret_cast<uint4*>(o + 2048 + 16) = tc::tf32x4(im + 4);
+  } else {
+    uint4 rh, rl, ih, il;
+    tc::split8(re, rh, rl);
+    tc::split8(im, ih, il);
+    uint8_t* o = outs + leaf * split_block_bytes(R8) + (k0 >> 3) * 2048 + (m >> 3) * 128 + (m & 7) * 16;
+    const int64_t half = int64_t(R8) * 256;
+    *reinterpret_cast<uint4*>(o) = rh;               // Re hi
+    *reinterpret_cast<uint4*>(o + 16) = ih;          // Im hi
+    *reinterpret_cast<uint4*>(o + half) = rl;        // Re lo
+    *reinterpret_cast<uint4*>(o + half + 16) = il;   // Im lo
+  }
+}
+
+// (V^L)^* for a panel of 64 RHS, one CTA of 64 R8 / 8 threads per leaf j (of group
 // g = j / c):
-//   y_j[k][n] = sum over the points b of leaf j of W[b][k] x[b][n],
-// W = conj(V^L_j) as the group's item stores it (line = point, tree order from the
-// group's first point; entry = k), x = the leaf's rows of g, stored as split block j
-// (rows k >= R are zero).  The leaf product is a small dense contraction, run on warp-
-// level BF16 MMAs (m16n8k16, FP32 accumulation) with split operands, hi*hi + hi*lo +
-// lo*hi as in the tensor kernel, in real form
-//   [Y_re; Y_im] = [[W_re^T, -W_im^T]; [W_im^T, W_re^T]] [X_re; X_im]
-// (M = 2 R8 rows, K = the real and imaginary parts of up to 16 points a round, N = 64).
-// A round: every thread gathers its rows of x and its entries of W (all loads in
-// flight at once), splits them into bf16 hi / lo and stores them as the MMA operands
-// (A: [m][k], B: [n][k], rows padded to 40 bf16 against ldmatrix bank conflicts); warp
-// w then runs the MMAs for RHS 16 w .. 16 w + 15.  After the last round the
-// accumulators go through shared memory to the split-block layout (16-byte runs of 8
-// consecutive k).  With `gather` the rows come straight from g in natural order through
-// the tree permutation (device buffers: no panel, no permute kernel); else from the
-// tree-ordered panel (page-locked host buffers), whose L2 lines are then dropped.
+//   y_j[k][n] = sum over the points b of leaf j of conj(V^L_j[b][k]) gt[b][n],
+// gt = the panel in tree order (permute_in_kernel), stored as split block j (rows k >= R
+// are zero).  The group's item holds conj(V) with line = point (tree order from the
+// group's first point), entry = k.  Up to a.pts_cap points at a time, the leaf's panel
+// rows (contiguous, 512 bytes each) are copied into shared memory by 16-byte cp.async
+// while its item entries are loaded, every load of the round in flight at once; then
+// thread (n, kg) accumulates rows 8 kg .. 8 kg + 7 of column n from shared memory only.
 // One CTA per leaf bounds a CTA's work by the largest leaf, not the largest group (a
-// ragged tree puts several times the mean number of points into some groups).  Empty
-// leaves give zero blocks.
+// ragged tree puts several times the mean number of points into some groups).  The
+// panel rows are read by this CTA alone and never again: their L2 lines are discarded
+// rather than written back.  With `gather` the rows come straight from g in natural
+// order through the tree permutation instead (no panel, no permute kernel): device
+// buffers take this route; page-locked host buffers keep the panel, read row by row.
+// Empty leaves give zero blocks.
+__device__ __forceinline__ void leaf_v_point(float2 (&acc)[8], const float2* vrow, float2 x) {
+  const float4* vp = reinterpret_cast<const float4*>(vrow);
+#pragma unroll
+  for (int j2 = 0; j2 < 4; ++j2) {
+    const float4 v = vp[j2];
+    acc[2 * j2].x = fmaf(v.x, x.x, fmaf(-v.y, x.y, acc[2 * j2].x));
+    acc[2 * j2].y = fmaf(v.x, x.y, fmaf(v.y, x.x, acc[2 * j2].y));
+    acc[2 * j2 + 1].x = fmaf(v.z, x.x, fmaf(-v.w, x.y, acc[2 * j2 + 1].x));
+    acc[2 * j2 + 1].y = fmaf(v.z, x.y, fmaf(v.w, x.x, acc[2 * j2 + 1].y));
+  }
+}
+
 // XPOSE (the adjoint's U^* leaf products): the group's item is a U^L item (line = k,
 // entry = point of the group, U itself), read transposed and conjugated.
-constexpr int kLeafVThreads = 128;
-constexpr int kLeafVPts = 16;                 // points a round (K = 32)
-constexpr int kLeafVStride = 40;              // bf16 per operand row in shared memory
-
-__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
-               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-               : "r"(addr));
-}
-__device__ __forceinline__ void mma_m16n8k16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-      "{%0, %1, %2, %3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-// bf16 hi / lo words of two floats (x0 in the low half)
-__device__ __forceinline__ void split2(float x0, float x1, uint32_t& hi, uint32_t& lo) {
-  hi = tc::pack_bf16x2(x0, x1);
-  lo = tc::pack_bf16x2(x0 - __uint_as_float(hi << 16), x1 - __uint_as_float(hi & 0xffff0000u));
-}
-
-size_t leaf_v_smem_bytes(int R8) {
-  const size_t ops = (size_t(2) * kTcNR + size_t(4) * R8) * kLeafVStride * 2;   // B hi, lo; A hi, lo
-  const size_t stage = size_t(kTcNR) * size_t(2 * R8 + 4) * sizeof(float);
-  return std::max(ops, stage);
-}
-
-template <int MTMAX, bool TF32, bool XPOSE>
-__global__ void __launch_bounds__(kLeafVThreads, MTMAX <= 4 ? 6 : 3) leaf_v_kernel(const __grid_constant__ LeafArgs a) {
-  constexpr int NR = kTcNR, ST = kLeafVStride, KP = kLeafVPts;
-  extern __shared__ __align__(16) uint8_t lvs[];
-  uint16_t* bh = reinterpret_cast<uint16_t*>(lvs);   // [64][ST]: B hi, k = point (re) | 16 + point (im)
-  uint16_t* bl = bh + NR * ST;                        // B lo
-  uint16_t* ah = bl + NR * ST;                        // [2 R8][ST]: A hi
-  const int R8 = a.R8, R = a.R, MT = R8 / 8;          // m16 tiles of the 2 R8 rows
-  uint16_t* al = ah + 2 * R8 * ST;                    // A lo
-  const int j = blockIdx.x, c = a.c, g = j / c;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+template <bool TF32, bool XPOSE>
+__global__ void __launch_bounds__(kTcNR * kLeafMaxR8 / 8) leaf_v_kernel(const __grid_constant__ LeafArgs a) {
+  using tc::sa;
+  using tc::cp_async16;
+  using tc::cp_async_wait_all;
+  using tc::l2_discard;
+  constexpr int NR = kTcNR;
+  extern __shared__ __align__(16) float2 lsm[];
+  __shared__ int nat[kLeafPts];            // gather: natural indices of the round's points
+  const int j = blockIdx.x, c = a.c, g = j / c, R = a.R, R8 = a.R8, cap = a.pts_cap;
+  const int tid = threadIdx.x, nth = int(blockDim.x), n = tid % NR, k0 = 8 * (tid / NR);
+  // a gathered row is written one RHS per thread: padded to NR + 1 entries against bank conflicts
+  const int xstride = a.gather ? NR + 1 : NR;
+  float2* xs = lsm;                        // [cap][xstride]: the round's panel rows
+  float2* vs = lsm + cap * xstride;        // [cap][R8]: conj V, zero for k >= R
   const int pg = __ldg(a.off + c * g), p0 = __ldg(a.off + j), np = __ldg(a.off + j + 1) - p0;
-  float acc[MTMAX][2][4];
+  float2 acc[8];
 #pragma unroll
-  for (int mt = 0; mt < MTMAX; ++mt)
-#pragma unroll
-    for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) acc[mt][nt][r] = 0.f;
+  for (int u = 0; u < 8; ++u) acc[u] = make_float2(0.f, 0.f);
   if (np > 0) {
     const Item it = a.items[a.item_base + int64_t(g) * a.item_stride];
     const uint8_t* ibase = a.arena + size_t(it.off128) * 128;
-    const int bp = tid & 7, nq = tid >> 3;          // x: points 2 bp, 2 bp + 1; RHS 4 nq .. 4 nq + 3
-    for (int b0 = 0; b0 < np; b0 += KP) {
-      const int nb = min(KP, np - b0);
-      if (b0 > 0) __syncthreads();                  // the previous round's operands are consumed
-      // ---- loads: x (8 values) and W (entries of this thread's (point pair, k) items)
-      float2 x[2][4];
-      {
-        const int b = 2 * bp;
-        int nat0 = 0, nat1 = 0;
-        if (a.gather) {
-          if (b < nb) nat0 = __ldg(a.perm + p0 + b0 + b);
-          if (b + 1 < nb) nat1 = __ldg(a.perm + p0 + b0 + b + 1);
-        }
+    const int kq = tid % R8, bq = tid / R8, bstep = nth / R8;   // entry k = kq of points bq + bstep u
+    for (int b0 = 0; b0 < np; b0 += cap) {
+      const int nb = min(cap, np - b0);
+      if (b0 > 0) __syncthreads();         // previous round's shared reads done
+      const float2* src = a.vec + int64_t(p0 + b0) * NR;
+      if (a.gather) {
+        // the round's points straight from g in natural order: thread q reads RHS
+        // q / nb of point q % nb, so that a warp's loads fall on a few nearby rows
+        for (int q = tid; q < nb; q += nth) nat[q] = __ldg(a.perm + p0 + b0 + q);
+        __syncthreads();
+        for (int q0 = tid; q0 < nb * NR; q0 += 4 * nth) {        // 4 loads in flight per thread
+          float2 v[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int n = 4 * nq + q, rhs = a.rhs0 + n;
-          x[0][q] = make_float2(0.f, 0.f);
-          x[1][q] = make_float2(0.f, 0.f);
-          if (a.gather) {
-            if (rhs < a.nrhs) {
-              const float2* row = a.vec + int64_t(rhs) * a.len_vec;
-              if (b < nb) x[0][q] = __ldg(row + nat0);
-              if (b + 1 < nb) x[1][q] = __ldg(row + nat1);
-            }
-          } else {
-            const float2* src = a.vec + int64_t(p0 + b0 + b) * NR + n;
-            if (b < nb) x[0][q] = __ldg(src);
-            if (b + 1 < nb) x[1][q] = __ldg(src + NR);
+          for (int u = 0; u < 4; ++u) {
+            const int q = q0 + u * nth, nn = q / nb, b = q - nn * nb, rhs = a.rhs0 + nn;
+            v[u] = (q < nb * NR && rhs < a.nrhs) ? __ldg(a.vec + int64_t(rhs) * a.len_vec + nat[b])
+                                                 : make_float2(0.f, 0.f);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int q = q0 + u * nth, nn = q / nb, b = q - nn * nb;
+            if (q < nb * NR) xs[b * xstride + nn] = v[u];
           }
         }
+      } else {
+        for (int q = tid; q < nb * (NR / 2); q += nth) cp_async16(sa(xs) + uint32_t(q) * 16u, src + 2 * q);
       }
-      // W: pairs (point pair pp, k), q = pp * R8 + k over 8 R8 pairs
-      constexpr int kWMax = 4;                      // 8 R8 / 128 <= 4 for R8 <= 64
-      float2 w[kWMax][2];
+      for (int b1 = bq; b1 < nb; b1 += 8 * bstep) {             // 8 loads in flight per thread
+        float2 v[8];
 #pragma unroll
-      for (int u = 0; u < kWMax; ++u) {
-        const int q = tid + u * kLeafVThreads;
-        w[u][0] = w[u][1] = make_float2(0.f, 0.f);
-        if (q < 8 * R8) {
-          const int pp = q / R8, k = q - pp * R8, b = 2 * pp;
-          if (k < R) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              if (b + h < nb) {
-                const int pt = p0 - pg + b0 + b + h;
-                if (XPOSE) {
-                  const float2 e = item_entry(ibase, it, k, pt);
-                  w[u][h] = make_float2(e.x, -e.y);
-                } else {
-                  w[u][h] = item_entry(ibase, it, pt, k);
-                }
-              }
+        for (int u = 0; u < 8; ++u) {
+          const int b = b1 + u * bstep, pt = p0 - pg + b0 + b;
+          v[u] = make_float2(0.f, 0.f);
+          if (b < nb && kq < R) {
+            if (XPOSE) {
+              const float2 e = item_entry(ibase, it, kq, pt);
+              v[u] = make_float2(e.x, -e.y);
+            } else {
+              v[u] = item_entry(ibase, it, pt, kq);
             }
           }
         }
-      }
-      // ---- split and store the operands
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int n = 4 * nq + q;
-        uint32_t h, l;
-        split2(x[0][q].x, x[1][q].x, h, l);          // real parts, k = 2 bp, 2 bp + 1
-        *reinterpret_cast<uint32_t*>(bh + n * ST + 2 * bp) = h;
-        *reinterpret_cast<uint32_t*>(bl + n * ST + 2 * bp) = l;
-        split2(x[0][q].y, x[1][q].y, h, l);          // imaginary parts, k = 16 + 2 bp, ...
-        *reinterpret_cast<uint32_t*>(bh + n * ST + KP + 2 * bp) = h;
-        *reinterpret_cast<uint32_t*>(bl + n * ST + KP + 2 * bp) = l;
+        for (int u = 0; u < 8; ++u)
+          if (b1 + u * bstep < nb) vs[(b1 + u * bstep) * R8 + kq] = v[u];
       }
-#pragma unroll
-      for (int u = 0; u < kWMax; ++u) {
-        const int q = tid + u * kLeafVThreads;
-        if (q < 8 * R8) {
-          const int pp = q / R8, k = q - pp * R8;
-          uint32_t h, l;
-          // row k (Y_re): [W_re | -W_im]; row R8 + k (Y_im): [W_im | W_re]
-          split2(w[u][0].x, w[u][1].x, h, l);
-          *reinterpret_cast<uint32_t*>(ah + k * ST + 2 * pp) = h;
-          *reinterpret_cast<uint32_t*>(al + k * ST + 2 * pp) = l;
-          *reinterpret_cast<uint32_t*>(ah + (R8 + k) * ST + KP + 2 * pp) = h;
-          *reinterpret_cast<uint32_t*>(al + (R8 + k) * ST + KP + 2 * pp) = l;
-          split2(-w[u][0].y, -w[u][1].y, h, l);
-          *reinterpret_cast<uint32_t*>(ah + k * ST + KP + 2 * pp) = h;
-          *reinterpret_cast<uint32_t*>(al + k * ST + KP + 2 * pp) = l;
-          split2(w[u][0].y, w[u][1].y, h, l);
-          *reinterpret_cast<uint32_t*>(ah + (R8 + k) * ST + 2 * pp) = h;
-          *reinterpret_cast<uint32_t*>(al + (R8 + k) * ST + 2 * pp) = l;
-        }
-      }
+      cp_async_wait_all();
       __syncthreads();
       if (!a.gather) {   // the panel rows are read by this CTA alone and never again
-        const char* lines = reinterpret_cast<const char*>(a.vec + int64_t(p0 + b0) * NR);
-        for (int q = tid; q < nb * (NR * int(sizeof(float2)) / 128); q += kLeafVThreads)
-          tc::l2_discard(lines + 128 * q);
+        const char* lines = reinterpret_cast<const char*>(src);
+        for (int q = tid; q < nb * (NR * int(sizeof(float2)) / 128); q += nth) l2_discard(lines + 128 * q);
       }
-      // ---- MMAs: two K16 steps (real parts, imaginary parts of the round's points)
-      const uint32_t sbh = tc::sa(bh), sbl = tc::sa(bl), sah = tc::sa(ah), sal = tc::sa(al);
-      // ldmatrix row addresses: B (two n8 tiles of this warp): n = 16 warp + lane % 8 +
-      // 8 (lane / 16), k offset 8 ((lane / 8) % 2); A: m = lane % 8 + 8 ((lane / 8) % 2),
-      // k offset 8 (lane / 16)
-      const uint32_t boff = uint32_t((16 * warp + (lane & 7) + 8 * (lane >> 4)) * ST + 8 * ((lane >> 3) & 1)) * 2u;
-      const uint32_t aoff = uint32_t(((lane & 7) + 8 * ((lane >> 3) & 1)) * ST + 8 * (lane >> 4)) * 2u;
-#pragma unroll
-      for (int ks = 0; ks < 2; ++ks) {
-        uint32_t bhi[4], blo[4];
-        ldsm_x4(sbh + boff + uint32_t(ks) * 32u, bhi[0], bhi[1], bhi[2], bhi[3]);
-        ldsm_x4(sbl + boff + uint32_t(ks) * 32u, blo[0], blo[1], blo[2], blo[3]);
-#pragma unroll
-        for (int mt = 0; mt < MTMAX; ++mt) {
-          if (mt < MT) {
-            uint32_t ahi[4], alo[4];
-            const uint32_t mo = uint32_t(16 * mt * ST) * 2u + aoff + uint32_t(ks) * 32u;
-            ldsm_x4(sah + mo, ahi[0], ahi[1], ahi[2], ahi[3]);
-            ldsm_x4(sal + mo, alo[0], alo[1], alo[2], alo[3]);
-#pragma unroll
-            for (int nt = 0; nt < 2; ++nt) {
-              mma_m16n8k16(acc[mt][nt], ahi, bhi[2 * nt], bhi[2 * nt + 1]);
-              mma_m16n8k16(acc[mt][nt], ahi, blo[2 * nt], blo[2 * nt + 1]);
-              mma_m16n8k16(acc[mt][nt], alo, bhi[2 * nt], bhi[2 * nt + 1]);
-            }
-          }
-        }
-      }
-    }
-    __syncthreads();                                // operands consumed: the stage area is free
-  }
-  // ---- accumulators -> shared [n][2 R8 + 4] floats (row m: Y_re for m < R8, else Y_im)
-  float* ds = reinterpret_cast<float*>(lvs);
-  const int SD = 2 * R8 + 4;
-#pragma unroll
-  for (int mt = 0; mt < MTMAX; ++mt) {
-    if (mt < MT) {
-#pragma unroll
-      for (int nt = 0; nt < 2; ++nt) {
-        const int m = 16 * mt + (lane >> 2), n = 16 * warp + 8 * nt + 2 * (lane & 3);
-        ds[n * SD + m] = acc[mt][nt][0];
-        ds[(n + 1) * SD + m] = acc[mt][nt][1];
-        ds[n * SD + m + 8] = acc[mt][nt][2];
-        ds[(n + 1) * SD + m + 8] = acc[mt][nt][3];
-      }
+#pragma unroll 4
+      for (int b = 0; b < nb; ++b) leaf_v_point(acc, vs + b * R8 + k0, xs[b * xstride + n]);
     }
   }
-  __syncthreads();
-  // ---- split block j: for (k8 chunk kc, row mo = 2 n + ri) a 16-byte run of 8 k
-  const int64_t blk = split_block_bytes(R8);
-  for (int q = tid; q < (R8 / 8) * 2 * NR; q += kLeafVThreads) {
-    const int kc = q / (2 * NR), mo = q - kc * (2 * NR), n = mo >> 1, ri = mo & 1;
-    const float4* src = reinterpret_cast<const float4*>(ds + n * SD + ri * R8 + 8 * kc);
-    const float4 v0 = src[0], v1 = src[1];
-    const float y[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-    if constexpr (TF32) {   // TF32 block: byte (k / 4) 2048 + (m / 8) 128 + (m % 8) 16 + (k % 4) 4
-      uint8_t* o = a.outs + int64_t(j) * blk + (2 * kc) * 2048 + (mo >> 3) * 128 + (mo & 7) * 16;
-      *reinterpret_cast<uint4*>(o) = tc::tf32x4(y);
-      *reinterpret_cast<uint4*>(o + 2048) = tc::tf32x4(y + 4);
-    } else {
-      uint4 hi, lo;
-      tc::split8(y, hi, lo);
-      uint8_t* o = a.outs + int64_t(j) * blk + kc * 2048 + (mo >> 3) * 128 + (mo & 7) * 16;
-      *reinterpret_cast<uint4*>(o) = hi;
-      *reinterpret_cast<uint4*>(o + int64_t(R8) * 256) = lo;
-    }
-  }
+  store_split8<TF32>(a.outs, j, R8, n, k0, acc);
 }
 
 // U^L for a panel, one CTA per group g (leaves i = c g + t) or, with leaf_split, one
@@ -1099,12 +1009,16 @@ size_t tc_smem_bytes(int nsa, int nxb, int nsets, int mt_max, int kpad_max) {
          (2 * size_t(nsa) + 20) * 8 + 64;
 }
 
-size_t leaf_smem_bytes(int R, int c, bool u_side) {
+size_t leaf_smem_bytes(int R, int c, bool u_side, int pts_cap) {
   const int R8 = (R + 7) & ~7;
   return u_side ? size_t(c) * R * 2 * kTcNR * sizeof(float) + size_t(R) * kLeafPts * sizeof(float2)
-                : leaf_v_smem_bytes(R8);
+                : sizeof(float2) * size_t(pts_cap) * (kTcNR + 1 + R8);
 }
 
+int leaf_pts_cap(int64_t max_leaf_points) {
+  const int64_t r8 = (max_leaf_points + 7) & ~int64_t(7);
+  return int(std::min<int64_t>(kLeafPts, std::max<int64_t>(8, r8)));
+}
 
 bool leaf_fits(int R8, int c) { return R8 <= kLeafMaxR8 && c <= kLeafMaxC; }
 
@@ -1210,21 +1124,16 @@ cudaError_t launch_permute_in(const LeafArgs& a, cudaStream_t stream) {
 }
 
 cudaError_t launch_leaf(const LeafArgs& a, bool u_side, int n_groups, cudaStream_t stream, bool tf32, bool xpose) {
-  const size_t smem = u_side ? leaf_smem_bytes(a.R, a.leaf_split ? 1 : a.c, true) : leaf_v_smem_bytes(a.R8);
-  void (*kern)(LeafArgs) = nullptr;
-  if (u_side) {
-    kern = xpose ? leaf_u_kernel<true> : leaf_u_kernel<false>;
-  } else if (a.R8 <= 32) {   // m16 tiles of the 2 R8 accumulator rows: 4 at most
-    kern = tf32 ? (xpose ? leaf_v_kernel<4, true, true> : leaf_v_kernel<4, true, false>)
-                : (xpose ? leaf_v_kernel<4, false, true> : leaf_v_kernel<4, false, false>);
-  } else {
-    kern = tf32 ? (xpose ? leaf_v_kernel<8, true, true> : leaf_v_kernel<8, true, false>)
-                : (xpose ? leaf_v_kernel<8, false, true> : leaf_v_kernel<8, false, false>);
-  }
-  // U^L: a CTA per group (or leaf); (V^L)^*: a CTA per leaf
-  const int threads = u_side ? kLeafThreads : kLeafVThreads;
+  const size_t smem = u_side ? leaf_smem_bytes(a.R, a.leaf_split ? 1 : a.c, true)
+                             : sizeof(float2) * size_t(a.pts_cap) * (kTcNR + (a.gather ? 1 : 0) + a.R8);
+  void (*kern)(LeafArgs) =
+      u_side ? (xpose ? leaf_u_kernel<true> : leaf_u_kernel<false>)
+             : (tf32 ? (xpose ? leaf_v_kernel<true, true> : leaf_v_kernel<true, false>)
+                     : (xpose ? leaf_v_kernel<false, true> : leaf_v_kernel<false, false>));
+  // U^L: a CTA per group; (V^L)^*: a CTA per leaf, one thread per RHS column and group of 8 rows
+  const int threads = u_side ? kLeafThreads : kTcNR * (a.R8 / 8);
   const int64_t blocks = (u_side && !a.leaf_split) ? int64_t(n_groups) : int64_t(n_groups) * a.c;
-  if (!u_side && (a.R8 < 8 || a.R8 > kLeafMaxR8 || a.R8 % 8 != 0)) return cudaErrorInvalidValue;
+  if (!u_side && (a.pts_cap < 8 || a.pts_cap > kLeafPts || a.pts_cap % 8 != 0)) return cudaErrorInvalidValue;
   if (blocks <= 0) return cudaSuccess;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (err != cudaSuccess) return err;

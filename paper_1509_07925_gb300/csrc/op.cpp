@@ -529,6 +529,8 @@ mbf_op_s* op_create(const mbf_factors_t& f) {
     pk.run(*op);
     op->nnz_leaf_x = pk.leaf_x_nnz;
     op->bytes_packed = int64_t(pk.arena.size());
+    if (op->nnz <= 0)   // not given with the factors: the nonzero entries packed
+      for (int64_t v : op->nnz_stage) op->nnz += v;
     int64_t rmax = 1;
     for (int l = op->h; l <= op->L; ++l) rmax = std::max<int64_t>({rmax, op->RU[size_t(l)], op->RV[size_t(l)]});
     op->positions = Tree::ipow(op->c, op->L) * rmax;
@@ -747,6 +749,7 @@ void apply_tc(mbf_op_s* op, Workspace& w, const float2* g, float2* u, int64_t nr
     la.c = op->c;
     la.R = op->RV[size_t(op->L)];
     la.R8 = tp.st[0].R8_in;
+    la.pts_cap = leaf_pts_cap(op->leaf_pts_w);
     e0 = prof_begin(op, st);
     cuda_check(launch_leaf(la, false, leaf_st.n_groups, st, tf32), "leaf (V^L)^* launch");
     prof_end(op, PK_LEAF_V, e0, st);
@@ -857,6 +860,7 @@ void apply_tc_adj(mbf_op_s* op, Workspace& w, const float2* u, float2* g, int64_
     la.c = op->c;
     la.R = op->RU[size_t(op->L)];
     la.R8 = ap.st[0].R8_in;
+    la.pts_cap = leaf_pts_cap(op->leaf_pts_x);
     e0 = prof_begin(op, st);
     cuda_check(launch_leaf(la, false, last_st.n_groups, st, false, true), "leaf (U^L)^* launch");
     prof_end(op, PK_LEAF_V, e0, st);

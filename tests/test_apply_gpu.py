@@ -49,6 +49,17 @@ def ops(bd):
     return get
 
 
+@pytest.mark.parametrize("case", CASES[:3])
+def test_nnz_counted_when_factors_do_not_give_it(ops, case):
+    """Factors imported without a nonzero count (mbf_factors_t.nnz = 0): the operator reports
+    the nonzero entries its packer stored, i.e. the oracle's count of the unpadded factors
+    less the diagonal S entries, which are folded into the G^h tiles."""
+    op, fs, _ = ops(case)
+    nnz = op.info().nnz_algorithmic
+    exp = fs.nnz_algorithmic()
+    assert exp - int(np.sum(fs.kU[fs.h])) <= nnz <= exp
+
+
 @pytest.mark.parametrize("case", CASES)
 @pytest.mark.parametrize("nrhs", [1, 3, 4, 9])
 def test_forward_matches_oracle(ops, case, nrhs):
