@@ -90,7 +90,9 @@ struct LeafArgs {
   int32_t pts_cap;          // (V^L)^*: points staged per round (leaf_pts_cap of the largest leaf)
   int32_t leaf_split;       // U^L side: 1 = one CTA per leaf (ragged trees), 0 = one per group
   int32_t gather;           // (V^L)^* side: 1 = vec is [nrhs][len_vec] in natural order, read through
-                            // perm (tree position -> natural index); 0 = the tree-ordered panel
+                            // nat; 0 = the tree-ordered panel
+  int32_t nat_stride;       // (V^L)^* gather: entries per leaf in nat
+  const int32_t* nat;       // (V^L)^* gather: leaf j's natural indices at nat[j * nat_stride + b]
 };
 
 size_t simt_smem_bytes(int nrb, int ns);

@@ -783,7 +783,8 @@ __device__ __forceinline__ void store_split8(uint8_t* outs, int64_t leaf, int R8
 // ragged tree puts several times the mean number of points into some groups).  The
 // panel rows are read by this CTA alone and never again: their L2 lines are discarded
 // rather than written back.  With `gather` the rows come straight from g in natural
-// order through the tree permutation instead (no panel, no permute kernel): device
+// order through the leaf's table of natural indices instead (no panel, no permute
+// kernel; the table, unlike the tree permutation, needs no offset load first): device
 // buffers take this route; page-locked host buffers keep the panel, read row by row.
 // Empty leaves give zero blocks.
 __device__ __forceinline__ void leaf_v_point(float2 (&acc)[8], const float2* vrow, float2 x) {
@@ -815,12 +816,17 @@ __global__ void __launch_bounds__(kTcNR * kLeafMaxR8 / 8) leaf_v_kernel(const __
   const int xstride = a.gather ? NR + 1 : NR;
   float2* xs = lsm;                        // [cap][xstride]: the round's panel rows
   float2* vs = lsm + cap * xstride;        // [cap][R8]: conj V, zero for k >= R
-  const int pg = __ldg(a.off + c * g), p0 = __ldg(a.off + j), np = __ldg(a.off + j + 1) - p0;
+  // first-level loads, all independent of one another: the leaf's offsets, its group's
+  // item and (gather) the natural indices of its first round's points
+  const int pg = __ldg(a.off + c * g), p0 = __ldg(a.off + j), p1 = __ldg(a.off + j + 1);
+  const Item it = a.items[a.item_base + int64_t(g) * a.item_stride];
+  const int32_t* natj = a.nat + int64_t(j) * a.nat_stride;
+  const int nat0 = (a.gather && tid < cap) ? __ldg(natj + tid) : 0;
+  const int np = p1 - p0;
   float2 acc[8];
 #pragma unroll
   for (int u = 0; u < 8; ++u) acc[u] = make_float2(0.f, 0.f);
   if (np > 0) {
-    const Item it = a.items[a.item_base + int64_t(g) * a.item_stride];
     const uint8_t* ibase = a.arena + size_t(it.off128) * 128;
     const int kq = tid % R8, bq = tid / R8, bstep = nth / R8;   // entry k = kq of points bq + bstep u
     for (int b0 = 0; b0 < np; b0 += cap) {
@@ -830,7 +836,7 @@ __global__ void __launch_bounds__(kTcNR * kLeafMaxR8 / 8) leaf_v_kernel(const __
       if (a.gather) {
         // the round's points straight from g in natural order: thread q reads RHS
         // q / nb of point q % nb, so that a warp's loads fall on a few nearby rows
-        for (int q = tid; q < nb; q += nth) nat[q] = __ldg(a.perm + p0 + b0 + q);
+        for (int q = tid; q < nb; q += nth) nat[q] = b0 == 0 ? nat0 : __ldg(natj + b0 + q);
         __syncthreads();
         for (int q0 = tid; q0 < nb * NR; q0 += 4 * nth) {        // 4 loads in flight per thread
           float2 v[4];

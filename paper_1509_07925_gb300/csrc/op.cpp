@@ -492,6 +492,8 @@ void op_free(mbf_op_s* op) {
   cudaFree(op->d_x_off);
   cudaFree(op->d_w_perm);
   cudaFree(op->d_w_off);
+  cudaFree(op->d_x_nat);
+  cudaFree(op->d_w_nat);
   ws_free(op->ws);
   cudaFree(op->d_stage_in);
   cudaFree(op->d_stage_out);
@@ -567,6 +569,15 @@ mbf_op_s* op_create(const mbf_factors_t& f) {
     op->d_x_off = dev_upload(to32(f.x_off, nL + 1), "x_off");
     op->d_w_perm = dev_upload(to32(f.w_perm, std::max<int64_t>(f.n_w, 1)), "w_perm");
     op->d_w_off = dev_upload(to32(f.w_off, nL + 1), "w_off");
+    auto nat_table = [&](const int64_t* perm, const int64_t* off, int64_t max_pts, int32_t* stride) {
+      *stride = int32_t(std::max<int64_t>(8, (max_pts + 7) & ~int64_t(7)));
+      std::vector<int32_t> t(size_t(nL) * size_t(*stride), 0);
+      for (int64_t q = 0; q < nL; ++q)
+        for (int64_t b = off[q]; b < off[q + 1]; ++b) t[size_t(q) * size_t(*stride) + size_t(b - off[q])] = int32_t(perm[b]);
+      return t;
+    };
+    op->d_x_nat = dev_upload(nat_table(f.x_perm, f.x_off, op->leaf_pts_x, &op->x_nat_stride), "X leaf index table");
+    op->d_w_nat = dev_upload(nat_table(f.w_perm, f.w_off, op->leaf_pts_w, &op->w_nat_stride), "Omega leaf index table");
     ws_init(op, op->ws);
     for (int nrb : {1, 2, 4}) cuda_check(simt_config(nrb, &op->grid, &op->ns[nrb], &op->smem[nrb]), "simt_config");
     cuda_check(cudaDeviceGetAttribute(&op->sms, cudaDevAttrMultiProcessorCount, op->device), "attr");
@@ -742,6 +753,8 @@ void apply_tc(mbf_op_s* op, Workspace& w, const float2* g, float2* u, int64_t nr
     la.vec = host_io ? w.tc_gt : g;
     la.gather = host_io ? 0 : 1;
     la.perm = op->d_w_perm;
+    la.nat = op->d_w_nat;
+    la.nat_stride = op->w_nat_stride;
     la.len_vec = op->n_in;
     la.nrhs = int32_t(nrhs);
     la.rhs0 = int32_t(r0);
@@ -853,6 +866,8 @@ void apply_tc_adj(mbf_op_s* op, Workspace& w, const float2* u, float2* g, int64_
     la.vec = host_io ? w.tc_gt : u;
     la.gather = host_io ? 0 : 1;
     la.perm = op->d_x_perm;
+    la.nat = op->d_x_nat;
+    la.nat_stride = op->x_nat_stride;
     la.len_vec = op->n_out;
     la.nrhs = int32_t(nrhs);
     la.rhs0 = int32_t(r0);

@@ -43,6 +43,10 @@ struct mbf_op_s {
   mbf::Item* d_items = nullptr;
   int32_t *d_x_perm = nullptr, *d_x_off = nullptr, *d_w_perm = nullptr, *d_w_off = nullptr;
   int64_t leaf_pts_x = 0, leaf_pts_w = 0;   // points of the largest X / Omega leaf
+  // per leaf, the natural indices of its points (tree order), padded to a stride of the
+  // largest leaf rounded up to 8: the leaf kernels' gathers need no offset load first
+  int32_t *d_x_nat = nullptr, *d_w_nat = nullptr;
+  int32_t x_nat_stride = 0, w_nat_stride = 0;
   int32_t split_x = 0, split_w = 0;         // U^L-side leaf kernels: one CTA per leaf (ragged tree)
   mbf::Workspace ws;                // the scratch of the operator's own applies
   int grid = 0, ns[5] = {0, 0, 0, 0, 0};
