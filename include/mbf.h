@@ -370,7 +370,8 @@ mbf_status mbf_msbf_destroy(mbf_msbf_t m);
  * The paper has no counterpart (its applies are single-threaded CPU loops).  Measures,
  * on `stream` with device buffers it allocates and frees itself, (a) the FP32 SIMT apply
  * for 1, 2, 4, 8, 16, 32 and 64 RHS, (b) the tensor-core apply of one 64-RHS panel for
- * the even A-tile ring depths 2 .. 16 that fit shared memory, then keeps the fastest and
+ * two or three panel buffers, each with the even A-tile ring depths 2 .. 16 that fit
+ * shared memory beside them (8 configurations at most), then keeps the fastest and
  * sets the RHS count from which MBF_PREC_AUTO takes the tensor cores to the smallest
  * measured count at which one panel is faster than the SIMT apply.  Blocking; the
  * operator must be idle.  The choices stay with the operator until it is destroyed. */
@@ -380,9 +381,13 @@ typedef struct mbf_tune_result {
   double simt_ms[8];            /* device time of one SIMT apply of simt_rhs[i] RHS  */
   int32_t n_slots;
   int32_t slots[8];
-  double tc_ms[8];              /* one 64-RHS panel with slots[i] A-ring slots       */
+  double tc_ms[8];              /* one 64-RHS panel with slots[i] A-ring slots and
+                                   panel_buffers[i] panel buffers                    */
   int32_t tc_slots_chosen;      /* 0 if the tensor path is unavailable               */
   int32_t tc_min_rhs;           /* AUTO uses the tensor cores from this many RHS     */
+  int32_t panel_buffers[8];     /* panel buffers of configuration i (2 or 3)          */
+  int32_t tc_buffers_chosen;    /* panel buffers kept                                 */
+  int32_t reserved_tune;
 } mbf_tune_result_t;
 mbf_status mbf_op_tune(mbf_op_t op, void* stream, mbf_tune_result_t* out);
 
@@ -396,8 +401,9 @@ mbf_status mbf_op_tune(mbf_op_t op, void* stream, mbf_tune_result_t* out);
  *                queue returns MBF_ERR_BUSY.
  *   worker       continuous batching: whenever a slot is free it forms a batch: the
  *                oldest queued request with the queued requests on the same operator
- *                (FIFO, up to max_batch_rhs RHS, applied at once through a staging panel)
- *                is its first group.  When requests back up (more queued than
+ *                (FIFO, up to max_batch_rhs RHS, applied at once: in place through a
+ *                table of the requests' rows up to 64 RHS, beyond that through a staging
+ *                panel) is its first group.  When requests back up (more queued than
  *                max_inflight * max_batch_ops) and more operators are queued than slots
  *                are free, the oldest requests on other operators add groups the same
  *                way, spreading the queued operators over the free slots, at most

@@ -74,7 +74,8 @@ PROFILE_KINDS = 8
 class TuneResult(C.Structure):
     _fields_ = [("n_simt", C.c_int32), ("simt_rhs", C.c_int32 * 8), ("simt_ms", C.c_double * 8),
                 ("n_slots", C.c_int32), ("slots", C.c_int32 * 8), ("tc_ms", C.c_double * 8),
-                ("tc_slots_chosen", C.c_int32), ("tc_min_rhs", C.c_int32)]
+                ("tc_slots_chosen", C.c_int32), ("tc_min_rhs", C.c_int32), ("panel_buffers", C.c_int32 * 8),
+                ("tc_buffers_chosen", C.c_int32), ("reserved_tune", C.c_int32)]
 
 
 class ServerOpts(C.Structure):

@@ -9,6 +9,15 @@
 
 namespace mbf {
 
+// Per-RHS row addresses of an apply's input and output, for up to kRowTab RHS: a served
+// batch applies its requests' rows where the callers put them, with no staging copies.
+// in[r] (n_in entries) and out[r] (n_out entries) for RHS r < nrhs.
+constexpr int kRowTab = 64;
+struct RowTable {
+  const float2* in[kRowTab];
+  float2* out[kRowTab];
+};
+
 struct ApplyArgs {
   const uint8_t* arena;
   const Item* items;
@@ -33,6 +42,8 @@ struct ApplyArgs {
   // gives up after wait_ns instead of kTimeoutNs.
   uint64_t wait_ns;
   int32_t stall_stage1, stall_pad_;
+  int32_t use_rows, rows_pad_;   // 1: in / out rows from `rows` (nrhs <= kRowTab)
+  RowTable rows;
   Plan plan;
 };
 
@@ -93,6 +104,8 @@ struct LeafArgs {
                             // nat; 0 = the tree-ordered panel
   int32_t nat_stride;       // (V^L)^* gather: entries per leaf in nat
   const int32_t* nat;       // (V^L)^* gather: leaf j's natural indices at nat[j * nat_stride + b]
+  int32_t use_rows, rows_pad_;   // 1: (V^L)^* gather reads rows.in[rhs], U^L writes rows.out[rhs]
+  RowTable rows;
 };
 
 size_t simt_smem_bytes(int nrb, int ns);

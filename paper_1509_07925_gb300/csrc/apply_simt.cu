@@ -88,6 +88,14 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   return v;
 }
 
+// Row of RHS `rhs` of the input / output: contiguous [nrhs][len], or the row table.
+__device__ __forceinline__ const float2* in_row(const ApplyArgs& a, int rhs) {
+  return a.use_rows ? a.rows.in[rhs] : a.in + int64_t(rhs) * a.in_len;
+}
+__device__ __forceinline__ float2* out_row(const ApplyArgs& a, int rhs) {
+  return a.use_rows ? a.rows.out[rhs] : a.out + int64_t(rhs) * a.out_len;
+}
+
 __device__ __forceinline__ void set_status(int* status, volatile int* abort, int code) {
   atomicCAS(status, 0, code);
   *abort = 1;
@@ -491,7 +499,7 @@ __global__ void __launch_bounds__(Cfg<NRB>::W * 32, 1) bf_apply_simt(const __gri
 #pragma unroll
                 for (int r = 0; r < NRB; ++r)
                   v[u][r] = (pt < npts && rhs0 + r < a.nrhs)
-                                ? __ldg(a.in + int64_t(rhs0 + r) * a.in_len + idx[u])
+                                ? __ldg(in_row(a, rhs0 + r) + idx[u])
                                 : make_float2(0.f, 0.f);
               }
 #pragma unroll
@@ -764,7 +772,7 @@ __global__ void __launch_bounds__(Cfg<NRB>::W * 32, 1) bf_apply_simt(const __gri
 #pragma unroll
                 for (int r = 0; r < NRB; ++r)
                   if (rhs0 + r < a.nrhs) {
-                    float2* o = a.out + int64_t(rhs0 + r) * a.out_len + idx[u];
+                    float2* o = out_row(a, rhs0 + r) + idx[u];
                     float2 v = res[pt * NRB + r];
                     if (a.accumulate) {
                       const float2 w = *o;

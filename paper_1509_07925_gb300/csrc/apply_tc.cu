@@ -235,6 +235,7 @@ __device__ __forceinline__ bool wait_bar(uint64_t* b, uint32_t ph, volatile int*
 
 constexpr int kTcThreads = 448;   // 14 warps (roles above)
 constexpr int kAProducers = 2;    // lanes of warp 0 issuing the tile copies
+constexpr int kMaxXBufs = 3;      // panel buffers at most (the autotuner picks 2 or 3)
 constexpr int kTcChunk = 16;   // accumulator columns per epilogue step
 
 // TF32: the vectors between stages are TF32 blocks (apply.hpp) and the tiles two FP32
@@ -251,8 +252,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
   uint64_t* afull = reinterpret_cast<uint64_t*>(xbuf + size_t(nxb) * x_buf);
   uint64_t* aempty = afull + nsa;
   uint64_t* xfull = aempty + nsa;
-  uint64_t* xempty = xfull + 2;
-  uint64_t* dfull = xempty + 2;
+  uint64_t* xempty = xfull + kMaxXBufs;
+  uint64_t* dfull = xempty + kMaxXBufs;
   uint64_t* dempty = dfull + 2;
   uint64_t* stored = dempty + 2;     // [set]: the set's output blocks of a group are written
   uint64_t* signaled = stored + 2;   // [set]: the signal warp has counted them in
@@ -266,9 +267,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
       mbar_init(&afull[i], 1);
       mbar_init(&aempty[i], 1);
     }
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < nxb; ++s) {
       mbar_init(&xfull[s], 1);
       mbar_init(&xempty[s], 1);
+    }
+    for (int s = 0; s < 2; ++s) {
       mbar_init(&dfull[s], 1);
       mbar_init(&dempty[s], 128);
     }
@@ -843,7 +846,8 @@ __global__ void __launch_bounds__(kTcNR * kLeafMaxR8 / 8) leaf_v_kernel(const __
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const int q = q0 + u * nth, nn = q / nb, b = q - nn * nb, rhs = a.rhs0 + nn;
-            v[u] = (q < nb * NR && rhs < a.nrhs) ? __ldg(a.vec + int64_t(rhs) * a.len_vec + nat[b])
+            v[u] = (q < nb * NR && rhs < a.nrhs)
+                       ? __ldg((a.use_rows ? a.rows.in[rhs] : a.vec + int64_t(rhs) * a.len_vec) + nat[b])
                                                  : make_float2(0.f, 0.f);
           }
 #pragma unroll
@@ -993,7 +997,7 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_u_kernel(const __grid_const
       for (int j = 0; j < MN; ++j) {
         const int rhs = a.rhs0 + MN * nq + j;
         if (rhs < a.nrhs) {
-          float2* o = a.outp + int64_t(rhs) * a.len_out + nat;
+          float2* o = (a.use_rows ? a.rows.out[rhs] : a.outp + int64_t(rhs) * a.len_out) + nat;
           float2 v = acc[j];
           if (a.accumulate) {
             const float2 w = *o;
@@ -1030,6 +1034,7 @@ bool leaf_fits(int R8, int c) { return R8 <= kLeafMaxR8 && c <= kLeafMaxC; }
 
 cudaError_t launch_apply_tc(const TCArgs& a, int grid, size_t smem, cudaStream_t stream, bool tf32) {
   if (a.nsa < kAProducers || a.nsa % kAProducers != 0) return cudaErrorInvalidValue;
+  if (a.nxb < 1 || a.nxb > kMaxXBufs) return cudaErrorInvalidValue;
   cudaError_t err = cudaMemsetAsync(a.counters, 0, tc_counter_bytes(a.plan), stream);
   if (err != cudaSuccess) return err;
   void (*kern)(TCArgs) = tf32 ? bf_apply_tc<true> : bf_apply_tc<false>;

@@ -702,7 +702,7 @@ void prof_collect(mbf_op_s* op) {
 // (V^L)^* leaf kernel, the persistent tcgen05 kernel over the G / H levels, the U^L leaf
 // kernel (which scatters u to natural order).
 void apply_tc(mbf_op_s* op, Workspace& w, const float2* g, float2* u, int64_t nrhs, cudaStream_t st, int grid, bool accumulate,
-              bool host_io, bool tf32) {
+              bool host_io, bool tf32, const RowTable* rows = nullptr) {
   if (!op->tc_unavailable.empty()) fail(MBF_ERR_INVALID, "tensor path unavailable: " + op->tc_unavailable);
   const TCPlan& tp = op->tcplan;
   const int S = tp.n_stages;
@@ -751,6 +751,10 @@ void apply_tc(mbf_op_s* op, Workspace& w, const float2* g, float2* u, int64_t nr
     la.item_stride = leaf_st.n_items;
     la.off = op->d_w_off;
     la.vec = host_io ? w.tc_gt : g;
+    if (rows) {   // one panel (nrhs <= kRowTab): the rows are addressed by RHS index
+      la.use_rows = 1;
+      la.rows = *rows;
+    }
     la.gather = host_io ? 0 : 1;
     la.perm = op->d_w_perm;
     la.nat = op->d_w_nat;
@@ -794,6 +798,10 @@ void apply_tc(mbf_op_s* op, Workspace& w, const float2* g, float2* u, int64_t nr
     lu.off = op->d_x_off;
     lu.wl = ylast;
     lu.outp = u;
+    if (rows) {
+      lu.use_rows = 1;
+      lu.rows = *rows;
+    }
     lu.len_out = op->n_out;
     lu.nrhs = int32_t(nrhs);
     lu.rhs0 = int32_t(r0);
@@ -921,12 +929,14 @@ void apply_tc_adj(mbf_op_s* op, Workspace& w, const float2* u, float2* g, int64_
 }
 
 void apply_impl(mbf_op_s* op, const void* in, void* out, int64_t nrhs, int32_t precision, void* stream,
-                bool adj, int grid = 0, bool accumulate = false, Workspace* ws = nullptr, bool host_io = false) {
+                bool adj, int grid = 0, bool accumulate = false, Workspace* ws = nullptr, bool host_io = false,
+                const RowTable* rows = nullptr) {
   if (!op) fail(MBF_ERR_INVALID, "operator is NULL");
   Workspace& w = ws ? *ws : op->ws;
   if (nrhs < 0) fail(MBF_ERR_INVALID, "nrhs < 0");
   if (nrhs == 0) return;
-  if ((!in || !out)) fail(MBF_ERR_INVALID, "NULL vector");
+  if (rows && (adj || host_io || nrhs > kRowTab)) fail(MBF_ERR_INVALID, "row tables: forward device applies of <= 64 RHS");
+  if (!rows && (!in || !out)) fail(MBF_ERR_INVALID, "NULL vector");
   if (precision != MBF_PREC_AUTO && precision != MBF_PREC_FP32_SIMT && precision != MBF_PREC_BF16X3 &&
       precision != MBF_PREC_TF32)
     fail(MBF_ERR_INVALID, "precision not available");
@@ -940,7 +950,7 @@ void apply_impl(mbf_op_s* op, const void* in, void* out, int64_t nrhs, int32_t p
       return;
     }
     apply_tc(op, w, static_cast<const float2*>(in), static_cast<float2*>(out), nrhs, st, grid, accumulate, host_io,
-             precision == MBF_PREC_TF32);
+             precision == MBF_PREC_TF32, rows);
     return;
   }
   if (!op->simt_unavailable.empty()) fail(MBF_ERR_INVALID, "FP32 SIMT path unavailable: " + op->simt_unavailable);
@@ -968,6 +978,10 @@ void apply_impl(mbf_op_s* op, const void* in, void* out, int64_t nrhs, int32_t p
   a.accumulate = accumulate ? 1 : 0;
   a.wait_ns = op->dbg_wait_ns;
   a.stall_stage1 = op->dbg_stall_stage1;
+  if (rows) {
+    a.use_rows = 1;
+    a.rows = *rows;
+  }
   if (adj && op->n_w < op->n_in && !accumulate)
     cuda_check(cudaMemsetAsync(out, 0, size_t(nrhs) * size_t(op->n_in) * sizeof(float2), st), "cudaMemsetAsync");
   cudaEvent_t e0 = prof_begin(op, st);
@@ -1104,8 +1118,8 @@ void ws_release(mbf_op_s* op, Workspace* w) {
 }
 
 void apply_dev(mbf_op_s* op, const void* in, void* out, int64_t nrhs, int32_t precision, cudaStream_t st,
-               bool adj, int grid, bool accumulate, Workspace* ws) {
-  apply_impl(op, in, out, nrhs, precision, st, adj, grid, accumulate, ws);
+               bool adj, int grid, bool accumulate, Workspace* ws, const RowTable* rows) {
+  apply_impl(op, in, out, nrhs, precision, st, adj, grid, accumulate, ws, false, rows);
 }
 
 }  // namespace mbf

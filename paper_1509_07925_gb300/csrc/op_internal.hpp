@@ -15,11 +15,13 @@ struct mbf_factors_s {
 };
 
 namespace mbf {
+struct RowTable;   // apply.hpp
+
 // Scratch of one apply in flight: the SIMT kernel's coefficient vectors, grid-barrier
 // word and dependency counters, the status word its waits report to, and the tensor
 // path's vectors, counters and tree-ordered input panel (allocated on first tensor
-// use).  An operator owns one; the server owns one per (slot, operator), so that
-// batches of one operator can run at the same time.
+// use).  An operator owns one, and lends further ones from a pool it keeps to the
+// server, so that batches of one operator can run at the same time.
 struct Workspace {
   float2* bufs = nullptr;          // one coefficient vector per stage, 4 RHS wide
   unsigned* barrier = nullptr;     // barrier word, then (256 bytes on) the dependency counters
@@ -116,9 +118,10 @@ void ws_release(mbf_op_s* op, Workspace* w);
 int64_t tc_vec_bytes(const mbf_op_s* op);
 // Apply on the device; grid > 0 caps the persistent kernels' CTA count (an SM share);
 // accumulate adds the result into out (which the caller initialised).
-// ws: the workspace to use (nullptr: the operator's own).
+// ws: the workspace to use (nullptr: the operator's own).  rows: per-RHS input and
+// output rows instead of in / out (forward, device buffers, nrhs <= kRowTab).
 void apply_dev(mbf_op_s* op, const void* in, void* out, int64_t nrhs, int32_t precision, cudaStream_t st,
-               bool adj, int grid, bool accumulate = false, Workspace* ws = nullptr);
+               bool adj, int grid, bool accumulate = false, Workspace* ws = nullptr, const RowTable* rows = nullptr);
 // The error estimator of §3.3 (estimate.cpp); keeps the result in op->eps.
 double estimate_error(mbf_op_s* op, mbf_entry_fn fn, void* ctx, int32_t n_samples, uint64_t seed,
                       cudaStream_t st);

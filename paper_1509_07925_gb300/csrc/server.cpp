@@ -7,8 +7,9 @@
 // when requests back up and more operators are queued than slots are free, the oldest
 // requests on other operators add further groups the same way, up to max_batch_ops
 // operators of at most mix_work_pct percent of the first group's factor traffic.  A
-// group of one request runs in place; several are gathered
-// into a staging panel (device-to-device copies), applied once, and scattered back.
+// group's requests are applied at once in place: the kernels read and write the
+// requests' own rows through a table of row addresses (up to 64 RHS); a larger group
+// is gathered into a staging panel (device-to-device copies) and scattered back.
 // Each group borrows a workspace of its operator for the batch (the operator's own one
 // when free, else one of its pool, allocated once and kept by the operator), so batches
 // of one operator in different slots run at the same time.  With use_graphs the whole batch --
@@ -30,6 +31,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "apply.hpp"
 #include "op_internal.hpp"
 
 namespace {
@@ -115,6 +117,17 @@ struct mbf_server_s {
       mbf::apply_dev(op, gr.rq[0]->g, gr.rq[0]->u, gr.rq[0]->nrhs, MBF_PREC_AUTO, st, false, grid, false, gr.ws);
       return;
     }
+    if (!gr.stage) {   // up to kRowTab RHS: applied in place through a table of the requests' rows
+      mbf::RowTable rows{};
+      int64_t r0 = 0;
+      for (Request* r : gr.rq)
+        for (int64_t k = 0; k < r->nrhs; ++k, ++r0) {
+          rows.in[r0] = static_cast<const float2*>(r->g) + k * op->n_in;
+          rows.out[r0] = static_cast<float2*>(r->u) + k * op->n_out;
+        }
+      mbf::apply_dev(op, nullptr, nullptr, gr.rhs, MBF_PREC_AUTO, st, false, grid, false, gr.ws, &rows);
+      return;
+    }
     auto* in = static_cast<float2*>(gr.stage);
     float2* out = in + gr.rhs * op->n_in;
     int64_t r0 = 0;
@@ -189,7 +202,7 @@ struct mbf_server_s {
     for (Group& gr : b.groups) {
       // no allocation inside the capture: workspaces and staging first
       gr.ws = mbf::ws_acquire(gr.op, mbf::uses_tensor(gr.op, gr.rhs, MBF_PREC_AUTO, false));
-      if (gr.rq.size() > 1)
+      if (gr.rq.size() > 1 && gr.rhs > mbf::kRowTab)   // beyond a row table: through a staging panel
         cuda_ok(cudaMallocAsync(&gr.stage, size_t(gr.rhs * (gr.op->n_in + gr.op->n_out)) * sizeof(float2), st),
                 "staging allocation");
       key += "|" + std::to_string(gr.op->serial);

@@ -1,7 +1,7 @@
 // Autotuner for one operator (the paper has no counterpart): times the FP32 SIMT apply
-// over RHS counts and the tensor-core panel over A-ring depths on the device, keeps
-// the fastest ring depth and the RHS count from which MBF_PREC_AUTO switches to the
-// tensor cores.
+// over RHS counts and the tensor-core panel over (panel buffers, A-ring depth) on the
+// device, keeps the fastest configuration and the RHS count from which MBF_PREC_AUTO
+// switches to the tensor cores.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -74,33 +74,46 @@ extern "C" mbf_status mbf_op_tune(mbf_op_t op, void* stream, mbf_tune_result_t* 
     if (op->tc_unavailable.empty()) {
       int optin = 0;
       cuda_ok(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, op->device), "attr");
-      const int keep_nsa = op->tc_nsa;
+      const int keep_nsa = op->tc_nsa, keep_nxb = op->tc_nxb;
       const size_t keep_smem = op->tc_smem;
       double best = 1e30;
-      int best_nsa = keep_nsa;
+      int best_nsa = keep_nsa, best_nxb = keep_nxb;
       size_t best_smem = keep_smem;
-      for (int nsa = 2; nsa <= 16 && out->n_slots < 8; nsa += 2) {
-        const size_t sm = mbf::tc_smem_bytes(nsa, op->tc_nxb, op->tc_nsets, op->tc_mt_max, op->tc_kpad_max);
-        if (sm > size_t(optin)) break;
-        op->tc_nsa = nsa;
-        op->tc_smem = std::max(sm, size_t(optin) / 2 + 1024);
-        double ms = 0.0;
-        try {
-          ms = time_apply(op, g.p, u.p, kMaxRhs, MBF_PREC_BF16X3, st, ev, 3);
-        } catch (...) {
-          op->tc_nsa = keep_nsa;
-          op->tc_smem = keep_smem;
-          throw;
-        }
-        out->slots[out->n_slots] = nsa;
-        out->tc_ms[out->n_slots] = ms;
-        ++out->n_slots;
-        if (ms < best) {
-          best = ms;
-          best_nsa = nsa;
-          best_smem = op->tc_smem;
+      // panel buffers 2 and 3; for each, the deepest ring depths that fit first (at most
+      // 8 configurations in all: 5 with two buffers, 3 with three)
+      for (int nxb = 2; nxb <= 3; ++nxb) {
+        int deepest = 0;
+        for (int nsa = 2; nsa <= 16; nsa += 2)
+          if (mbf::tc_smem_bytes(nsa, nxb, op->tc_nsets, op->tc_mt_max, op->tc_kpad_max) <= size_t(optin)) deepest = nsa;
+        const int quota = nxb == 2 ? 5 : 3;
+        for (int nsa = std::max(2, deepest - 2 * (quota - 1)); nsa <= deepest && out->n_slots < 8; nsa += 2) {
+          op->tc_nsa = nsa;
+          op->tc_nxb = nxb;
+          op->tc_smem = std::max(mbf::tc_smem_bytes(nsa, nxb, op->tc_nsets, op->tc_mt_max, op->tc_kpad_max),
+                                 size_t(optin) / 2 + 1024);
+          double ms = 0.0;
+          try {
+            ms = time_apply(op, g.p, u.p, kMaxRhs, MBF_PREC_BF16X3, st, ev, 3);
+          } catch (...) {
+            op->tc_nsa = keep_nsa;
+            op->tc_nxb = keep_nxb;
+            op->tc_smem = keep_smem;
+            throw;
+          }
+          out->slots[out->n_slots] = nsa;
+          out->panel_buffers[out->n_slots] = nxb;
+          out->tc_ms[out->n_slots] = ms;
+          ++out->n_slots;
+          if (ms < best) {
+            best = ms;
+            best_nsa = nsa;
+            best_nxb = nxb;
+            best_smem = op->tc_smem;
+          }
         }
       }
+      op->tc_nxb = best_nxb;
+      out->tc_buffers_chosen = best_nxb;
       op->tc_nsa = best_nsa;
       op->tc_smem = best_smem;
       out->tc_slots_chosen = best_nsa;

@@ -156,18 +156,18 @@ def test_mixed_operators_in_one_graph_launch(bd, ops):
     alone_srv.close()
 
 
-def _queue_behind_blocker(bd, srv, ops, order, seed):
+def _queue_behind_blocker(bd, srv, ops, order, seed, nrhs=2):
     """Hold the server's only slot with a stalled blocker, queue requests on the
-    operators `order` (in that order, two RHS each) behind it, and wait for all."""
+    operators `order` (in that order, nrhs RHS each) behind it, and wait for all."""
     import time
     fs0, _ = oracle_case(*OPS[2])
     blocker = bd.Operator(import_factors(bd, fs0))
     blocker.debug_stall(1, 200_000_000)
-    reqs = [(k, complex_normal(ops[k][1].n_in, 2, seed=seed + i)) for i, k in enumerate(order)]
+    reqs = [(k, complex_normal(ops[k][1].n_in, nrhs, seed=seed + i)) for i, k in enumerate(order)]
     bufs = []
     for k, g in reqs:
         bufs.append((torch.from_numpy(g.astype(np.complex64)).cuda(),
-                     torch.empty((2, ops[k][1].n_out), dtype=torch.complex64, device="cuda")))
+                     torch.empty((nrhs, ops[k][1].n_out), dtype=torch.complex64, device="cuda")))
     gb = torch.zeros((1, fs0.n_in), dtype=torch.complex64, device="cuda")
     ub = torch.empty((1, fs0.n_out), dtype=torch.complex64, device="cuda")
     torch.cuda.synchronize()
@@ -175,7 +175,7 @@ def _queue_behind_blocker(bd, srv, ops, order, seed):
     t0 = time.time()
     while srv.poll(tb).state != bd.MBF_REQ_RUNNING:
         assert time.time() - t0 < 10.0
-    tickets = [srv.submit(ops[k][0], gt.data_ptr(), ut.data_ptr(), 2) for (k, _), (gt, ut) in zip(reqs, bufs)]
+    tickets = [srv.submit(ops[k][0], gt.data_ptr(), ut.data_ptr(), nrhs) for (k, _), (gt, ut) in zip(reqs, bufs)]
     sts = _wait(bd, srv, tickets)
     _wait(bd, srv, [tb])
     blocker.close()
@@ -209,6 +209,17 @@ def test_batch_policy_work_ratio_and_backlog(bd, ops):
     stats = srv.stats()
     srv.close()
     assert stats.mixed_batches == 0
+
+
+def test_groups_in_place_and_through_staging(bd, ops):
+    """A group of up to 64 RHS is applied in place through a table of the requests' rows;
+    a larger one (max_batch_rhs 128: three requests of 30 RHS) through a staging panel.
+    Both equal the oracle request by request."""
+    for nrhs, rhs_total in ((20, 60), (30, 90)):
+        srv = bd.Server(max_inflight=1, max_batch_rhs=128)
+        sts = _queue_behind_blocker(bd, srv, ops, [3, 3, 3], seed=400 + nrhs, nrhs=nrhs)
+        srv.close()
+        assert all(st.batch_requests == 3 and st.batch_rhs == rhs_total for st in sts)
 
 
 def test_batches_of_one_operator_overlap(bd, ops):
@@ -289,7 +300,9 @@ def test_tuner_choices_keep_results(bd, ops):
     st = torch.cuda.current_stream().cuda_stream
     r = op.tune(st)
     assert r.n_simt == 7 and all(r.simt_ms[i] > 0 for i in range(r.n_simt))
-    assert r.n_slots >= 1 and r.tc_slots_chosen in list(r.slots)[:r.n_slots]
+    assert r.n_slots >= 1
+    tried = list(zip(list(r.slots)[:r.n_slots], list(r.panel_buffers)[:r.n_slots]))
+    assert all(b in (2, 3) for _, b in tried) and (r.tc_slots_chosen, r.tc_buffers_chosen) in tried
     assert 1 <= r.tc_min_rhs <= 65
     # SIMT time grows with the RHS count; one tensor panel covers up to 64 RHS
     assert r.simt_ms[r.n_simt - 1] > r.simt_ms[0]
