@@ -95,11 +95,6 @@ __device__ __forceinline__ void cp_async_wait_all() {
 __device__ __forceinline__ void l2_discard(const void* p) {
   asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
 }
-// Programmatic dependent launch: let the next kernel on the stream be scheduled (its
-// prologue overlaps this kernel's tail) / wait until the previous kernel has finished
-// and its writes are visible.  Both are no-ops without the launch attribute.
-__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -248,7 +243,6 @@ constexpr int kTcChunk = 16;   // accumulator columns per epilogue step
 template <bool TF32>
 __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_constant__ TCArgs a) {
   using namespace tc;
-  pdl_launch_dependents();   // the U^L kernel may be scheduled once every CTA of this one runs
   extern __shared__ __align__(1024) uint8_t smem[];
   const int nsa = a.nsa, nxb = a.nxb, nsets = a.nsets;
   const uint32_t a_slot = 4u * uint32_t(a.mt_max) * 32u;       // one K16 chunk of a tile (4 planes)
@@ -348,9 +342,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
     // one run per block), all completing on the buffer's xfull barrier: a thread issues
     // one bulk copy every few hundred ns, so the copies go out from separate lanes.  The
     // consumed blocks are dropped from L2 later, by the discard warps, once the group's
-    // MMAs are done.  The stage-0 inputs come from the (V^L)^* kernel, which may still be
-    // running when this one starts (programmatic launch): wait for it first.
-    pdl_wait();
+    // MMAs are done.
     int j = 0;
     bool ok = true;
     for (int e = 0; e < S && ok; ++e) {
@@ -412,7 +404,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) bf_apply_tc(const __grid_consta
     // Once a group's MMAs are done (its panel buffer's xempty phase), its c input blocks
     // are neither in shared memory nor read again: their lines are dropped from L2
     // without a write-back.  Each discard takes a while, so two warps share them.
-    pdl_wait();   // (the stage-0 blocks are the previous kernel's output)
     const int dt = (warp == 3 ? 0 : 32) + lane;
     int j = 0;
     bool ok = true;
@@ -815,7 +806,6 @@ __device__ __forceinline__ void leaf_v_point(float2 (&acc)[8], const float2* vro
 // entry = point of the group, U itself), read transposed and conjugated.
 template <bool TF32, bool XPOSE>
 __global__ void __launch_bounds__(kTcNR * kLeafMaxR8 / 8) leaf_v_kernel(const __grid_constant__ LeafArgs a) {
-  tc::pdl_launch_dependents();   // the tensor kernel may be scheduled (its tile stream needs nothing from here)
   using tc::sa;
   using tc::cp_async16;
   using tc::cp_async_wait_all;
@@ -928,7 +918,6 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_u_kernel(const __grid_const
   if (tid <= c) lend[tid] = a.off[c * g + tid] - pg;
   const Item it = a.items[a.item_base + int64_t(g) * a.item_stride];
   const uint8_t* ibase = a.arena + size_t(it.off128) * 128;
-  tc::pdl_wait();   // the rows are the tensor kernel's output (programmatic launch)
   float* ws = reinterpret_cast<float*>(lsm);                        // [nl R][2 NR]
   float2* us = reinterpret_cast<float2*>(ws + size_t(nl) * R * 2 * NR);   // [R][kLeafPts]
   const float* rows_g = a.wl + (int64_t(c) * g + t0) * R * 2 * NR;     // the CTA's leaves' rows
@@ -1046,7 +1035,7 @@ bool leaf_fits(int R8, int c) { return R8 <= kLeafMaxR8 && c <= kLeafMaxC; }
 cudaError_t launch_apply_tc(const TCArgs& a, int grid, size_t smem, cudaStream_t stream, bool tf32) {
   if (a.nsa < kAProducers || a.nsa % kAProducers != 0) return cudaErrorInvalidValue;
   if (a.nxb < 1 || a.nxb > kMaxXBufs) return cudaErrorInvalidValue;
-  cudaError_t err = cudaSuccess;
+  cudaError_t err = cudaSuccess;   // (the caller clears the dependency counters)
   void (*kern)(TCArgs) = tf32 ? bf_apply_tc<true> : bf_apply_tc<false>;
   if ((err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem))) != cudaSuccess)
     return err;
@@ -1055,20 +1044,12 @@ cudaError_t launch_apply_tc(const TCArgs& a, int grid, size_t smem, cudaStream_t
   cfg.blockDim = dim3(kTcThreads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = stream;
-  cudaLaunchAttribute attr[2];
+  cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;
-  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 2;
-  err = cudaLaunchKernelEx(&cfg, kern, a);
-  if (err == cudaErrorInvalidValue || err == cudaErrorNotSupported) {   // no programmatic launch here
-    cudaGetLastError();
-    cfg.numAttrs = 1;
-    err = cudaLaunchKernelEx(&cfg, kern, a);
-  }
-  return err;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
 // TF32 tiles from the split-BF16 tiles: T = hi + lo (FP32), rounded to TF32, in the
@@ -1166,29 +1147,8 @@ cudaError_t launch_leaf(const LeafArgs& a, bool u_side, int n_groups, cudaStream
   if (blocks <= 0) return cudaSuccess;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (err != cudaSuccess) return err;
-  if (!u_side) {
-    kern<<<unsigned(blocks), threads, smem, stream>>>(a);
-    return cudaGetLastError();
-  }
-  // U^L follows the tensor kernel: programmatic launch (it waits for that kernel's
-  // output in the kernel itself)
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(unsigned(blocks));
-  cfg.blockDim = dim3(unsigned(threads));
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = stream;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  err = cudaLaunchKernelEx(&cfg, kern, a);
-  if (err == cudaErrorInvalidValue || err == cudaErrorNotSupported) {
-    cudaGetLastError();
-    cfg.numAttrs = 0;
-    err = cudaLaunchKernelEx(&cfg, kern, a);
-  }
-  return err;
+  kern<<<unsigned(blocks), threads, smem, stream>>>(a);
+  return cudaGetLastError();
 }
 
 }  // namespace mbf

@@ -728,8 +728,7 @@ void apply_tc(mbf_op_s* op, Workspace& w, const float2* g, float2* u, int64_t nr
   uint8_t* bufs = yl + vec_bytes;                    // main stage e < S - 1 writes bufs + e * vec_bytes
   float* ylast = reinterpret_cast<float*>(yl + int64_t(S) * vec_bytes);   // last main stage
   for (int64_t r0 = 0; r0 < nrhs; r0 += kTcNR) {
-    // the tensor kernel's dependency counters, cleared before the leaf kernel so that
-    // nothing but kernels lies between the leaf and tensor launches (programmatic launch)
+    // the tensor kernel's dependency counters (cleared per panel)
     cuda_check(cudaMemsetAsync(w.tc_counters, 0, tc_counter_bytes(tp), st), "counter clear");
     // page-locked host input: g -> panel in tree order first (rows read across the
     // host link as 16-byte runs); device input: gathered by the leaf kernel itself
@@ -853,8 +852,7 @@ void apply_tc_adj(mbf_op_s* op, Workspace& w, const float2* u, float2* g, int64_
   uint8_t* bufs = yl + vec_bytes;
   float* ylast = reinterpret_cast<float*>(yl + int64_t(S) * vec_bytes);
   for (int64_t r0 = 0; r0 < nrhs; r0 += kTcNR) {
-    // the tensor kernel's dependency counters, cleared before the leaf kernel so that
-    // nothing but kernels lies between the leaf and tensor launches (programmatic launch)
+    // the tensor kernel's dependency counters (cleared per panel)
     cuda_check(cudaMemsetAsync(w.tc_counters, 0, tc_counter_bytes(ap), st), "counter clear");
     // u -> panel in X-tree order (page-locked host input), or gathered by the leaf kernel
     cudaEvent_t e0 = nullptr;
