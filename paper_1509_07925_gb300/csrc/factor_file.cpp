@@ -363,7 +363,7 @@ FactorSet build_or_load(const mbf_problem_t& prob, mbf_entry_fn fn, void* ctx, c
     if (fs.w_perm != wt.perm || fs.w_off != wt.off) fail(MBF_ERR_INVALID, who + "Omega tree or point set");
     for (int l = fs.L / 2; l <= fs.L; ++l)
       if (fs.RU[size_t(l)] > prob.r || fs.RV[size_t(l)] > prob.r) fail(MBF_ERR_INVALID, who + "ranks above r");
-    // and the kernel: the recorded entries against the entry function of this build
+    // and the kernel: the recorded entries against the entry function of the problem being built
     const std::vector<KernelEntry> rec = load_kernel_record(std::string(path) + ".kernel");
     const std::vector<KernelEntry> now = kernel_entries(prob, fs, fn, ctx);
     bool same = rec.size() == now.size();
