@@ -450,6 +450,14 @@ typedef struct mbf_server_stats {
   int32_t reserved_stats;
 } mbf_server_stats_t;
 mbf_status mbf_server_create(const mbf_server_opts_t* opts, mbf_server_t* out);
+/* The worker's batch rule as a pure host function (for tests of the policy): for n
+ * queued requests, oldest first, on operators ops[i] in [0, n_ops) with nrhs[i] RHS,
+ * a group's factor traffic taken as op_work[op] * its RHS count, and free_slots free
+ * slots, writes the group of the next batch each request joins (-1: stays queued) to
+ * group_of[i].  opts as for mbf_server_create (NULL: defaults).  Needs no device. */
+mbf_status mbf_debug_form_batch(const int32_t* ops, const int64_t* nrhs, int64_t n, const double* op_work,
+                                int32_t n_ops, int32_t free_slots, const mbf_server_opts_t* opts,
+                                int32_t* group_of);
 mbf_status mbf_submit(mbf_server_t s, mbf_op_t op, const void* g, void* u, int64_t nrhs,
                       mbf_ticket_t* ticket);
 mbf_status mbf_poll(mbf_server_t s, mbf_ticket_t ticket, mbf_request_status_t* status);

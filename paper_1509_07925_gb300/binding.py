@@ -155,6 +155,8 @@ SIGNATURES = {
     "mbf_msbf_part": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p)]),
     "mbf_msbf_destroy": (C.c_int, [C.c_void_p]),
     "mbf_server_create": (C.c_int, [C.POINTER(ServerOpts), C.POINTER(C.c_void_p)]),
+    "mbf_debug_form_batch": (C.c_int, [C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.c_int64, C.POINTER(C.c_double),
+                                       C.c_int32, C.c_int32, C.POINTER(ServerOpts), C.POINTER(C.c_int32)]),
     "mbf_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                              C.POINTER(C.c_int64)]),
     "mbf_poll": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(RequestStatus)]),
@@ -442,6 +444,21 @@ class Operator:
             self.close()
         except Exception:
             pass
+
+
+def form_batch(ops, nrhs, op_work, free_slots=1, **opts):
+    """The server's batch rule (mbf_debug_form_batch) on a queue of requests on operators
+    ops[i] with nrhs[i] RHS, oldest first: the group of the next batch each request joins
+    (-1: stays queued).  op_work[k]: factor traffic of operator k per RHS."""
+    n = len(ops)
+    o = ServerOpts(opts.get("staging_budget_bytes", 0), opts.get("max_inflight", 0), opts.get("max_batch_rhs", 0),
+                   opts.get("max_queue", 0), 1, opts.get("max_batch_ops", 0), opts.get("mix_work_pct", 0))
+    a_ops = (C.c_int32 * max(n, 1))(*ops)
+    a_rhs = (C.c_int64 * max(n, 1))(*nrhs)
+    a_w = (C.c_double * max(len(op_work), 1))(*op_work)
+    out = (C.c_int32 * max(n, 1))()
+    _check(lib().mbf_debug_form_batch(a_ops, a_rhs, n, a_w, len(op_work), free_slots, C.byref(o), out))
+    return list(out)[:n]
 
 
 class Server:

@@ -23,6 +23,7 @@
 #include <chrono>
 #include <condition_variable>
 #include <deque>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <set>
@@ -74,6 +75,74 @@ struct GraphEntry {
   cudaGraphExec_t exec = nullptr;
   uint64_t last_use = 0;
 };
+
+// The server options with the defaults of their zero fields applied; invalid ones fail.
+mbf_server_opts_t with_defaults(const mbf_server_opts_t* in) {
+  mbf_server_opts_t o{};
+  if (in) o = *in;
+  if (o.staging_budget_bytes <= 0) o.staging_budget_bytes = int64_t(1) << 30;
+  if (o.max_inflight <= 0) o.max_inflight = 4;
+  if (o.max_inflight > 16) fail(MBF_ERR_INVALID, "max_inflight > 16");
+  if (o.max_batch_rhs <= 0) o.max_batch_rhs = 64;
+  if (o.max_queue <= 0) o.max_queue = 4096;
+  if (o.max_batch_ops <= 0) o.max_batch_ops = 4;
+  if (o.max_batch_ops > kMaxGroups) fail(MBF_ERR_INVALID, "max_batch_ops > 8");
+  if (o.mix_work_pct < 0) fail(MBF_ERR_INVALID, "mix_work_pct < 0");
+  if (o.mix_work_pct == 0) o.mix_work_pct = 25;
+  return o;
+}
+
+// One queued request as the batch rule sees it: its operator (an index) and RHS count.
+struct QueuedReq {
+  int32_t op;
+  int64_t nrhs;
+};
+
+// The batch rule: which queued requests (oldest first) form the next batch on a slot
+// while `free_slots` slots are free.  groups[k] lists the queue positions of group k's
+// requests in FIFO order.  One operator per batch unless requests back up (more queued
+// than max_inflight * max_batch_ops) and the free slots cannot take every queued
+// operator on its own; then the queued operators are spread over the free slots, up to
+// max_batch_ops per batch.  The oldest request on an operator not yet in (or passed over
+// for) the batch opens a group, and that operator's queued requests join it while they
+// fit max_batch_rhs; a further group joins only if its factor traffic work(op, rhs) is at
+// most mix_work_pct percent of the first group's (the batch ends with its longest group).
+std::vector<std::vector<size_t>> form_batch(const std::vector<QueuedReq>& q, int free_slots,
+                                            const mbf_server_opts_t& o,
+                                            const std::function<double(int32_t, int64_t)>& work) {
+  std::vector<std::vector<size_t>> groups;
+  if (q.empty()) return groups;
+  std::set<int32_t> qops;
+  for (const QueuedReq& r : q) qops.insert(r.op);
+  const bool backlog = int64_t(q.size()) > int64_t(o.max_inflight) * o.max_batch_ops;
+  const int want = backlog ? (int(qops.size()) + free_slots - 1) / std::max(1, free_slots) : 1;
+  const int max_ops = std::min({kMaxGroups, std::max(1, o.max_batch_ops), std::max(1, want)});
+  std::set<int32_t> in_batch, passed;
+  double work0 = 0;
+  while (int(groups.size()) < max_ops) {
+    size_t qo = 0;
+    while (qo < q.size() && (in_batch.count(q[qo].op) || passed.count(q[qo].op))) ++qo;
+    if (qo == q.size()) break;
+    const int32_t op = q[qo].op;
+    std::vector<size_t> take;
+    int64_t rhs = 0;
+    for (size_t i = qo; i < q.size(); ++i)
+      if (q[i].op == op && (take.empty() || rhs + q[i].nrhs <= o.max_batch_rhs)) {
+        take.push_back(i);
+        rhs += q[i].nrhs;
+      }
+    const double wk = work(op, rhs);
+    if (groups.empty()) {
+      work0 = wk;
+    } else if (wk * 100.0 > double(o.mix_work_pct) * work0) {
+      passed.insert(op);
+      continue;
+    }
+    in_batch.insert(op);
+    groups.push_back(std::move(take));
+  }
+  return groups;
+}
 
 }  // namespace
 
@@ -150,11 +219,10 @@ struct mbf_server_s {
   // Factor bytes a group streams: the operator's factors once per pass (a 64-RHS panel
   // on the tensor cores, up to 4 RHS on the SIMT kernel).  The apply is bound by this
   // traffic, so it sets the group's share of the batch's SMs.
-  static double group_work(const Group& gr) {
-    const mbf_op_s* op = gr.op;
-    if (mbf::uses_tensor(op, gr.rhs, MBF_PREC_AUTO, false))
-      return double(std::max<int64_t>(op->tc_bytes, 1)) * double((gr.rhs + 63) / 64);
-    return 8.0 * double(std::max<int64_t>(op->nnz, 1)) * double((gr.rhs + 3) / 4);
+  static double group_work(const mbf_op_s* op, int64_t rhs) {
+    if (mbf::uses_tensor(op, rhs, MBF_PREC_AUTO, false))
+      return double(std::max<int64_t>(op->tc_bytes, 1)) * double((rhs + 63) / 64);
+    return 8.0 * double(std::max<int64_t>(op->nnz, 1)) * double((rhs + 3) / 4);
   }
 
   // SMs of each group: the batch's share (grid, or the whole GPU when 0) split in
@@ -166,7 +234,7 @@ struct mbf_server_s {
     const int share = grid > 0 ? grid : sms;
     std::vector<double> w(ng);
     double sum = 0;
-    for (size_t k = 0; k < ng; ++k) sum += (w[k] = group_work(b.groups[k]));
+    for (size_t k = 0; k < ng; ++k) sum += (w[k] = group_work(b.groups[k].op, b.groups[k].rhs));
     std::vector<int> g(ng);
     int used = 0;
     size_t big = 0;
@@ -331,57 +399,44 @@ struct mbf_server_s {
         if (!slots[i].groups.empty() || queue.empty()) continue;
         Batch& b = slots[i];
         b.slot = int(i);
-        // operators per batch: one unless requests back up (more queued than the slots
-        // take as batches of max_batch_ops requests each) and the free slots cannot take
-        // every queued operator on its own; then the queued operators are spread over the
-        // free slots, up to max_batch_ops per batch.  Below that backlog a request of a
-        // small operator is not held back by a larger operator's group.
         int free_slots = 0;
         for (const auto& x : slots) free_slots += x.groups.empty();
-        std::set<mbf_op_s*> qops;
-        for (mbf_ticket_t id : queue) qops.insert(reqs[id].op);
-        const bool backlog = int64_t(queue.size()) > int64_t(opts.max_inflight) * opts.max_batch_ops;
-        const int want = backlog ? (int(qops.size()) + free_slots - 1) / std::max(1, free_slots) : 1;
-        const int max_ops = std::min({kMaxGroups, std::max(1, opts.max_batch_ops), std::max(1, want)});
+        // the batch rule on the queue, operators numbered in order of appearance
+        std::vector<QueuedReq> qv;
+        std::vector<mbf_op_s*> opv;
+        std::unordered_map<mbf_op_s*, int32_t> opi;
+        qv.reserve(queue.size());
+        for (mbf_ticket_t id : queue) {
+          mbf_op_s* op = reqs[id].op;
+          auto it = opi.find(op);
+          const int32_t k = it != opi.end() ? it->second : int32_t(opv.size());
+          if (it == opi.end()) {
+            opi.emplace(op, k);
+            opv.push_back(op);
+          }
+          qv.push_back({k, reqs[id].nrhs});
+        }
+        const auto gl = form_batch(qv, free_slots, opts,
+                                   [&](int32_t k, int64_t rhs) { return group_work(opv[size_t(k)], rhs); });
         int64_t nreq = 0, nrhs_all = 0;
-        std::set<mbf_op_s*> passed;   // operators left out of this batch by the work ratio
-        double work0 = 0;
-        while (int(b.groups.size()) < max_ops) {
-          // the oldest queued request on an operator not yet in (or passed over for) the
-          // batch opens a group (a batch holds one group per operator: they share the
-          // slot's workspace for it); that operator's queued requests join it
-          auto qo = queue.begin();
-          while (qo != queue.end() && (passed.count(reqs[*qo].op) ||
-                                       std::any_of(b.groups.begin(), b.groups.end(),
-                                                   [&](const Group& x) { return x.op == reqs[*qo].op; })))
-            ++qo;
-          if (qo == queue.end()) break;
+        std::vector<size_t> taken;
+        for (const auto& gpos : gl) {
           Group gr;
-          gr.op = reqs[*qo].op;
-          std::vector<size_t> take;   // queue positions of the group's requests
-          for (auto it = qo; it != queue.end(); ++it) {
-            Request& r = reqs[*it];
-            if (r.op == gr.op && (gr.rq.empty() || gr.rhs + r.nrhs <= opts.max_batch_rhs)) {
-              gr.ids.push_back(*it);
-              gr.rq.push_back(&r);
-              gr.rhs += r.nrhs;
-              take.push_back(size_t(it - queue.begin()));
-            }
+          gr.op = opv[size_t(qv[gpos[0]].op)];
+          for (size_t pos : gpos) {
+            const mbf_ticket_t id = queue[pos];
+            Request& r = reqs[id];
+            gr.ids.push_back(id);
+            gr.rq.push_back(&r);
+            gr.rhs += r.nrhs;
+            taken.push_back(pos);
           }
-          // a further operator joins only if its factor traffic is at most mix_work_pct
-          // percent of the first group's: the batch ends with its longest group
-          const double wk = group_work(gr);
-          if (b.groups.empty()) {
-            work0 = wk;
-          } else if (wk * 100.0 > double(opts.mix_work_pct) * work0) {
-            passed.insert(gr.op);
-            continue;
-          }
-          for (auto t = take.rbegin(); t != take.rend(); ++t) queue.erase(queue.begin() + std::ptrdiff_t(*t));
           nreq += int64_t(gr.rq.size());
           nrhs_all += gr.rhs;
           b.groups.push_back(std::move(gr));
         }
+        std::sort(taken.begin(), taken.end());
+        for (auto t = taken.rbegin(); t != taken.rend(); ++t) queue.erase(queue.begin() + std::ptrdiff_t(*t));
         const double t = now();
         for (Group& gr : b.groups)
           for (Request* r : gr.rq) {
@@ -496,16 +551,7 @@ mbf_status mbf_server_create(const mbf_server_opts_t* opts, mbf_server_t* out) {
     if (!out) fail(MBF_ERR_INVALID, "NULL argument");
     auto* s = new mbf_server_s();
     try {
-      if (opts) s->opts = *opts;
-      if (s->opts.staging_budget_bytes <= 0) s->opts.staging_budget_bytes = int64_t(1) << 30;
-      if (s->opts.max_inflight <= 0) s->opts.max_inflight = 4;
-      if (s->opts.max_inflight > 16) fail(MBF_ERR_INVALID, "max_inflight > 16");
-      if (s->opts.max_batch_rhs <= 0) s->opts.max_batch_rhs = 64;
-      if (s->opts.max_queue <= 0) s->opts.max_queue = 4096;
-      if (s->opts.max_batch_ops <= 0) s->opts.max_batch_ops = 4;
-      if (s->opts.max_batch_ops > kMaxGroups) fail(MBF_ERR_INVALID, "max_batch_ops > 8");
-      if (s->opts.mix_work_pct < 0) fail(MBF_ERR_INVALID, "mix_work_pct < 0");
-      if (s->opts.mix_work_pct == 0) s->opts.mix_work_pct = 25;
+      s->opts = with_defaults(opts);
       cuda_ok(cudaGetDevice(&s->device), "cudaGetDevice");
       cuda_ok(cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device), "attr");
       s->t0 = std::chrono::steady_clock::now();
@@ -603,6 +649,27 @@ mbf_status mbf_server_stats(mbf_server_t s, mbf_server_stats_t* out) {
 
 mbf_status mbf_server_destroy(mbf_server_t s) {
   return sguard([&] { server_free(s); });
+}
+
+mbf_status mbf_debug_form_batch(const int32_t* ops, const int64_t* nrhs, int64_t n, const double* op_work,
+                                int32_t n_ops, int32_t free_slots, const mbf_server_opts_t* opts,
+                                int32_t* group_of) {
+  return sguard([&] {
+    if (n < 0 || n_ops < 0 || (n > 0 && (!ops || !nrhs || !group_of)) || (n_ops > 0 && !op_work))
+      fail(MBF_ERR_INVALID, "NULL argument or negative count");
+    if (free_slots < 1) fail(MBF_ERR_INVALID, "free_slots < 1");
+    const mbf_server_opts_t o = with_defaults(opts);
+    std::vector<QueuedReq> q(static_cast<size_t>(n));
+    for (int64_t i = 0; i < n; ++i) {
+      if (ops[i] < 0 || ops[i] >= n_ops) fail(MBF_ERR_INVALID, "operator index out of range");
+      if (nrhs[i] <= 0) fail(MBF_ERR_INVALID, "nrhs <= 0");
+      q[size_t(i)] = {ops[i], nrhs[i]};
+    }
+    const auto gl = form_batch(q, free_slots, o, [&](int32_t k, int64_t rhs) { return op_work[k] * double(rhs); });
+    for (int64_t i = 0; i < n; ++i) group_of[i] = -1;
+    for (size_t k = 0; k < gl.size(); ++k)
+      for (size_t pos : gl[k]) group_of[pos] = int32_t(k);
+  });
 }
 
 }  // extern "C"
