@@ -268,6 +268,18 @@ mbf_status mbf_apply_adjoint(mbf_op_t op, const void* u, void* g, int64_t nrhs,
  * (allocated on first use, kept by the operator). */
 mbf_status mbf_apply_host(mbf_op_t op, const void* g_host, void* u_host, int64_t nrhs,
                           int32_t precision, void* stream);
+/* u_b = K_f g_b for nbatch independent panels of nrhs vectors each, host buffers:
+ * g_host [nbatch][nrhs][n_in] and u_host [nbatch][nrhs][n_out] complex64 (every panel
+ * of u fully overwritten).  The panels are pipelined through two device staging pairs:
+ * the copy engines bring panel b+1 in and take panel b-1 out while panel b is applied
+ * on `stream`, so with page-locked buffers (cudaHostAlloc, cudaHostRegister) the
+ * transfers overlap the apply (pageable buffers give the same result, serialised).
+ * The staging pairs and the two copy streams are allocated on first use and kept by
+ * the operator.  Synchronizes before returning, also after an error.  nbatch = 0 or
+ * nrhs = 0 does nothing; MBF_ERR_INVALID for NULL buffers or negative counts.  Calls
+ * on one operator must not overlap (they share its workspace and staging). */
+mbf_status mbf_apply_host_batch(mbf_op_t op, const void* g_host, void* u_host, int64_t nbatch, int64_t nrhs,
+                                int32_t precision, void* stream);
 /* Allocation-free forward apply (FP32 SIMT kernel; MBF_ERR_INVALID on an operator it
  * cannot apply, see MBF_PREC_FP32_SIMT).  The paper has no counterpart: this is a service
  * for callers that may not allocate device memory when they apply an operator --

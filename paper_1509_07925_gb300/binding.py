@@ -139,6 +139,8 @@ SIGNATURES = {
                                     C.c_void_p]),
     "mbf_apply_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32,
                                  C.c_void_p]),
+    "mbf_apply_host_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int32,
+                                       C.c_void_p]),
     "mbf_op_check": (C.c_int, [C.c_void_p, C.c_void_p]),
     "mbf_op_debug_stall": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64]),
     "mbf_debug_fail_alloc": (C.c_int, [C.c_int64]),
@@ -411,6 +413,39 @@ class Operator:
         _check(lib().mbf_apply_host(self._h, g.ctypes.data_as(C.c_void_p),
                                     u.ctypes.data_as(C.c_void_p), nrhs, precision, C.c_void_p(stream)))
         return u
+
+    def apply_host_batch(self, g, nrhs: int, precision=MBF_PREC_AUTO, stream: int = 0, out=None):
+        """Host complex64 [nbatch][nrhs][n_in] -> host [nbatch][nrhs][n_out]: the panels
+        pipelined through the device (copy engines overlapping the applies).  g and out
+        may be numpy arrays or CPU torch tensors (page-locked ones overlap)."""
+        inf = self.info()
+        if hasattr(g, "data_ptr"):
+            if str(g.dtype) != "torch.complex64" or not g.is_contiguous() or g.device.type != "cpu":
+                raise ValueError("g must be a contiguous complex64 CPU tensor")
+            nb = g.numel() // max(1, nrhs * inf.n_in)
+            gp = g.data_ptr()
+        else:
+            g = np.ascontiguousarray(g, dtype=np.complex64)
+            nb = g.size // max(1, nrhs * inf.n_in)
+            gp = g.ctypes.data
+        if nb * nrhs * inf.n_in != (g.numel() if hasattr(g, "numel") else g.size):
+            raise ValueError("g is not nbatch x nrhs x n_in")
+        if out is None:
+            out = np.empty((nb, nrhs, inf.n_out), dtype=np.complex64)
+        if hasattr(out, "data_ptr"):
+            if str(out.dtype) != "torch.complex64" or not out.is_contiguous() or out.device.type != "cpu":
+                raise ValueError("out must be a contiguous complex64 CPU tensor")
+            up = out.data_ptr()
+        else:
+            if out.dtype != np.complex64 or not out.flags["C_CONTIGUOUS"]:
+                raise ValueError("out must be a C-contiguous complex64 array")
+            up = out.ctypes.data
+        osz = out.numel() if hasattr(out, "numel") else out.size
+        if osz != nb * nrhs * inf.n_out:
+            raise ValueError("out is not nbatch x nrhs x n_out")
+        _check(lib().mbf_apply_host_batch(self._h, C.c_void_p(gp), C.c_void_p(up), nb, nrhs, precision,
+                                          C.c_void_p(stream)))
+        return out
 
     def set_profiling(self, enable: bool = True):
         _check(lib().mbf_op_set_profiling(self._h, 1 if enable else 0))

@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -497,6 +498,13 @@ void op_free(mbf_op_s* op) {
   ws_free(op->ws);
   cudaFree(op->d_stage_in);
   cudaFree(op->d_stage_out);
+  for (int b = 0; b < 2; ++b) {
+    cudaFree(op->d_pipe_in[b]);
+    cudaFree(op->d_pipe_out[b]);
+    if (op->pipe_st[b]) cudaStreamDestroy(op->pipe_st[b]);
+    for (auto& ev : op->pipe_ev)
+      if (ev[b]) cudaEventDestroy(ev[b]);
+  }
   cudaFree(op->d_tc_arena);
   cudaFree(op->d_tc_arena_tf32);
   cudaFree(op->d_tc_arena_adj);
@@ -1352,6 +1360,75 @@ mbf_status mbf_apply_host(mbf_op_t op, const void* g_host, void* u_host, int64_t
     cuda_check(cudaMemcpyAsync(op->d_stage_in, g_host, in_b, cudaMemcpyHostToDevice, st), "H2D");
     apply_impl(op, op->d_stage_in, op->d_stage_out, nrhs, precision, stream, false);
     cuda_check(cudaMemcpyAsync(u_host, op->d_stage_out, out_b, cudaMemcpyDeviceToHost, st), "D2H");
+    cuda_check(cudaStreamSynchronize(st), "sync");
+  });
+}
+
+mbf_status mbf_apply_host_batch(mbf_op_t op, const void* g_host, void* u_host, int64_t nbatch, int64_t nrhs,
+                                int32_t precision, void* stream) {
+  return guard([&] {
+    if (!op) fail(MBF_ERR_INVALID, "operator is NULL");
+    if (nbatch < 0 || nrhs < 0) fail(MBF_ERR_INVALID, "negative count");
+    if (nbatch == 0 || nrhs == 0) return;
+    if (!g_host || !u_host) fail(MBF_ERR_INVALID, "NULL argument");
+    if (nrhs > (int64_t(1) << 24)) fail(MBF_ERR_INVALID, "nrhs too large");
+    const size_t in_b = size_t(nrhs) * size_t(op->n_in) * sizeof(float2);
+    const size_t out_b = size_t(nrhs) * size_t(op->n_out) * sizeof(float2);
+    if (size_t(nbatch) > SIZE_MAX / std::max<size_t>(std::max(in_b, out_b), 1))
+      fail(MBF_ERR_INVALID, "nbatch x panel bytes overflows");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // staging pairs (re)allocated when a larger panel comes; the previous call has
+    // synchronized, so none is in use
+    if (in_b > op->pipe_in_bytes || out_b > op->pipe_out_bytes) {
+      op->pipe_in_bytes = op->pipe_out_bytes = 0;
+      for (int b = 0; b < 2; ++b) {
+        cudaFree(op->d_pipe_in[b]);
+        cudaFree(op->d_pipe_out[b]);
+        op->d_pipe_in[b] = op->d_pipe_out[b] = nullptr;
+      }
+      for (int b = 0; b < 2; ++b)
+        if (dev_alloc(&op->d_pipe_in[b], in_b) != cudaSuccess || dev_alloc(&op->d_pipe_out[b], out_b) != cudaSuccess)
+          fail(MBF_ERR_OOM, "cudaMalloc pipeline staging");
+      op->pipe_in_bytes = in_b;
+      op->pipe_out_bytes = out_b;
+    }
+    for (int b = 0; b < 2; ++b) {
+      if (!op->pipe_st[b]) cuda_check(cudaStreamCreateWithFlags(&op->pipe_st[b], cudaStreamNonBlocking), "stream");
+      for (auto& ev : op->pipe_ev)
+        if (!ev[b]) cuda_check(cudaEventCreateWithFlags(&ev[b], cudaEventDisableTiming), "event");
+    }
+    cudaStream_t c_in = op->pipe_st[0], c_out = op->pipe_st[1];
+    cudaEvent_t* copied_in = op->pipe_ev[0];
+    cudaEvent_t* applied = op->pipe_ev[1];
+    cudaEvent_t* copied_out = op->pipe_ev[2];
+    const char* gi = static_cast<const char*>(g_host);
+    char* uo = static_cast<char*>(u_host);
+    try {
+      // panel i uses pair b = i mod 2: its input copy waits until apply i-2 has read the
+      // pair's input, its apply until the output of panel i-2 has left the pair
+      for (int64_t i = 0; i < nbatch; ++i) {
+        const int b = int(i & 1);
+        if (i >= 2) cuda_check(cudaStreamWaitEvent(c_in, applied[b], 0), "wait");
+        cuda_check(cudaMemcpyAsync(op->d_pipe_in[b], gi + size_t(i) * in_b, in_b, cudaMemcpyHostToDevice, c_in),
+                   "H2D");
+        cuda_check(cudaEventRecord(copied_in[b], c_in), "record");
+        cuda_check(cudaStreamWaitEvent(st, copied_in[b], 0), "wait");
+        if (i >= 2) cuda_check(cudaStreamWaitEvent(st, copied_out[b], 0), "wait");
+        apply_impl(op, op->d_pipe_in[b], op->d_pipe_out[b], nrhs, precision, stream, false);
+        cuda_check(cudaEventRecord(applied[b], st), "record");
+        cuda_check(cudaStreamWaitEvent(c_out, applied[b], 0), "wait");
+        cuda_check(cudaMemcpyAsync(uo + size_t(i) * out_b, op->d_pipe_out[b], out_b, cudaMemcpyDeviceToHost, c_out),
+                   "D2H");
+        cuda_check(cudaEventRecord(copied_out[b], c_out), "record");
+      }
+    } catch (...) {
+      // nothing of this call may still be in flight when it returns
+      cudaStreamSynchronize(c_in);
+      cudaStreamSynchronize(st);
+      cudaStreamSynchronize(c_out);
+      throw;
+    }
+    cuda_check(cudaStreamSynchronize(c_out), "sync");
     cuda_check(cudaStreamSynchronize(st), "sync");
   });
 }

@@ -85,6 +85,14 @@ struct mbf_op_s {
   // staging for mbf_apply_host
   float2 *d_stage_in = nullptr, *d_stage_out = nullptr;
   size_t stage_in_bytes = 0, stage_out_bytes = 0;
+  // pipeline of mbf_apply_host_batch: two staging pairs (input b, output b), the
+  // host-to-device and device-to-host copy streams, and per pair the events "input
+  // copied", "applied" and "output copied"
+  float2* d_pipe_in[2] = {nullptr, nullptr};
+  float2* d_pipe_out[2] = {nullptr, nullptr};
+  size_t pipe_in_bytes = 0, pipe_out_bytes = 0;
+  cudaStream_t pipe_st[2] = {nullptr, nullptr};
+  cudaEvent_t pipe_ev[3][2] = {};
   // error estimate against the direct sum (mbf_op_estimate_error; -1 until made)
   double eps = -1.0;
   int32_t eps_samples = 0;

@@ -137,6 +137,44 @@ def test_host_buffers_on_tensor_path(ops, bd):
     assert np.array_equal(u_pinned, u_paged)
 
 
+def test_host_batch_pipeline(ops, bd):
+    """mbf_apply_host_batch: independent panels pipelined through two device staging
+    pairs.  3 panels of 3 RHS (FP32 SIMT, pageable numpy buffers; staging allocated),
+    then 5 panels of 70 RHS (tensor path, two panels each, page-locked buffers; staging
+    grown): every panel equals the oracle's apply of its input and the same panel through
+    mbf_apply_host; one panel and zero panels; negative counts are rejected."""
+    op, fs, sb = ops(("fio_iso", 64, 2, 4, 24, "polar"))
+    st = torch.cuda.current_stream().cuda_stream
+    g3 = np.stack([complex_normal(fs.n_in, 3, seed=40 + b) for b in range(3)])
+    u3 = op.apply_host_batch(g3, 3, MBF_PREC_AUTO, st)
+    assert u3.shape == (3, 3, fs.n_out)
+    for b in range(3):
+        ref = sb.apply(g3[b])
+        one = op.apply_host(g3[b].astype(np.complex64), 3, MBF_PREC_AUTO, st)
+        for k in range(3):
+            assert rel(u3[b, k].astype(np.complex128), ref[k]) <= 1e-5
+        assert np.array_equal(u3[b], one)
+    g70 = np.stack([complex_normal(fs.n_in, 70, seed=50 + b) for b in range(5)]).astype(np.complex64)
+    gp = torch.from_numpy(g70).pin_memory()
+    up = torch.full((5, 70, fs.n_out), float("nan"), dtype=torch.complex64).pin_memory()
+    op.apply_host_batch(gp, 70, MBF_PREC_BF16X3, st, out=up)
+    u70 = up.numpy()
+    for b in range(5):
+        ref = sb.apply(g70[b].astype(np.complex128))
+        one = op.apply_host(g70[b], 70, MBF_PREC_BF16X3, st)
+        for k in range(70):
+            assert rel(u70[b, k].astype(np.complex128), ref[k]) <= TOL_BF16X3, (b, k)
+        assert np.array_equal(u70[b], one), b
+    u1 = op.apply_host_batch(g70[2:3], 70, MBF_PREC_BF16X3, st)
+    assert np.array_equal(u1[0], u70[2])
+    assert op.apply_host_batch(np.zeros((0, 70, fs.n_in), np.complex64), 70).shape == (0, 70, fs.n_out)
+    import ctypes as C
+    for nb, nr in ((-1, 3), (1, -3)):
+        with pytest.raises(bd.MbfError):
+            bd._check(bd.lib().mbf_apply_host_batch(op.handle, C.c_void_p(gp.data_ptr()),
+                                                    C.c_void_p(up.data_ptr()), nb, nr, 0, C.c_void_p(st)))
+
+
 @pytest.mark.parametrize("case", CASES)
 def test_tf32_forward_matches_oracle_within_tf32_error(ops, case):
     """The TF32 tensor path (tiles converted from the split ones on first use, kind::tf32
