@@ -672,13 +672,19 @@ constexpr int kLeafPts = 64;        // points staged per round (= kTcNR)
 constexpr int kLeafMaxR8 = 64;      // largest leaf rank (rounded up to 8) of the tensor path
 constexpr int kLeafMaxC = 8;        // children per node (3-D)
 
-// Entry e of line `line` of a chunked item (split real / imaginary planes per chunk).
-__device__ __forceinline__ float2 item_entry(const uint8_t* base, const Item& it, int line, int e) {
-  const int ci = line / it.lpc, li = line - ci * it.lpc;
+// Entry e of line ci lpc + li (chunk ci, line li within it) of a chunked item (split
+// real / imaginary planes per chunk).
+__device__ __forceinline__ float2 item_entry_cl(const uint8_t* base, const Item& it, int ci, int li, int e) {
   const int nl = min(int(it.lpc), int(it.nlines) - ci * int(it.lpc));
   const float* re = reinterpret_cast<const float*>(base + int64_t(ci) * chunk_bytes(it.lpc, it.len));
   const int64_t q = int64_t(li) * it.len + e;
   return make_float2(__ldg(re + q), __ldg(re + pad4(int64_t(nl) * it.len) + q));
+}
+
+// Entry e of line `line` of a chunked item.
+__device__ __forceinline__ float2 item_entry(const uint8_t* base, const Item& it, int line, int e) {
+  const int ci = line / it.lpc;
+  return item_entry_cl(base, it, ci, line - ci * it.lpc, e);
 }
 
 // Panel in tree order: gt[inv(i)][n] = g[rhs0 + n][i] for the natural Omega indices i
@@ -841,26 +847,46 @@ __global__ void __launch_bounds__(kTcNR * kLeafMaxR8 / 8) leaf_v_kernel(const __
         // q / nb of point q % nb, so that a warp's loads fall on a few nearby rows
         for (int q = tid; q < nb; q += nth) nat[q] = b0 == 0 ? nat0 : __ldg(natj + b0 + q);
         __syncthreads();
-        for (int q0 = tid; q0 < nb * NR; q0 += 4 * nth) {        // 4 loads in flight per thread
+        // (nn, b) = divmod(q, nb) for q = tid, tid + nth, ...: advanced by divmod(nth, nb)
+        // with one carry (b + db < 2 nb), two divisions per thread and round
+        const int total = nb * NR, dn = nth / nb, db = nth - dn * nb;
+        int nn = tid / nb;
+        int bb = tid - nn * nb;
+        for (int q0 = tid; q0 < total; q0 += 4 * nth) {          // 4 loads in flight per thread
           float2 v[4];
+          int bs[4], ns[4];
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
-            const int q = q0 + u * nth, nn = q / nb, b = q - nn * nb, rhs = a.rhs0 + nn;
-            v[u] = (q < nb * NR && rhs < a.nrhs)
-                       ? __ldg((a.use_rows ? a.rows.in[rhs] : a.vec + int64_t(rhs) * a.len_vec) + nat[b])
-                                                 : make_float2(0.f, 0.f);
+            const int q = q0 + u * nth, rhs = a.rhs0 + nn;
+            ns[u] = nn;
+            bs[u] = bb;
+            v[u] = (q < total && rhs < a.nrhs)
+                       ? __ldg((a.use_rows ? a.rows.in[rhs] : a.vec + int64_t(rhs) * a.len_vec) + nat[bb])
+                       : make_float2(0.f, 0.f);
+            nn += dn;
+            bb += db;
+            if (bb >= nb) {
+              bb -= nb;
+              ++nn;
+            }
           }
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int q = q0 + u * nth, nn = q / nb, b = q - nn * nb;
-            if (q < nb * NR) xs[b * xstride + nn] = v[u];
-          }
+          for (int u = 0; u < 4; ++u)
+            if (q0 + u * nth < total) xs[bs[u] * xstride + ns[u]] = v[u];
         }
       } else {
         for (int q = tid; q < nb * (NR / 2); q += nth) cp_async16(sa(xs) + uint32_t(q) * 16u, src + 2 * q);
       }
+      const int lpc = it.lpc;
       for (int b1 = bq; b1 < nb; b1 += 8 * bstep) {             // 8 loads in flight per thread
         float2 v[8];
+        // forward: line pt of the item, as (chunk, line in chunk), advanced by bstep per u
+        int ci = 0, li = 0;
+        if (!XPOSE) {
+          const int line = p0 - pg + b0 + b1;
+          ci = line / lpc;
+          li = line - ci * lpc;
+        }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const int b = b1 + u * bstep, pt = p0 - pg + b0 + b;
@@ -870,7 +896,14 @@ __global__ void __launch_bounds__(kTcNR * kLeafMaxR8 / 8) leaf_v_kernel(const __
               const float2 e = item_entry(ibase, it, kq, pt);
               v[u] = make_float2(e.x, -e.y);
             } else {
-              v[u] = item_entry(ibase, it, pt, kq);
+              v[u] = item_entry_cl(ibase, it, ci, li, kq);
+            }
+          }
+          if (!XPOSE) {
+            li += bstep;
+            while (li >= lpc) {
+              li -= lpc;
+              ++ci;
             }
           }
         }
