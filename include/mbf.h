@@ -470,6 +470,11 @@ mbf_status mbf_server_create(const mbf_server_opts_t* opts, mbf_server_t* out);
 mbf_status mbf_debug_form_batch(const int32_t* ops, const int64_t* nrhs, int64_t n, const double* op_work,
                                 int32_t n_ops, int32_t free_slots, const mbf_server_opts_t* opts,
                                 int32_t* group_of);
+/* The worker's split of a batch's SMs among its n groups, as a pure host function: share
+ * SMs in proportion to work[k] (each > 0 and finite), at least one per group, the rounding
+ * remainder to the group of most work (the first of equal ones); written to sms_out[k].
+ * The shares sum to share when share >= n.  Needs no device. */
+mbf_status mbf_debug_split_sms(const double* work, int32_t n, int32_t share, int32_t* sms_out);
 mbf_status mbf_submit(mbf_server_t s, mbf_op_t op, const void* g, void* u, int64_t nrhs,
                       mbf_ticket_t* ticket);
 mbf_status mbf_poll(mbf_server_t s, mbf_ticket_t ticket, mbf_request_status_t* status);

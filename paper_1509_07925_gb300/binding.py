@@ -159,6 +159,7 @@ SIGNATURES = {
     "mbf_server_create": (C.c_int, [C.POINTER(ServerOpts), C.POINTER(C.c_void_p)]),
     "mbf_debug_form_batch": (C.c_int, [C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.c_int64, C.POINTER(C.c_double),
                                        C.c_int32, C.c_int32, C.POINTER(ServerOpts), C.POINTER(C.c_int32)]),
+    "mbf_debug_split_sms": (C.c_int, [C.POINTER(C.c_double), C.c_int32, C.c_int32, C.POINTER(C.c_int32)]),
     "mbf_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                              C.POINTER(C.c_int64)]),
     "mbf_poll": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(RequestStatus)]),
@@ -493,6 +494,17 @@ def form_batch(ops, nrhs, op_work, free_slots=1, **opts):
     a_w = (C.c_double * max(len(op_work), 1))(*op_work)
     out = (C.c_int32 * max(n, 1))()
     _check(lib().mbf_debug_form_batch(a_ops, a_rhs, n, a_w, len(op_work), free_slots, C.byref(o), out))
+    return list(out)[:n]
+
+
+def split_sms(work, share):
+    """The server's split of a batch's SMs among its groups (mbf_debug_split_sms): share
+    SMs in proportion to work[k], at least one each, the remainder to the group of most
+    work."""
+    n = len(work)
+    a_w = (C.c_double * max(1, n))(*work)
+    out = (C.c_int32 * max(1, n))()
+    _check(lib().mbf_debug_split_sms(a_w, n, share, out))
     return list(out)[:n]
 
 

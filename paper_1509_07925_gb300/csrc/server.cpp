@@ -21,6 +21,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <deque>
 #include <functional>
@@ -144,6 +145,29 @@ std::vector<std::vector<size_t>> form_batch(const std::vector<QueuedReq>& q, int
   return groups;
 }
 
+// SMs of each group of a batch: `share` split in proportion to the groups' factor
+// traffic (work > 0), at least one each, the rounding remainder to the group of most
+// work (the first of equal ones), so that the groups finish together.  The shares sum
+// to `share` when it is at least the number of groups; with fewer SMs than groups every
+// group still gets one (the groups then share SMs).
+std::vector<int> split_share(const std::vector<double>& work, int share) {
+  const size_t ng = work.size();
+  if (ng == 0) return {};
+  if (ng == 1) return {share};
+  double sum = 0;
+  for (double w : work) sum += w;
+  std::vector<int> g(ng);
+  int used = 0;
+  size_t big = 0;
+  for (size_t k = 0; k < ng; ++k) {
+    g[k] = std::max(1, int(double(share) * work[k] / sum));
+    used += g[k];
+    if (work[k] > work[big]) big = k;
+  }
+  g[big] = std::max(1, g[big] + share - used);
+  return g;
+}
+
 }  // namespace
 
 struct mbf_server_s {
@@ -225,26 +249,13 @@ struct mbf_server_s {
     return 8.0 * double(std::max<int64_t>(op->nnz, 1)) * double((rhs + 3) / 4);
   }
 
-  // SMs of each group: the batch's share (grid, or the whole GPU when 0) split in
-  // proportion to the groups' factor traffic, at least one each, so that the groups
-  // finish together instead of the largest one running on an even split.
+  // SMs of each group: the batch's share (grid, or the whole GPU when 0) split by the
+  // groups' factor traffic (split_share).  A batch of one group keeps `grid` as it is.
   std::vector<int> group_grids(const Batch& b, int grid) const {
-    const size_t ng = b.groups.size();
-    if (ng == 1) return {grid};
-    const int share = grid > 0 ? grid : sms;
-    std::vector<double> w(ng);
-    double sum = 0;
-    for (size_t k = 0; k < ng; ++k) sum += (w[k] = group_work(b.groups[k].op, b.groups[k].rhs));
-    std::vector<int> g(ng);
-    int used = 0;
-    size_t big = 0;
-    for (size_t k = 0; k < ng; ++k) {
-      g[k] = std::max(1, int(double(share) * w[k] / sum));
-      used += g[k];
-      if (w[k] > w[big]) big = k;
-    }
-    g[big] = std::max(1, g[big] + share - used);   // the remainder to the largest group
-    return g;
+    if (b.groups.size() == 1) return {grid};
+    std::vector<double> w;
+    for (const Group& gr : b.groups) w.push_back(group_work(gr.op, gr.rhs));
+    return split_share(w, grid > 0 ? grid : sms);
   }
 
   // All groups of a batch: group 0 on the slot's stream, the others on branch streams
@@ -649,6 +660,20 @@ mbf_status mbf_server_stats(mbf_server_t s, mbf_server_stats_t* out) {
 
 mbf_status mbf_server_destroy(mbf_server_t s) {
   return sguard([&] { server_free(s); });
+}
+
+mbf_status mbf_debug_split_sms(const double* work, int32_t n, int32_t share, int32_t* sms_out) {
+  return sguard([&] {
+    if (n < 0 || (n > 0 && (!work || !sms_out))) fail(MBF_ERR_INVALID, "NULL argument or negative count");
+    if (share < 1) fail(MBF_ERR_INVALID, "share < 1");
+    std::vector<double> w(static_cast<size_t>(n));
+    for (int32_t k = 0; k < n; ++k) {
+      if (!(work[k] > 0.0) || !std::isfinite(work[k])) fail(MBF_ERR_INVALID, "work must be positive and finite");
+      w[size_t(k)] = work[k];
+    }
+    const std::vector<int> g = split_share(w, share);
+    for (int32_t k = 0; k < n; ++k) sms_out[k] = g[size_t(k)];
+  });
 }
 
 mbf_status mbf_debug_form_batch(const int32_t* ops, const int64_t* nrhs, int64_t n, const double* op_work,

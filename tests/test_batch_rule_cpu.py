@@ -71,3 +71,23 @@ def test_invalid_arguments(bd):
     with pytest.raises(bd.MbfError):
         bd.form_batch([0], [1], [1.0], max_batch_ops=9)    # more than 8 operators per batch
     assert bd.form_batch([], [], [1.0]) == []
+
+
+def test_sm_share_split_by_traffic(bd):
+    # proportional shares, the rounding remainder to the group of most work
+    assert bd.split_sms([3.0, 1.0], 152) == [114, 38]
+    assert bd.split_sms([1.0, 1.0, 1.0], 152) == [52, 50, 50]        # 50 each + 2 to the first
+    assert bd.split_sms([1.0, 5.0, 1.0], 100) == [14, 72, 14]
+    # one group keeps the share; every group gets at least one SM
+    assert bd.split_sms([7.0], 40) == [40]
+    g = bd.split_sms([1e-9, 1.0, 1.0], 10)
+    assert g[0] == 1 and sum(g) == 10
+    for work, share in (([2.0, 3.0, 5.0, 7.0], 152), ([1.0] * 8, 152), ([1.0, 1e6], 152), ([4.0, 4.0], 3)):
+        g = bd.split_sms(work, share)
+        assert sum(g) == share and min(g) >= 1, (work, share, g)
+    # fewer SMs than groups: one each (the groups share SMs)
+    assert bd.split_sms([1.0, 2.0, 3.0], 2) == [1, 1, 1]
+    assert bd.split_sms([], 10) == []
+    for work, share in (([1.0, 0.0], 10), ([1.0, -1.0], 10), ([1.0, float("nan")], 10), ([1.0], 0)):
+        with pytest.raises(bd.MbfError):
+            bd.split_sms(work, share)
