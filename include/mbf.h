@@ -475,6 +475,19 @@ mbf_status mbf_debug_form_batch(const int32_t* ops, const int64_t* nrhs, int64_t
  * remainder to the group of most work (the first of equal ones); written to sms_out[k].
  * The shares sum to share when share >= n.  Needs no device. */
 mbf_status mbf_debug_split_sms(const double* work, int32_t n, int32_t share, int32_t* sms_out);
+/* Host interpreter of the packed device layouts (for tests of the packers without a
+ * device): packs the factor set on the host exactly as mbf_op_create does before it
+ * uploads, then applies the packed data in FP64 as the layout defines it.  path 0: the
+ * FP32 SIMT arena (items of complex64 entries), forward (adjoint = 0, eq. gbf) or
+ * adjoint (1); path 1: the tensor path, forward only: the split-BF16 tiles of the G / H
+ * levels (each entry hi + lo) with the leaf items of the SIMT arena.  in / out: host
+ * complex128 (interleaved doubles), [nrhs][n_in] -> [nrhs][n_out] (adjoint: n_out ->
+ * n_in), out fully overwritten.  MBF_ERR_INVALID for an invalid factor set, a tensor
+ * path the tiles do not fit (the reason in mbf_last_error), or a packed layout that
+ * breaks its own definition (an entry outside the arena, a nonzero in the tiles' rank
+ * padding, a leaf point outside its group). */
+mbf_status mbf_debug_layout_apply(const mbf_factors_t* f, int32_t path, int32_t adjoint, const void* in,
+                                  void* out, int64_t nrhs);
 mbf_status mbf_submit(mbf_server_t s, mbf_op_t op, const void* g, void* u, int64_t nrhs,
                       mbf_ticket_t* ticket);
 mbf_status mbf_poll(mbf_server_t s, mbf_ticket_t ticket, mbf_request_status_t* status);

@@ -160,6 +160,7 @@ SIGNATURES = {
     "mbf_debug_form_batch": (C.c_int, [C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.c_int64, C.POINTER(C.c_double),
                                        C.c_int32, C.c_int32, C.POINTER(ServerOpts), C.POINTER(C.c_int32)]),
     "mbf_debug_split_sms": (C.c_int, [C.POINTER(C.c_double), C.c_int32, C.c_int32, C.POINTER(C.c_int32)]),
+    "mbf_debug_layout_apply": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_int64]),
     "mbf_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                              C.POINTER(C.c_int64)]),
     "mbf_poll": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(RequestStatus)]),
@@ -621,3 +622,16 @@ class MsBF:
             self.close()
         except Exception:
             pass
+
+
+def layout_apply(factors, g, path=0, adjoint=False):
+    """Host FP64 apply of the packed device layout (mbf_debug_layout_apply): path 0 the
+    SIMT arena (forward or adjoint), path 1 the tensor tiles (forward).  g: complex
+    [nrhs, n] -> complex128 [nrhs, n']."""
+    g = np.ascontiguousarray(np.atleast_2d(g), dtype=np.complex128)
+    v = factors.view
+    n_dst = v.n_in if adjoint else v.n_out
+    out = np.empty((g.shape[0], n_dst), dtype=np.complex128)
+    _check(lib().mbf_debug_layout_apply(C.byref(v), path, 1 if adjoint else 0, g.ctypes.data_as(C.c_void_p),
+                                        out.ctypes.data_as(C.c_void_p), g.shape[0]))
+    return out

@@ -1082,6 +1082,33 @@ void ws_free(Workspace& w) {
 
 void tc_prepare(mbf_op_s* op) { ws_prepare_tc(op, op->ws); }
 
+void pack_host(const mbf_factors_t& f, PackedHost& out) {
+  validate_factors(f);
+  mbf_op_s tmp;   // receives the plan and the per-stage counts; no device state
+  Packer pk(f);
+  pk.run(tmp);
+  int64_t rmax = 1;
+  for (int l = f.L / 2; l <= f.L; ++l) rmax = std::max<int64_t>({rmax, f.RU[l], f.RV[l]});
+  const int64_t positions = Tree::ipow(int64_t(1) << f.dim, f.L) * rmax;
+  out = PackedHost{};
+  check_plan(tmp.plan, pk.items, pk.arena.size(), positions, f, &out.simt_unavailable);
+  out.plan = tmp.plan;
+  out.items = std::move(pk.items);
+  out.arena = std::move(pk.arena);
+  try {
+    int mt = 0, kp = 0;
+    pack_tc(f, out.plan, out.tcplan, out.tc_arena, mt, kp);
+    const Stage& first = out.plan.st[0];
+    const Stage& last = out.plan.st[out.plan.n_stages - 1];
+    if (out.plan.n_stages < 2 || first.n_items != 1 || last.n_items != 2 || last.B != 1 ||
+        out.tcplan.st[0].in_pat != PAT_SPLIT || out.tcplan.st[0].B != 1)
+      fail(MBF_ERR_INVALID, "plan shape not supported by the tensor path");
+  } catch (const Error& err) {
+    out.tc_unavailable = err.what();
+    out.tc_arena.clear();
+  }
+}
+
 Workspace* ws_acquire(mbf_op_s* op, bool tensor) {
   std::lock_guard<std::mutex> lk(op->ws_mu);
   Workspace* w = nullptr;

@@ -130,6 +130,19 @@ int64_t tc_vec_bytes(const mbf_op_s* op);
 // output rows instead of in / out (forward, device buffers, nrhs <= kRowTab).
 void apply_dev(mbf_op_s* op, const void* in, void* out, int64_t nrhs, int32_t precision, cudaStream_t st,
                bool adj, int grid, bool accumulate = false, Workspace* ws = nullptr, const RowTable* rows = nullptr);
+// The packed layouts of a factor set, made on the host by the same packers and checks
+// that mbf_op_create runs before it uploads them: the SIMT plan, items and arena, and
+// the tensor path's tile plan and arena (unless the tiles do not fit: tc_unavailable
+// says why).  No device is touched.  Throws mbf::Error on an invalid factor set.
+struct PackedHost {
+  Plan plan{};
+  std::vector<Item> items;
+  std::vector<uint8_t> arena;
+  TCPlan tcplan{};
+  std::vector<uint8_t> tc_arena;
+  std::string simt_unavailable, tc_unavailable;
+};
+void pack_host(const mbf_factors_t& f, PackedHost& out);
 // The error estimator of §3.3 (estimate.cpp); keeps the result in op->eps.
 double estimate_error(mbf_op_s* op, mbf_entry_fn fn, void* ctx, int32_t n_samples, uint64_t seed,
                       cudaStream_t st);

@@ -1,0 +1,74 @@
+"""The packed device layouts checked on the CPU (mbf_debug_layout_apply): the factor
+set is packed on the host by the same packers mbf_op_create uses, and the packed data
+applied in FP64 as the layout defines it must give the oracle's FP64 apply of the same
+factors.  Path 0 is the FP32 SIMT arena (forward and adjoint); path 1 the split-BF16x3
+tiles of the tensor path (forward), whose rank padding must hold zeros.  The cases span
+2-D / 3-D, uniform and polar Omega trees (ragged and empty leaves), the corner turn with
+S folded into G^h, several tile chunks and the largest tile (c r = 256)."""
+import numpy as np
+import pytest
+
+from mbf_synth import complex_normal
+
+from gpu_util import import_factors, oracle_case, rel
+
+pytest.importorskip("torch")
+
+CASES = [
+    ("dft", 16, 2, 2, 8, "none"),         # L = 2: one H and one G stage
+    ("dft", 64, 2, 4, 16, "none"),        # depth 4: two H and two G stages
+    ("fio_iso", 64, 2, 4, 24, "polar"),   # ragged polar leaves, empty leaves, ranks not multiples of 8
+    ("dft", 8, 3, 2, 16, "none"),         # 3-D octree (c = 8)
+    ("dft", 32, 2, 2, 64, "none"),        # c r = 256 (the largest tile)
+]
+
+# complex64 entries: each rounded to 2^-24 relative; a few levels of sums
+TOL_SIMT = 2e-6
+# hi + lo bf16 of each entry: about 2^-17 relative
+TOL_TILES = 1e-4
+
+
+@pytest.fixture(scope="module")
+def bd():
+    from paper_1509_07925_gb300 import buildlib
+    buildlib.build()
+    from paper_1509_07925_gb300 import binding
+    return binding
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_simt_arena_forward_and_adjoint(bd, case):
+    fs, sb = oracle_case(*case)
+    hf = import_factors(bd, fs)
+    g = complex_normal(fs.n_in, 3, seed=11)
+    u = bd.layout_apply(hf, g, path=0)
+    ref = sb.apply(g)
+    for k in range(3):
+        assert rel(u[k], ref[k]) <= TOL_SIMT, (k, rel(u[k], ref[k]))
+    w = complex_normal(fs.n_out, 2, seed=12)
+    gt = bd.layout_apply(hf, w, path=0, adjoint=True)
+    ref_t = sb.adjoint(w)
+    for k in range(2):
+        assert rel(gt[k], ref_t[k]) <= TOL_SIMT, (k, rel(gt[k], ref_t[k]))
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_tensor_tiles_forward(bd, case):
+    fs, sb = oracle_case(*case)
+    hf = import_factors(bd, fs)
+    g = complex_normal(fs.n_in, 2, seed=13)
+    u = bd.layout_apply(hf, g, path=1)
+    ref = sb.apply(g)
+    for k in range(2):
+        assert rel(u[k], ref[k]) <= TOL_TILES, (k, rel(u[k], ref[k]))
+
+
+def test_layout_arguments(bd):
+    fs, _ = oracle_case("dft", 16, 2, 2, 8, "none")
+    hf = import_factors(bd, fs)
+    g = complex_normal(fs.n_in, 1, seed=1)
+    with pytest.raises(bd.MbfError):
+        bd.layout_apply(hf, g, path=2)
+    with pytest.raises(bd.MbfError):
+        bd.layout_apply(hf, complex_normal(fs.n_out, 1, seed=1), path=1, adjoint=True)   # tiles: forward only
+    assert bd.layout_apply(hf, np.zeros((0, fs.n_in)), path=0).shape == (0, fs.n_out)
