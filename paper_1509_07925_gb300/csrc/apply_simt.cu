@@ -529,15 +529,35 @@ __global__ void __launch_bounds__(Cfg<NRB>::W * 32, 1) bf_apply_simt(const __gri
           }
           __syncwarp();
           // the group's input segments from the previous stage's vector (L2), in
-          // batches of 8 independent loads per lane
-          const int nq = c * Rin * NRB;
+          // batches of 8 independent loads per lane; a compact stage's main item holds
+          // only the first r_t lines of segment t (c = 4), so only those are read, packed
+          // in line order: segment t starts at line p_t = r_0 + ... + r_(t-1)
+          const bool cmp = st.compact && !ADJ;
+          int p1 = Rin, p2 = 2 * Rin, p3 = 3 * Rin, nlin = c * Rin;
+          if (cmp) {
+            const int32_t rk = __shfl_sync(0xffffffffu, myit.base, st.main_idx);
+            p1 = seg_lines(rk, 0);
+            p2 = p1 + seg_lines(rk, 1);
+            p3 = p2 + seg_lines(rk, 2);
+            nlin = p3 + seg_lines(rk, 3);
+          }
+          const int nq = nlin * NRB;
           for (int qb = 0; qb < nq; qb += 32 * 8) {
             float2 v[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
               const int q = qb + lane + 32 * u;
               if (q < nq) {
-                const int r = q % NRB, kk = (q / NRB) % Rin, t = q / (NRB * Rin);
+                const int r = q % NRB;
+                int t, kk;
+                if (cmp) {
+                  const int line = q / NRB;
+                  t = (line >= p1 ? 1 : 0) + (line >= p2 ? 1 : 0) + (line >= p3 ? 1 : 0);
+                  kk = line - (t == 0 ? 0 : t == 1 ? p1 : t == 2 ? p2 : p3);
+                } else {
+                  kk = (q / NRB) % Rin;
+                  t = q / (NRB * Rin);
+                }
                 const int64_t pos = pat_off(in_pat, g, t, st, Rin, c) + kk;
                 v[u] = __ldcg(src + pos * NRB + r);
               }
@@ -742,12 +762,22 @@ __global__ void __launch_bounds__(Cfg<NRB>::W * 32, 1) bf_apply_simt(const __gri
                 for (int r = 0; r < NRB; ++r) xin[ee * NRB + r] = acc.v[j][r];
             }
           } else if (kind == ITEM_MAIN && ADJ && out_pat != PAT_LEAF) {
-            // adjoint main block: scatter yout (forward-input layout) to the next buffer
+            // adjoint main block: scatter yout (forward-input layout) to the next buffer;
+            // in a compact stage yout holds the item's lines (the first r_t entries of
+            // each segment t, in order) and the entries beyond r_t are zero
             __syncwarp();
             for (int q = lane; q < c * Rout * NRB; q += 32) {
               const int r = q % NRB, kk = (q / NRB) % Rout, t = q / (NRB * Rout);
               const int64_t pos = pat_off(out_pat, g, t, st, Rout, c) + kk;
-              dst[pos * NRB + r] = yout[q];
+              float2 v;
+              if (st.compact) {
+                int pre = 0;
+                for (int u = 0; u < t; ++u) pre += seg_lines(it.base, u);
+                v = kk < seg_lines(it.base, t) ? yout[(pre + kk) * NRB + r] : make_float2(0.f, 0.f);
+              } else {
+                v = yout[q];
+              }
+              dst[pos * NRB + r] = v;
             }
             notify_consumers(g);
           }

@@ -12,6 +12,8 @@
 // (its main block, plus c leaf blocks in the first/last stage), each item a set of
 // `nlines` lines of `len` complex entries streamed in chunks of `lpc` lines.  A
 // chunk holds its real plane then its imaginary plane, each padded to 16 bytes.
+// A main block's lines are its inputs (segment t, entry k); a compact stage stores
+// only the lines below each input segment's rank (Stage::compact).
 #pragma once
 #include <cstdint>
 
@@ -60,7 +62,11 @@ struct Stage {
   int32_t R_in, R_out;       // forward sense segment lengths
   int32_t B, ch;             // c^(L-l-1), c^h
   int32_t level, side;       // factor level l; side 0 = G (X tree), 1 = H (Omega tree)
-  int32_t leaf_only, pad_;   // 1: the stage applies only the (V^L)^* leaf products
+  int32_t leaf_only;         // 1: the stage applies only the (V^L)^* leaf products
+  // 1: a main item holds only the first r_t lines of each input segment t (the lines
+  // beyond a segment's rank are zero and are not stored); r_t is byte t of the item's
+  // base and the item's lines are those of segment 0, then 1, ... (c = 4 only)
+  int32_t compact;
   int64_t item_base;         // items of group g start at item_base + g * n_items
   int64_t bytes;             // packed bytes streamed by this stage
 };
@@ -92,6 +98,9 @@ struct TCPlan {
 
 constexpr int kTcMaxRows = 256;   // M_t limit (the MMA's N)
 constexpr int kTcMaxK = 256;      // K_t limit
+
+// Byte of an item's base holding r_t in a compact stage.
+MBF_HD int seg_lines(int32_t base, int t) { return int((uint32_t(base) >> (8 * t)) & 0xffu); }
 
 MBF_HD int64_t pad4(int64_t x) { return (x + 3) & ~int64_t(3); }
 MBF_HD int64_t chunk_bytes(int64_t nl, int64_t len) { return 2 * pad4(nl * len) * 4; }

@@ -97,6 +97,20 @@ struct Interp {
     return ph.items[size_t(i)];
   }
 
+  // Input entry (t, k), as line t Rin + k of the full block, of each stored line of a
+  // main item: all c Rin lines, or in a compact stage the first r_t of each segment t
+  // (r_t from byte t of the item's base).
+  std::vector<int> main_lines(const Stage& st, const Item& m) const {
+    std::vector<int> lines;
+    for (int t = 0; t < c; ++t) {
+      const int r = st.compact ? mbf::seg_lines(m.base, t) : st.R_in;
+      if (r > st.R_in) fail(MBF_ERR_INVALID, "layout: segment line count above the rank");
+      for (int k = 0; k < r; ++k) lines.push_back(t * st.R_in + k);
+    }
+    if (int(lines.size()) != m.nlines || m.len != c * st.R_out) fail(MBF_ERR_INVALID, "layout: main item shape");
+    return lines;
+  }
+
   // (V^L)^*: the level-L coefficient vector from g (natural Omega order)
   void leaf_forward(const cd* g, std::vector<cd>& out) const {
     const Stage& s0 = ph.plan.st[0];
@@ -133,10 +147,10 @@ struct Interp {
       std::vector<cd> y(size_t(c * st.R_out));
       for (int64_t grp = 0; grp < st.n_groups; ++grp) {
         const Item& m = item(st, grp, st.main_idx);
-        if (m.nlines != c * st.R_in || m.len != c * st.R_out) fail(MBF_ERR_INVALID, "layout: main item shape");
+        const std::vector<int> full = main_lines(st, m);
         std::fill(y.begin(), y.end(), cd(0.0));
         for (int line = 0; line < m.nlines; ++line) {
-          const int tp = line / st.R_in, k = line % st.R_in;
+          const int tp = full[size_t(line)] / st.R_in, k = full[size_t(line)] % st.R_in;
           const cd x = cur[size_t(seg(st.in_pat, grp, tp, st.B, st.ch, st.R_in, c) + k)];
           for (int q = 0; q < m.len; ++q) y[size_t(q)] += item_at(ph.arena, m, line, q) * x;
         }
@@ -176,8 +190,9 @@ struct Interp {
               y[size_t(t * st.R_out + k2)] = cur[size_t(seg(st.out_pat, grp, t, st.B, st.ch, st.R_out, c) + k2)];
         }
         const Item& m = item(st, grp, st.main_idx);
+        const std::vector<int> full = main_lines(st, m);
         for (int line = 0; line < m.nlines; ++line) {
-          const int tp = line / st.R_in, k = line % st.R_in;
+          const int tp = full[size_t(line)] / st.R_in, k = full[size_t(line)] % st.R_in;
           cd s = 0;
           for (int q = 0; q < m.len; ++q) s += std::conj(item_at(ph.arena, m, line, q)) * y[size_t(q)];
           nxt[size_t(seg(st.in_pat, grp, tp, st.B, st.ch, st.R_in, c) + k)] += s;

@@ -108,6 +108,32 @@ struct Packer {
     return it;
   }
 
+  // Main item of a group: c Rin lines (input entry (t, k) is line t Rin + k) of c Rout
+  // entries.  In a compact stage only the first r_t lines of each input segment t are
+  // stored, r_t = 1 + its last line holding a nonzero entry (0: none), with the c = 4
+  // counts in the item's base, one byte each.
+  template <class F>
+  Item add_main(const Stage& st, int Rin, int Rout, F value) {
+    if (!st.compact) return add_item(c * Rin, c * Rout, ITEM_MAIN, 0, value);
+    std::vector<int> lines;
+    uint32_t counts = 0;
+    for (int t = 0; t < c; ++t) {
+      int r = 0;
+      for (int k = Rin - 1; k >= 0 && r == 0; --k)
+        for (int e = 0; e < c * Rout; ++e)
+          if (value(t * Rin + k, e) != cd(0.0, 0.0)) {
+            r = k + 1;
+            break;
+          }
+      for (int k = 0; k < r; ++k) lines.push_back(t * Rin + k);
+      counts |= uint32_t(r) << (8 * t);
+    }
+    Item it = add_item(int(lines.size()), c * Rout, ITEM_MAIN, 0,
+                       [&](int line, int e) { return value(lines[size_t(line)], e); });
+    it.base = int32_t(counts);
+    return it;
+  }
+
   void run(mbf_op_s& op) {
     d = f.dim;
     L = f.L;
@@ -131,6 +157,7 @@ struct Packer {
       st.B = int32_t(ipow(c, L - level - 1));
       st.ch = int32_t(ipow(c, h));
       st.item_base = int64_t(items.size());
+      st.compact = c == 4 ? 1 : 0;   // r_t <= 64 fits a byte; four bytes fit the base
       return st;
     };
     // ---- leaf stage: (V^L_j)^* for the c leaves of each group, written to the
@@ -145,6 +172,7 @@ struct Packer {
       st.n_items = 1;
       st.main_idx = -1;
       st.leaf_only = 1;
+      st.compact = 0;
       const size_t a0 = arena.size();
       for (int64_t g = 0; g < st.n_groups; ++g) {
         // all points of the group's c leaves in one item: line = a point (tree order),
@@ -176,7 +204,7 @@ struct Packer {
       const size_t a0 = arena.size();
       for (int64_t g = 0; g < st.n_groups; ++g) {
         // T[(tp,k)][(t,k2)] = conj(H^l_{c j + t, ip}[k2][(tp,k)]), lines = (t,k2)
-        items.push_back(add_item(c * R2, c * R1, ITEM_MAIN, 0, [&](int line, int e) {
+        items.push_back(add_main(st, R2, R1, [&](int line, int e) {
           const int t = line / R2, k2 = line % R2, tp = e / R1, k = e % R1;
           return std::conj(cplx(Hl, ((((g * c + t) * R2 + k2) * c + tp) * R1) + k));
         }));
@@ -201,7 +229,7 @@ struct Packer {
       const size_t a0 = arena.size();
       for (int64_t g = 0; g < st.n_groups; ++g) {
         const int64_t i = g / B, jp = g % B;
-        items.push_back(add_item(c * R1, c * R2, ITEM_MAIN, 0, [&](int line, int e) {
+        items.push_back(add_main(st, R1, R2, [&](int line, int e) {
           const int tp = line / R1, k = line % R1, t = e / R2, k2 = e % R2;
           cd v = cplx(Gl, ((((g * c + t) * R2 + k2) * c + tp) * R1) + k);
           if (l == h) v *= f.S[(i * ch + (c * jp + tp)) * R1 + k];
@@ -461,7 +489,16 @@ void check_plan(const Plan& plan, const std::vector<Item>& items, size_t arena_b
           *simt_reason = "an item line or chunk exceeds the SIMT kernel's pipeline slot";
         const int64_t leaf = c * g;
         if (it.kind == ITEM_MAIN) {
-          if (it.nlines != c * st.R_in || it.len != c * st.R_out) fail(MBF_ERR_INVALID, "plan: main block shape");
+          int64_t lines = int64_t(c) * st.R_in;
+          if (st.compact) {
+            if (c != 4) fail(MBF_ERR_INVALID, "plan: compact stage with c != 4");
+            lines = 0;
+            for (int t = 0; t < c; ++t) {
+              if (seg_lines(it.base, t) > st.R_in) fail(MBF_ERR_INVALID, "plan: segment line count above the rank");
+              lines += seg_lines(it.base, t);
+            }
+          }
+          if (it.nlines != lines || it.len != c * st.R_out) fail(MBF_ERR_INVALID, "plan: main block shape");
         } else if (it.kind == ITEM_LEAF_W) {
           if (st.in_pat != PAT_LEAF || leaf + c > nL || it.len != st.R_in ||
               it.nlines != f.w_off[leaf + c] - f.w_off[leaf] || it.base != f.w_off[leaf])
