@@ -28,7 +28,7 @@ def _cmd(src: str, obj: str):
     if src.endswith(".cu"):
         return [f"{CUDA_HOME}/bin/nvcc", ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                 "--expt-relaxed-constexpr", "-Xptxas", "-v", *inc, "-c", src, "-o", obj]
-    return ["g++", "-O3", "-std=c++17", "-fPIC", "-pthread", "-Wall", "-Wno-unused-function", *inc,
+    return ["g++", "-O3", "-std=c++17", "-fPIC", "-pthread", "-fopenmp-simd", "-Wall", "-Wno-unused-function", *inc,
             "-c", src, "-o", obj]
 
 

@@ -12,21 +12,48 @@
 namespace mbf {
 
 static inline double norm2(const cd* x, int64_t n) {
+  const double* a = reinterpret_cast<const double*>(x);
   double s = 0;
-  for (int64_t i = 0; i < n; ++i) s += std::norm(x[i]);
+#pragma omp simd reduction(+ : s)
+  for (int64_t i = 0; i < 2 * n; ++i) s += a[i] * a[i];
   return s;
+}
+
+// w -= tau (v^* w) v for one column w of length n: the reflector I - tau v v^* applied
+// to w, in explicit real arithmetic on the interleaved (re, im) pairs (std::complex's
+// operator* carries NaN-recovery branches that keep these loops from vectorising).
+static inline void reflect(const cd* v, double tau, cd* w, int64_t n) {
+  const double* a = reinterpret_cast<const double*>(v);
+  double* b = reinterpret_cast<double*>(w);
+  // v^* w, a reduction the compiler may vectorise (its order of additions is free)
+  double sr = 0, si = 0;
+#pragma omp simd reduction(+ : sr, si)
+  for (int64_t i = 0; i < n; ++i) {
+    sr += a[2 * i] * b[2 * i] + a[2 * i + 1] * b[2 * i + 1];
+    si += a[2 * i] * b[2 * i + 1] - a[2 * i + 1] * b[2 * i];
+  }
+  sr *= tau;
+  si *= tau;
+  for (int64_t i = 0; i < n; ++i) {
+    b[2 * i] -= sr * a[2 * i] - si * a[2 * i + 1];
+    b[2 * i + 1] -= sr * a[2 * i + 1] + si * a[2 * i];
+  }
 }
 
 Mat matmul(const Mat& A, const Mat& B) {
   if (A.n != B.m) fail(MBF_ERR_INVALID, "matmul: shape mismatch");
   Mat C(A.m, B.n);
   for (int64_t j = 0; j < B.n; ++j) {
-    cd* c = C.col(j);
+    double* c = reinterpret_cast<double*>(C.col(j));
     for (int64_t k = 0; k < A.n; ++k) {
       const cd b = B(k, j);
       if (b == cd(0)) continue;
-      const cd* a = A.col(k);
-      for (int64_t i = 0; i < A.m; ++i) c[i] += a[i] * b;
+      const double br = b.real(), bi = b.imag();
+      const double* a = reinterpret_cast<const double*>(A.col(k));
+      for (int64_t i = 0; i < A.m; ++i) {
+        c[2 * i] += a[2 * i] * br - a[2 * i + 1] * bi;
+        c[2 * i + 1] += a[2 * i] * bi + a[2 * i + 1] * br;
+      }
     }
   }
   return C;
@@ -84,8 +111,13 @@ std::vector<int64_t> pivoted_qr(const Mat& A, int64_t kmax, double tol, Mat* Q) 
   Mat W = A;
   std::vector<int64_t> piv(static_cast<size_t>(n));
   std::iota(piv.begin(), piv.end(), 0);
-  std::vector<double> cn(static_cast<size_t>(n));
-  for (int64_t j = 0; j < n; ++j) cn[size_t(j)] = norm2(W.col(j), m);
+  // squared norms of the trailing parts of the columns, downdated after each step by
+  // the entry the step removes; recomputed where cancellation has consumed all but a
+  // sqrt(eps) fraction of the norm since it was last computed (the rule of LAPACK's
+  // xGEQP3 / xLAQP2), cn_ref holding that last computed value
+  std::vector<double> cn(static_cast<size_t>(n)), cn_ref(static_cast<size_t>(n));
+  for (int64_t j = 0; j < n; ++j) cn_ref[size_t(j)] = cn[size_t(j)] = norm2(W.col(j), m);
+  const double tol3z = std::sqrt(std::numeric_limits<double>::epsilon());
   std::vector<std::vector<cd>> vs;
   std::vector<double> taus;
   double first = -1;
@@ -101,20 +133,25 @@ std::vector<int64_t> pivoted_qr(const Mat& A, int64_t kmax, double tol, Mat* Q) 
     if (p != k) {
       std::swap(piv[size_t(p)], piv[size_t(k)]);
       std::swap(cn[size_t(p)], cn[size_t(k)]);
+      std::swap(cn_ref[size_t(p)], cn_ref[size_t(k)]);
       std::swap_ranges(W.col(k), W.col(k) + m, W.col(p));
     }
     double tau;
     cd beta;
     householder(W.col(k) + k, m - k, v, tau, beta);
     // apply H to the trailing columns
-    for (int64_t j = k; j < n; ++j) {
-      cd* w = W.col(j) + k;
-      cd s = 0;
-      for (int64_t i = 0; i < m - k; ++i) s += std::conj(v[size_t(i)]) * w[i];
-      s *= tau;
-      for (int64_t i = 0; i < m - k; ++i) w[i] -= s * v[size_t(i)];
+    for (int64_t j = k; j < n; ++j) reflect(v.data(), tau, W.col(j) + k, m - k);
+    for (int64_t j = k + 1; j < n; ++j) {
+      double& c = cn[size_t(j)];
+      if (c == 0.0) continue;
+      const double left = c - std::norm(W(k, j));
+      if (left <= tol3z * cn_ref[size_t(j)]) {
+        c = norm2(W.col(j) + k + 1, m - k - 1);
+        cn_ref[size_t(j)] = c;
+      } else {
+        c = left;
+      }
     }
-    for (int64_t j = k + 1; j < n; ++j) cn[size_t(j)] = norm2(W.col(j) + k + 1, m - k - 1);
     vs.push_back(v);
     taus.push_back(tau);
   }
@@ -124,13 +161,7 @@ std::vector<int64_t> pivoted_qr(const Mat& A, int64_t kmax, double tol, Mat* Q) 
     for (int64_t q = k - 1; q >= 0; --q) {
       const auto& vq = vs[size_t(q)];
       const double tau = taus[size_t(q)];
-      for (int64_t j = 0; j < k; ++j) {
-        cd* col = Q->col(j) + q;
-        cd s = 0;
-        for (int64_t i = 0; i < m - q; ++i) s += std::conj(vq[size_t(i)]) * col[i];
-        s *= tau;
-        for (int64_t i = 0; i < m - q; ++i) col[i] -= s * vq[size_t(i)];
-      }
+      for (int64_t j = 0; j < k; ++j) reflect(vq.data(), tau, Q->col(j) + q, m - q);
     }
   }
   piv.resize(size_t(k));
