@@ -42,20 +42,7 @@ Mat gram_hn(const Mat& A) {
   for (int64_t j = 0; j < A.n; ++j) {
     const cd* b = A.col(j);
     for (int64_t i = 0; i <= j; ++i) {
-      const cd* a = A.col(i);
-      double r0 = 0, r1 = 0, i0 = 0, i1 = 0;
-      int64_t k = 0;
-      for (; k + 1 < A.m; k += 2) {
-        r0 += a[k].real() * b[k].real() + a[k].imag() * b[k].imag();
-        i0 += a[k].real() * b[k].imag() - a[k].imag() * b[k].real();
-        r1 += a[k + 1].real() * b[k + 1].real() + a[k + 1].imag() * b[k + 1].imag();
-        i1 += a[k + 1].real() * b[k + 1].imag() - a[k + 1].imag() * b[k + 1].real();
-      }
-      for (; k < A.m; ++k) {
-        r0 += a[k].real() * b[k].real() + a[k].imag() * b[k].imag();
-        i0 += a[k].real() * b[k].imag() - a[k].imag() * b[k].real();
-      }
-      C(i, j) = cd(r0 + r1, i0 + i1);
+      C(i, j) = dot_hn(A.col(i), b, A.m);
       C(j, i) = std::conj(C(i, j));
     }
   }

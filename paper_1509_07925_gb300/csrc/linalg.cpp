@@ -25,15 +25,8 @@ static inline double norm2(const cd* x, int64_t n) {
 static inline void reflect(const cd* v, double tau, cd* w, int64_t n) {
   const double* a = reinterpret_cast<const double*>(v);
   double* b = reinterpret_cast<double*>(w);
-  // v^* w, a reduction the compiler may vectorise (its order of additions is free)
-  double sr = 0, si = 0;
-#pragma omp simd reduction(+ : sr, si)
-  for (int64_t i = 0; i < n; ++i) {
-    sr += a[2 * i] * b[2 * i] + a[2 * i + 1] * b[2 * i + 1];
-    si += a[2 * i] * b[2 * i + 1] - a[2 * i + 1] * b[2 * i];
-  }
-  sr *= tau;
-  si *= tau;
+  const cd s = dot_hn(v, w, n) * tau;
+  const double sr = s.real(), si = s.imag();
   for (int64_t i = 0; i < n; ++i) {
     b[2 * i] -= sr * a[2 * i] - si * a[2 * i + 1];
     b[2 * i + 1] -= sr * a[2 * i + 1] + si * a[2 * i];
@@ -62,19 +55,8 @@ Mat matmul(const Mat& A, const Mat& B) {
 Mat matmul_hn(const Mat& A, const Mat& B) {
   if (A.m != B.m) fail(MBF_ERR_INVALID, "matmul_hn: shape mismatch");
   Mat C(A.n, B.n);
-  for (int64_t j = 0; j < B.n; ++j) {
-    const cd* b = B.col(j);
-    for (int64_t i = 0; i < A.n; ++i) {
-      const cd* a = A.col(i);
-      double re = 0, im = 0;
-      for (int64_t k = 0; k < A.m; ++k) {
-        // conj(a) * b
-        re += a[k].real() * b[k].real() + a[k].imag() * b[k].imag();
-        im += a[k].real() * b[k].imag() - a[k].imag() * b[k].real();
-      }
-      C(i, j) = cd(re, im);
-    }
-  }
+  for (int64_t j = 0; j < B.n; ++j)
+    for (int64_t i = 0; i < A.n; ++i) C(i, j) = dot_hn(A.col(i), B.col(j), A.m);
   return C;
 }
 
@@ -290,6 +272,21 @@ void eig_herm(const Mat& A0, std::vector<double>& w, Mat& V) {
   }
 }
 
+// Columns (x, y) <- (c x - sn y', sn x + c y') with y' = y (pr + i pi): the complex
+// Jacobi rotation of svd_small, in explicit real arithmetic.
+static inline void rotate_pair(cd* xp, cd* yp, int64_t n, double c, double sn, double pr, double pi) {
+  double* x = reinterpret_cast<double*>(xp);
+  double* y = reinterpret_cast<double*>(yp);
+  for (int64_t i = 0; i < n; ++i) {
+    const double xr = x[2 * i], xi = x[2 * i + 1];
+    const double yr = y[2 * i] * pr - y[2 * i + 1] * pi, yi = y[2 * i] * pi + y[2 * i + 1] * pr;
+    x[2 * i] = c * xr - sn * yr;
+    x[2 * i + 1] = c * xi - sn * yi;
+    y[2 * i] = sn * xr + c * yr;
+    y[2 * i + 1] = sn * xi + c * yi;
+  }
+}
+
 void svd_small(const Mat& A, Mat& U, std::vector<double>& s, Mat& V) {
   const int64_t m = A.m, n = A.n;
   Mat W = A;
@@ -302,13 +299,18 @@ void svd_small(const Mat& A, Mat& U, std::vector<double>& s, Mat& V) {
       for (int64_t q = p + 1; q < n; ++q) {
         cd* ap = W.col(p);
         cd* aq = W.col(q);
-        double alpha = 0, beta = 0;
-        cd gamma = 0;
+        // |a_p|^2, |a_q|^2 and a_p^* a_q in one pass (explicit arithmetic, vectorisable)
+        const double* xa = reinterpret_cast<const double*>(ap);
+        const double* xb = reinterpret_cast<const double*>(aq);
+        double alpha = 0, beta = 0, gr = 0, gi = 0;
+#pragma omp simd reduction(+ : alpha, beta, gr, gi)
         for (int64_t i = 0; i < m; ++i) {
-          alpha += std::norm(ap[i]);
-          beta += std::norm(aq[i]);
-          gamma += std::conj(ap[i]) * aq[i];
+          alpha += xa[2 * i] * xa[2 * i] + xa[2 * i + 1] * xa[2 * i + 1];
+          beta += xb[2 * i] * xb[2 * i] + xb[2 * i + 1] * xb[2 * i + 1];
+          gr += xa[2 * i] * xb[2 * i] + xa[2 * i + 1] * xb[2 * i + 1];
+          gi += xa[2 * i] * xb[2 * i + 1] - xa[2 * i + 1] * xb[2 * i];
         }
+        const cd gamma(gr, gi);
         const double g = std::abs(gamma);
         if (g == 0.0 || g <= eps * std::sqrt(alpha * beta)) continue;
         rotated = true;
@@ -316,19 +318,8 @@ void svd_small(const Mat& A, Mat& U, std::vector<double>& s, Mat& V) {
         const double zeta = (beta - alpha) / (2.0 * g);
         const double t = (zeta >= 0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
         const double c = 1.0 / std::sqrt(1.0 + t * t), sn = c * t;
-        const cd phc = std::conj(ph);
-        for (int64_t i = 0; i < m; ++i) {
-          const cd x = ap[i], y = aq[i] * phc;
-          ap[i] = c * x - sn * y;
-          aq[i] = sn * x + c * y;
-        }
-        cd* vp = V.col(p);
-        cd* vq = V.col(q);
-        for (int64_t i = 0; i < n; ++i) {
-          const cd x = vp[i], y = vq[i] * phc;
-          vp[i] = c * x - sn * y;
-          vq[i] = sn * x + c * y;
-        }
+        rotate_pair(ap, aq, m, c, sn, ph.real(), -ph.imag());
+        rotate_pair(V.col(p), V.col(q), n, c, sn, ph.real(), -ph.imag());
       }
     }
     if (!rotated) break;

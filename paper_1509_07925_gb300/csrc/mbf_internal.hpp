@@ -80,6 +80,20 @@ struct Mat {
   cd* col(int64_t j) { return a.data() + m * j; }
   const cd* col(int64_t j) const { return a.data() + m * j; }
 };
+// sum_i conj(a_i) b_i, in explicit real arithmetic as a reduction the compiler may
+// vectorise (std::complex's operator* carries NaN-recovery branches that keep such loops
+// scalar; the order of the additions is left free).
+inline cd dot_hn(const cd* a, const cd* b, int64_t n) {
+  const double* x = reinterpret_cast<const double*>(a);
+  const double* y = reinterpret_cast<const double*>(b);
+  double re = 0, im = 0;
+#pragma omp simd reduction(+ : re, im)
+  for (int64_t i = 0; i < n; ++i) {
+    re += x[2 * i] * y[2 * i] + x[2 * i + 1] * y[2 * i + 1];
+    im += x[2 * i] * y[2 * i + 1] - x[2 * i + 1] * y[2 * i];
+  }
+  return cd(re, im);
+}
 Mat matmul(const Mat& A, const Mat& B);                 // A B
 Mat matmul_hn(const Mat& A, const Mat& B);              // A^* B
 Mat adjoint(const Mat& A);
