@@ -109,15 +109,5 @@ void apply_static_impl(mbf_op_s* op, const void* g, void* u, int64_t nrhs, void*
 }  // namespace
 
 extern "C" mbf_status mbf_apply_static(mbf_op_t op, const void* g, void* u, int64_t nrhs, void* stream) {
-  try {
-    apply_static_impl(op, g, u, nrhs, stream);
-    mbf::set_last_error("");
-    return MBF_OK;
-  } catch (const mbf::Error& err) {
-    mbf::set_last_error(err.what());
-    return err.code;
-  } catch (const std::exception& err) {
-    mbf::set_last_error(err.what());
-    return MBF_ERR_INVALID;
-  }
+  return mbf::abi_guard([&] { apply_static_impl(op, g, u, nrhs, stream); });
 }

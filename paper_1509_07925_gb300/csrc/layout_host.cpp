@@ -263,7 +263,7 @@ extern "C" {
 
 mbf_status mbf_debug_layout_apply(const mbf_factors_t* f, int32_t path, int32_t adjoint, const void* in, void* out,
                                   int64_t nrhs) {
-  try {
+  return mbf::abi_guard([&] {
     if (!f || (nrhs > 0 && (!in || !out))) fail(MBF_ERR_INVALID, "NULL argument");
     if (nrhs < 0) fail(MBF_ERR_INVALID, "nrhs < 0");
     if (path != 0 && path != 1) fail(MBF_ERR_INVALID, "path must be 0 (SIMT arena) or 1 (tensor tiles)");
@@ -285,18 +285,7 @@ mbf_status mbf_debug_layout_apply(const mbf_factors_t* f, int32_t path, int32_t 
       else
         ip.simt_forward(src + r * n_src, o);
     }
-    mbf::set_last_error("");
-    return MBF_OK;
-  } catch (const Error& e) {
-    mbf::set_last_error(e.what());
-    return e.code;
-  } catch (const std::bad_alloc&) {
-    mbf::set_last_error("host allocation failed");
-    return MBF_ERR_OOM;
-  } catch (const std::exception& e) {
-    mbf::set_last_error(e.what());
-    return MBF_ERR_INVALID;
-  }
+  });
 }
 
 }  // extern "C"

@@ -19,6 +19,18 @@ static inline double norm2(const cd* x, int64_t n) {
   return s;
 }
 
+cd dot_hn(const cd* a, const cd* b, int64_t n) {
+  const double* x = reinterpret_cast<const double*>(a);
+  const double* y = reinterpret_cast<const double*>(b);
+  double re = 0, im = 0;
+#pragma omp simd reduction(+ : re, im)
+  for (int64_t i = 0; i < n; ++i) {
+    re += x[2 * i] * y[2 * i] + x[2 * i + 1] * y[2 * i + 1];
+    im += x[2 * i] * y[2 * i + 1] - x[2 * i + 1] * y[2 * i];
+  }
+  return cd(re, im);
+}
+
 // w -= tau (v^* w) v for one column w of length n: the reflector I - tau v v^* applied
 // to w, in explicit real arithmetic on the interleaved (re, im) pairs (std::complex's
 // operator* carries NaN-recovery branches that keep these loops from vectorising).

@@ -3,6 +3,7 @@
 
 #include <complex>
 #include <cstdint>
+#include <new>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -20,6 +21,27 @@ struct Error : std::runtime_error {
 };
 [[noreturn]] inline void fail(mbf_status c, const std::string& m) { throw Error(c, m); }
 void set_last_error(const std::string& m);
+
+// Runs fn at the C ABI boundary: an mbf::Error becomes its status, a failed host
+// allocation MBF_ERR_OOM and any other exception MBF_ERR_INVALID; mbf_last_error() then
+// returns the message ("" after a success).  No exception crosses the ABI.
+template <class F>
+mbf_status abi_guard(F&& fn) noexcept {
+  try {
+    fn();
+    set_last_error("");
+    return MBF_OK;
+  } catch (const Error& e) {
+    set_last_error(e.what());
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    set_last_error("host allocation failed");
+    return MBF_ERR_OOM;
+  } catch (const std::exception& e) {
+    set_last_error(e.what());
+    return MBF_ERR_INVALID;
+  }
+}
 
 // ---------------------------------------------------------------- trees (§2.2)
 // A Z-order tree of depth L stored as the permutation tree order -> point index
@@ -80,20 +102,9 @@ struct Mat {
   cd* col(int64_t j) { return a.data() + m * j; }
   const cd* col(int64_t j) const { return a.data() + m * j; }
 };
-// sum_i conj(a_i) b_i, in explicit real arithmetic as a reduction the compiler may
-// vectorise (std::complex's operator* carries NaN-recovery branches that keep such loops
-// scalar; the order of the additions is left free).
-inline cd dot_hn(const cd* a, const cd* b, int64_t n) {
-  const double* x = reinterpret_cast<const double*>(a);
-  const double* y = reinterpret_cast<const double*>(b);
-  double re = 0, im = 0;
-#pragma omp simd reduction(+ : re, im)
-  for (int64_t i = 0; i < n; ++i) {
-    re += x[2 * i] * y[2 * i] + x[2 * i + 1] * y[2 * i + 1];
-    im += x[2 * i] * y[2 * i + 1] - x[2 * i + 1] * y[2 * i];
-  }
-  return cd(re, im);
-}
+// sum_i conj(a_i) b_i (linalg.cpp: explicit real arithmetic, a reduction the compiler
+// may vectorise).
+cd dot_hn(const cd* a, const cd* b, int64_t n);
 Mat matmul(const Mat& A, const Mat& B);                 // A B
 Mat matmul_hn(const Mat& A, const Mat& B);              // A^* B
 Mat adjoint(const Mat& A);

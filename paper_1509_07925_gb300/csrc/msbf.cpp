@@ -34,24 +34,6 @@ void cuda_ok(cudaError_t e, const char* what) {
   if (e != cudaSuccess) fail(MBF_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-template <class F>
-mbf_status mguard(F&& fn) {
-  try {
-    fn();
-    mbf::set_last_error("");
-    return MBF_OK;
-  } catch (const mbf::Error& e) {
-    mbf::set_last_error(e.what());
-    return e.code;
-  } catch (const std::bad_alloc&) {
-    mbf::set_last_error("host allocation failed");
-    return MBF_ERR_OOM;
-  } catch (const std::exception& e) {
-    mbf::set_last_error(e.what());
-    return MBF_ERR_INVALID;
-  }
-}
-
 void msbf_free(mbf_msbf_s* m) {
   if (!m) return;
   if (m->own)
@@ -104,7 +86,7 @@ extern "C" {
 mbf_status mbf_msbf_create(const mbf_op_t* parts, int32_t n_parts, const double* center_kernel,
                            const int64_t* center_index, int64_t n_center_points, int32_t take_ownership,
                            mbf_msbf_t* out) {
-  return mguard([&] {
+  return mbf::abi_guard([&] {
     if (!out || (n_parts > 0 && !parts) || n_parts < 0) fail(MBF_ERR_INVALID, "bad parts");
     if (n_center_points < 0 || (n_center_points > 0 && (!center_kernel || !center_index)))
       fail(MBF_ERR_INVALID, "bad centre");
@@ -138,7 +120,7 @@ mbf_status mbf_msbf_create(const mbf_op_t* parts, int32_t n_parts, const double*
 
 mbf_status mbf_build_msbf(const mbf_problem_t* prob, mbf_entry_fn fn, void* ctx, const mbf_build_opts_t* opts,
                           int32_t n_center, mbf_msbf_t* out) {
-  return mguard([&] {
+  return mbf::abi_guard([&] {
     if (!prob || !fn || !out) fail(MBF_ERR_INVALID, "NULL argument");
     if (prob->dim != 2) fail(MBF_ERR_INVALID, "the multiscale split is two-dimensional (§4)");
     const int n = prob->n;
@@ -212,7 +194,7 @@ mbf_status mbf_build_msbf(const mbf_problem_t* prob, mbf_entry_fn fn, void* ctx,
 }
 
 mbf_status mbf_msbf_apply(mbf_msbf_t m, const void* g, void* u, int64_t nrhs, int32_t precision, void* stream) {
-  return mguard([&] {
+  return mbf::abi_guard([&] {
     if (!m || !g || !u) fail(MBF_ERR_INVALID, "NULL argument");
     if (nrhs < 0 || nrhs > (int64_t(1) << 24)) fail(MBF_ERR_INVALID, "nrhs out of range");
     if (nrhs == 0) return;
@@ -227,7 +209,7 @@ mbf_status mbf_msbf_apply(mbf_msbf_t m, const void* g, void* u, int64_t nrhs, in
 
 mbf_status mbf_msbf_apply_adjoint(mbf_msbf_t m, const void* u, void* g, int64_t nrhs, int32_t precision,
                                   void* stream) {
-  return mguard([&] {
+  return mbf::abi_guard([&] {
     if (!m || !g || !u) fail(MBF_ERR_INVALID, "NULL argument");
     if (nrhs < 0 || nrhs > (int64_t(1) << 24)) fail(MBF_ERR_INVALID, "nrhs out of range");
     if (nrhs == 0) return;
@@ -243,7 +225,7 @@ mbf_status mbf_msbf_apply_adjoint(mbf_msbf_t m, const void* u, void* g, int64_t 
 }
 
 mbf_status mbf_msbf_info(mbf_msbf_t m, mbf_msbf_info_t* info) {
-  return mguard([&] {
+  return mbf::abi_guard([&] {
     if (!m || !info) fail(MBF_ERR_INVALID, "NULL argument");
     *info = mbf_msbf_info_t{};
     info->n_parts = int32_t(m->parts.size());
@@ -264,14 +246,14 @@ mbf_status mbf_msbf_info(mbf_msbf_t m, mbf_msbf_info_t* info) {
 }
 
 mbf_status mbf_msbf_part(mbf_msbf_t m, int32_t i, mbf_op_t* op) {
-  return mguard([&] {
+  return mbf::abi_guard([&] {
     if (!m || !op || i < 0 || i >= int32_t(m->parts.size())) fail(MBF_ERR_INVALID, "bad part index");
     *op = m->parts[size_t(i)];
   });
 }
 
 mbf_status mbf_msbf_destroy(mbf_msbf_t m) {
-  return mguard([&] { msbf_free(m); });
+  return mbf::abi_guard([&] { msbf_free(m); });
 }
 
 }  // extern "C"

@@ -1039,24 +1039,6 @@ void apply_impl(mbf_op_s* op, const void* in, void* out, int64_t nrhs, int32_t p
   prof_end(op, PK_SIMT, e0, st);
 }
 
-template <class F>
-mbf_status guard(F&& fn) {
-  try {
-    fn();
-    g_last_error.clear();
-    return MBF_OK;
-  } catch (const Error& e) {
-    g_last_error = e.what();
-    return e.code;
-  } catch (const std::bad_alloc&) {
-    g_last_error = "host allocation failed";
-    return MBF_ERR_OOM;
-  } catch (const std::exception& e) {
-    g_last_error = e.what();
-    return MBF_ERR_INVALID;
-  }
-}
-
 }  // namespace
 
 void validate(const mbf_factors_t& f) { validate_factors(f); }
@@ -1209,7 +1191,7 @@ const char* mbf_version(void) { return "mbf-gb300 0.1 (sm_103a)"; }
 
 mbf_status mbf_build_factors(const mbf_problem_t* prob, mbf_entry_fn fn, void* ctx,
                              const mbf_build_opts_t* opts, mbf_factors_h* out) {
-  return guard([&] {
+  return abi_guard([&] {
     if (!prob || !out) fail(MBF_ERR_INVALID, "NULL argument");
     mbf_build_opts_t o{};
     if (opts) o = *opts;
@@ -1226,7 +1208,7 @@ mbf_status mbf_build_factors(const mbf_problem_t* prob, mbf_entry_fn fn, void* c
 
 mbf_status mbf_build_from_applies(const mbf_problem_t* prob, mbf_apply_fn fn, void* ctx,
                                   const mbf_build_opts_t* opts, mbf_factors_h* out) {
-  return guard([&] {
+  return abi_guard([&] {
     if (!prob || !out) fail(MBF_ERR_INVALID, "NULL argument");
     mbf_build_opts_t o{};
     if (opts) o = *opts;
@@ -1242,25 +1224,25 @@ mbf_status mbf_build_from_applies(const mbf_problem_t* prob, mbf_apply_fn fn, vo
 }
 
 mbf_status mbf_factors_view(mbf_factors_h f, mbf_factors_t* view) {
-  return guard([&] {
+  return abi_guard([&] {
     if (!f || !view) fail(MBF_ERR_INVALID, "NULL argument");
     *view = f->fs.view();
   });
 }
 
 mbf_status mbf_factors_destroy(mbf_factors_h f) {
-  return guard([&] { delete f; });
+  return abi_guard([&] { delete f; });
 }
 
 mbf_status mbf_factors_save(const mbf_factors_t* f, const char* path) {
-  return guard([&] {
+  return abi_guard([&] {
     if (!f || !path) fail(MBF_ERR_INVALID, "NULL argument");
     save_factors(*f, path);
   });
 }
 
 mbf_status mbf_factors_load(const char* path, mbf_factors_h* out) {
-  return guard([&] {
+  return abi_guard([&] {
     if (!path || !out) fail(MBF_ERR_INVALID, "NULL argument");
     auto* h = new mbf_factors_s();
     try {
@@ -1274,7 +1256,7 @@ mbf_status mbf_factors_load(const char* path, mbf_factors_h* out) {
 }
 
 mbf_status mbf_op_create(const mbf_factors_t* f, mbf_op_t* out) {
-  return guard([&] {
+  return abi_guard([&] {
     if (!f || !out) fail(MBF_ERR_INVALID, "NULL argument");
     *out = op_create(*f);
   });
@@ -1282,7 +1264,7 @@ mbf_status mbf_op_create(const mbf_factors_t* f, mbf_op_t* out) {
 
 mbf_status mbf_build_from_entries(const mbf_problem_t* prob, mbf_entry_fn fn, void* ctx,
                                   const mbf_build_opts_t* opts, mbf_op_t* out) {
-  return guard([&] {
+  return abi_guard([&] {
     if (!prob || !out) fail(MBF_ERR_INVALID, "NULL argument");
     mbf_build_opts_t o{};
     if (opts) o = *opts;
@@ -1303,7 +1285,7 @@ mbf_status mbf_build_from_entries(const mbf_problem_t* prob, mbf_entry_fn fn, vo
 
 mbf_status mbf_op_estimate_error(mbf_op_t op, mbf_entry_fn fn, void* ctx, int32_t n_samples, uint64_t seed,
                                  void* stream, double* eps) {
-  return guard([&] {
+  return abi_guard([&] {
     if (!op) fail(MBF_ERR_INVALID, "NULL operator");
     const double e = estimate_error(op, fn, ctx, n_samples, seed, static_cast<cudaStream_t>(stream));
     if (eps) *eps = e;
@@ -1311,11 +1293,11 @@ mbf_status mbf_op_estimate_error(mbf_op_t op, mbf_entry_fn fn, void* ctx, int32_
 }
 
 mbf_status mbf_op_destroy(mbf_op_t op) {
-  return guard([&] { op_free(op); });
+  return abi_guard([&] { op_free(op); });
 }
 
 mbf_status mbf_op_info(mbf_op_t op, mbf_op_info_t* info) {
-  return guard([&] {
+  return abi_guard([&] {
     if (!op || !info) fail(MBF_ERR_INVALID, "NULL argument");
     std::memset(info, 0, sizeof(*info));
     info->dim = op->d;
@@ -1349,7 +1331,7 @@ mbf_status mbf_op_info(mbf_op_t op, mbf_op_info_t* info) {
 }
 
 mbf_status mbf_op_set_profiling(mbf_op_t op, int32_t enable) {
-  return guard([&] {
+  return abi_guard([&] {
     if (!op) fail(MBF_ERR_INVALID, "NULL operator");
     prof_collect(op);
     op->prof_on = enable != 0;
@@ -1361,7 +1343,7 @@ mbf_status mbf_op_set_profiling(mbf_op_t op, int32_t enable) {
 }
 
 mbf_status mbf_op_profile(mbf_op_t op, mbf_profile_t* out) {
-  return guard([&] {
+  return abi_guard([&] {
     if (!op || !out) fail(MBF_ERR_INVALID, "NULL argument");
     prof_collect(op);
     std::memset(out, 0, sizeof(*out));
@@ -1377,17 +1359,17 @@ mbf_status mbf_op_profile(mbf_op_t op, mbf_profile_t* out) {
 }
 
 mbf_status mbf_apply(mbf_op_t op, const void* g, void* u, int64_t nrhs, int32_t precision, void* stream) {
-  return guard([&] { apply_impl(op, g, u, nrhs, precision, stream, false); });
+  return abi_guard([&] { apply_impl(op, g, u, nrhs, precision, stream, false); });
 }
 
 mbf_status mbf_apply_adjoint(mbf_op_t op, const void* u, void* g, int64_t nrhs, int32_t precision,
                              void* stream) {
-  return guard([&] { apply_impl(op, u, g, nrhs, precision, stream, true); });
+  return abi_guard([&] { apply_impl(op, u, g, nrhs, precision, stream, true); });
 }
 
 mbf_status mbf_apply_host(mbf_op_t op, const void* g_host, void* u_host, int64_t nrhs, int32_t precision,
                           void* stream) {
-  return guard([&] {
+  return abi_guard([&] {
     if (!op || !g_host || !u_host) fail(MBF_ERR_INVALID, "NULL argument");
     if (nrhs <= 0) return;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1430,7 +1412,7 @@ mbf_status mbf_apply_host(mbf_op_t op, const void* g_host, void* u_host, int64_t
 
 mbf_status mbf_apply_host_batch(mbf_op_t op, const void* g_host, void* u_host, int64_t nbatch, int64_t nrhs,
                                 int32_t precision, void* stream) {
-  return guard([&] {
+  return abi_guard([&] {
     if (!op) fail(MBF_ERR_INVALID, "operator is NULL");
     if (nbatch < 0 || nrhs < 0) fail(MBF_ERR_INVALID, "negative count");
     if (nbatch == 0 || nrhs == 0) return;
@@ -1498,11 +1480,11 @@ mbf_status mbf_apply_host_batch(mbf_op_t op, const void* g_host, void* u_host, i
 }
 
 mbf_status mbf_debug_fail_alloc(int64_t after) {
-  return guard([&] { g_alloc_budget.store(after < 0 ? -1 : after); });
+  return abi_guard([&] { g_alloc_budget.store(after < 0 ? -1 : after); });
 }
 
 mbf_status mbf_op_debug_stall(mbf_op_t op, int32_t stage, int64_t wait_ns) {
-  return guard([&] {
+  return abi_guard([&] {
     if (!op) fail(MBF_ERR_INVALID, "NULL operator");
     if (stage >= op->plan.n_stages) fail(MBF_ERR_INVALID, "stall stage beyond the plan");
     if (wait_ns < 0) fail(MBF_ERR_INVALID, "negative wait limit");
@@ -1512,7 +1494,7 @@ mbf_status mbf_op_debug_stall(mbf_op_t op, int32_t stage, int64_t wait_ns) {
 }
 
 mbf_status mbf_op_check(mbf_op_t op, void* stream) {
-  return guard([&] {
+  return abi_guard([&] {
     if (!op) fail(MBF_ERR_INVALID, "NULL operator");
     cuda_check(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)), "cudaStreamSynchronize");
     int st = 0;

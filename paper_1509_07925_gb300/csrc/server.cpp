@@ -512,24 +512,6 @@ struct mbf_server_s {
 
 namespace {
 
-template <class F>
-mbf_status sguard(F&& fn) {
-  try {
-    fn();
-    mbf::set_last_error("");
-    return MBF_OK;
-  } catch (const Error& e) {
-    mbf::set_last_error(e.what());
-    return e.code;
-  } catch (const std::bad_alloc&) {
-    mbf::set_last_error("host allocation failed");
-    return MBF_ERR_OOM;
-  } catch (const std::exception& e) {
-    mbf::set_last_error(e.what());
-    return MBF_ERR_INVALID;
-  }
-}
-
 void server_free(mbf_server_s* s) {
   if (!s) return;
   if (s->worker.joinable()) {
@@ -558,7 +540,7 @@ void server_free(mbf_server_s* s) {
 extern "C" {
 
 mbf_status mbf_server_create(const mbf_server_opts_t* opts, mbf_server_t* out) {
-  return sguard([&] {
+  return mbf::abi_guard([&] {
     if (!out) fail(MBF_ERR_INVALID, "NULL argument");
     auto* s = new mbf_server_s();
     try {
@@ -600,7 +582,7 @@ mbf_status mbf_server_create(const mbf_server_opts_t* opts, mbf_server_t* out) {
 }
 
 mbf_status mbf_submit(mbf_server_t s, mbf_op_t op, const void* g, void* u, int64_t nrhs, mbf_ticket_t* ticket) {
-  return sguard([&] {
+  return mbf::abi_guard([&] {
     if (!s || !op || !g || !u || !ticket) fail(MBF_ERR_INVALID, "NULL argument");
     if (nrhs <= 0 || nrhs > (int64_t(1) << 24)) fail(MBF_ERR_INVALID, "nrhs out of range");
     if (op->device != s->device) fail(MBF_ERR_INVALID, "operator lives on another device");
@@ -629,7 +611,7 @@ mbf_status mbf_submit(mbf_server_t s, mbf_op_t op, const void* g, void* u, int64
 }
 
 mbf_status mbf_poll(mbf_server_t s, mbf_ticket_t ticket, mbf_request_status_t* status) {
-  return sguard([&] {
+  return mbf::abi_guard([&] {
     if (!s || !status) fail(MBF_ERR_INVALID, "NULL argument");
     std::lock_guard<std::mutex> lk(s->mu);
     auto it = s->reqs.find(ticket);
@@ -640,7 +622,7 @@ mbf_status mbf_poll(mbf_server_t s, mbf_ticket_t ticket, mbf_request_status_t* s
 }
 
 mbf_status mbf_server_drain(mbf_server_t s, double timeout_s) {
-  return sguard([&] {
+  return mbf::abi_guard([&] {
     if (!s) fail(MBF_ERR_INVALID, "NULL argument");
     std::unique_lock<std::mutex> lk(s->mu);
     s->cv_work.notify_all();
@@ -651,7 +633,7 @@ mbf_status mbf_server_drain(mbf_server_t s, double timeout_s) {
 }
 
 mbf_status mbf_server_stats(mbf_server_t s, mbf_server_stats_t* out) {
-  return sguard([&] {
+  return mbf::abi_guard([&] {
     if (!s || !out) fail(MBF_ERR_INVALID, "NULL argument");
     std::lock_guard<std::mutex> lk(s->mu);
     *out = s->stats;
@@ -659,11 +641,11 @@ mbf_status mbf_server_stats(mbf_server_t s, mbf_server_stats_t* out) {
 }
 
 mbf_status mbf_server_destroy(mbf_server_t s) {
-  return sguard([&] { server_free(s); });
+  return mbf::abi_guard([&] { server_free(s); });
 }
 
 mbf_status mbf_debug_split_sms(const double* work, int32_t n, int32_t share, int32_t* sms_out) {
-  return sguard([&] {
+  return mbf::abi_guard([&] {
     if (n < 0 || (n > 0 && (!work || !sms_out))) fail(MBF_ERR_INVALID, "NULL argument or negative count");
     if (share < 1) fail(MBF_ERR_INVALID, "share < 1");
     std::vector<double> w(static_cast<size_t>(n));
@@ -679,7 +661,7 @@ mbf_status mbf_debug_split_sms(const double* work, int32_t n, int32_t share, int
 mbf_status mbf_debug_form_batch(const int32_t* ops, const int64_t* nrhs, int64_t n, const double* op_work,
                                 int32_t n_ops, int32_t free_slots, const mbf_server_opts_t* opts,
                                 int32_t* group_of) {
-  return sguard([&] {
+  return mbf::abi_guard([&] {
     if (n < 0 || n_ops < 0 || (n > 0 && (!ops || !nrhs || !group_of)) || (n_ops > 0 && !op_work))
       fail(MBF_ERR_INVALID, "NULL argument or negative count");
     if (free_slots < 1) fail(MBF_ERR_INVALID, "free_slots < 1");

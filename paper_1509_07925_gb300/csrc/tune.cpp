@@ -50,7 +50,7 @@ double time_apply(mbf_op_s* op, const void* g, void* u, int64_t nrhs, int32_t pr
 }  // namespace
 
 extern "C" mbf_status mbf_op_tune(mbf_op_t op, void* stream, mbf_tune_result_t* out) {
-  try {
+  return mbf::abi_guard([&] {
     if (!op || !out) fail(MBF_ERR_INVALID, "NULL argument");
     *out = mbf_tune_result_t{};
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -134,13 +134,5 @@ extern "C" mbf_status mbf_op_tune(mbf_op_t op, void* stream, mbf_tune_result_t* 
       cudaMemset(op->ws.status, 0, sizeof(int));
       fail(MBF_ERR_TIMEOUT, "a device wait gave up while tuning");
     }
-    mbf::set_last_error("");
-    return MBF_OK;
-  } catch (const mbf::Error& e) {
-    mbf::set_last_error(e.what());
-    return e.code;
-  } catch (const std::exception& e) {
-    mbf::set_last_error(e.what());
-    return MBF_ERR_INVALID;
-  }
+  });
 }
