@@ -50,7 +50,8 @@ def parse():
     p.add_argument("--serve-requests", type=int, default=512)
     p.add_argument("--no-small", action="store_true", help="skip the 2-D DFT n = 64 latency leg")
     p.add_argument("--factor-file", default=None,
-                   help="multiscale leg: factor files <path>.t<k> to load (or write) instead of building")
+                   help="factor checkpoint to load (or write) instead of building: the workload's file, "
+                        "or for the multiscale leg the files <path>.t<k>")
     return p.parse_args()
 
 
@@ -181,10 +182,12 @@ def recorded_traffic(workload, nrhs, kernel):
     return ent.get("dram_bytes_per_launch")
 
 
-def build_factors(bd, wl):
+def build_factors(bd, wl, factor_file=None):
+    """Host FP64 construction of the workload's factors; with factor_file, loaded from
+    that checkpoint when it exists (and matches), else built and written there."""
     tree = {"none": bd.MBF_TREE_UNIFORM, "polar": bd.MBF_TREE_POLAR}[wl.transform]
     return bd.HostFactors.build(wl.dim, wl.n, wl.L, wl.r, tree=tree, kernel=wl.kernel,
-                                seed=wl.seed_build)
+                                seed=wl.seed_build, factor_file=factor_file)
 
 
 def oracle_apply_rate(hf, wl, nrhs, budget_s=15.0, threads=None):
@@ -223,7 +226,7 @@ def run_reference(args, rank, world):
     buildlib.build()
     wl = WORKLOADS[args.workload]
     nrhs = args.nrhs or 64
-    hf = build_factors(bd, wl)
+    hf = build_factors(bd, wl, args.factor_file)
     rates = []
     for k in range(args.warmup + args.steps):
         r, sample, cores = oracle_apply_rate(hf, wl, nrhs, budget_s=2.0)
@@ -469,7 +472,7 @@ def main():
         return msbf_bench(args, torch, bd, torch.cuda.current_stream(), peak, peak_kind)
     wl = WORKLOADS[args.workload]
     N = wl.N
-    hf = build_factors(bd, wl)
+    hf = build_factors(bd, wl, args.factor_file)
     op = bd.Operator(hf)
     info = op.info()
     stream = torch.cuda.current_stream()

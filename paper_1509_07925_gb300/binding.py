@@ -334,7 +334,9 @@ class HostFactors:
         return self
 
     # ---- read-only numpy views of the padded arrays (library-built factors)
-    def arrays(self):
+    def arrays(self, copy=True):
+        """The factor set as numpy arrays (the oracle's FactorSet fields); copy=False
+        gives views of the library's arrays, valid until close()."""
         v = self.view
         d, L = v.dim, v.L
         c, h = 2 ** d, L // 2
@@ -344,7 +346,8 @@ class HostFactors:
 
         def carr(p, shape):
             n = int(np.prod(shape))
-            return np.ctypeslib.as_array(p, shape=(2 * n,)).view(np.complex128).reshape(shape).copy()
+            a = np.ctypeslib.as_array(p, shape=(2 * n,)).view(np.complex128).reshape(shape)
+            return a.copy() if copy else a
 
         out = dict(d=d, L=L, n_out=v.n_out, n_in=v.n_in,
                    x_perm=np.ctypeslib.as_array(v.x_perm, shape=(v.n_out,)).copy(),
