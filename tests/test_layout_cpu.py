@@ -72,3 +72,53 @@ def test_layout_arguments(bd):
     with pytest.raises(bd.MbfError):
         bd.layout_apply(hf, complex_normal(fs.n_out, 1, seed=1), path=1, adjoint=True)   # tiles: forward only
     assert bd.layout_apply(hf, np.zeros((0, fs.n_in)), path=0).shape == (0, fs.n_out)
+
+
+def _clustered(nx, nw, lo, side, seed):
+    """X half in a blob, half uniform in [0,1)^2; Omega half near the square's centre, half
+    uniform: ragged trees with empty nodes at every level (compact segments of 0 lines)."""
+    rng = np.random.default_rng(seed)
+    X = np.mod(np.concatenate([rng.normal(0.3, 0.08, (nx // 2, 2)), rng.random((nx - nx // 2, 2))]), 1.0)
+    W = np.concatenate([rng.normal(lo + side / 2, side / 10, (nw // 2, 2)),
+                        rng.uniform(lo, lo + side, (nw - nw // 2, 2))])
+    return X, np.clip(W, lo, lo + side * (1 - 1e-9))
+
+
+def _check_library_factors(bd, hf, rhs=2):
+    from gpu_util import export_factors
+    from oracle import bf as B
+    sb = B.SparseBF(export_factors(hf.arrays()))
+    v = hf.view
+    g = complex_normal(v.n_in, rhs, seed=21)
+    ref = sb.apply(g)
+    for path, tol in ((0, TOL_SIMT), (1, TOL_TILES)):
+        u = bd.layout_apply(hf, g, path=path)
+        for k in range(rhs):
+            assert rel(u[k], ref[k]) <= tol, (path, k, rel(u[k], ref[k]))
+    w = complex_normal(v.n_out, rhs, seed=22)
+    gt = bd.layout_apply(hf, w, path=0, adjoint=True)
+    ref_t = sb.adjoint(w)
+    for k in range(rhs):
+        assert rel(gt[k], ref_t[k]) <= TOL_SIMT
+
+
+def test_layouts_of_explicit_point_sets(bd):
+    """Explicit non-uniform point sets (§2.6): the library's factors on clustered X and
+    Omega, whose trees keep empty nodes."""
+    X, W = _clustered(1500, 1200, -16.0, 32.0, seed=3)
+    hf = bd.HostFactors.build(2, 32, 4, 8, tree=bd.MBF_TREE_POINTS, kernel="dft", x_pts=X, w_pts=W,
+                              w_lo=-16.0, w_side=32.0)
+    _check_library_factors(bd, hf)
+
+
+def test_layouts_of_a_multiscale_corona(bd):
+    """Corona t = 0 of the multiscale split of §4 (n = 64): an Omega tree over a square
+    holding a hole, so that whole subtrees are empty."""
+    from oracle import msbf as MS
+    n, r = 64, 12
+    coronas, _ = MS.corona_sets(n, 16)
+    t, idx = coronas[0]
+    half = n / 2 ** (t + 1)
+    hf = bd.HostFactors.build(2, n, 4, r, tree=bd.MBF_TREE_SQUARE, kernel="fio_iso", seed=7 + 101 * (t + 1),
+                              w_index=idx, w_lo=-half, w_side=2 * half)
+    _check_library_factors(bd, hf)
