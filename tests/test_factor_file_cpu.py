@@ -187,3 +187,16 @@ def test_build_option_rejects_a_checkpoint_of_another_kernel(bd, tmp_path):
     with pytest.raises(bd.MbfError) as e:
         bd.HostFactors.build(2, 16, 2, 8, kernel="dft", factor_file=p)
     assert e.value.code == bd.MBF_ERR_INVALID and "no kernel record" in str(e.value)
+
+
+def test_array_views_equal_the_copies(bd):
+    """HostFactors.arrays(copy=False) gives views of the library's arrays (no second copy
+    of a large factor set) with the same contents as the copies."""
+    hf = bd.HostFactors.build(2, 32, 4, 8, tree=bd.MBF_TREE_POLAR, kernel="fio_iso", seed=3)
+    a, v = hf.arrays(), hf.arrays(copy=False)
+    for key in ("UL", "VL", "S", "x_perm", "w_off"):
+        assert np.array_equal(a[key], v[key]), key
+    for q in range(len(a["G"])):
+        assert np.array_equal(a["G"][q], v["G"][q]) and np.array_equal(a["H"][q], v["H"][q])
+    assert not v["G"][0].flags["OWNDATA"] and a["G"][0].flags["OWNDATA"]
+    hf.close()
