@@ -478,12 +478,13 @@ mbf_status mbf_debug_split_sms(const double* work, int32_t n, int32_t share, int
 /* Host interpreter of the packed device layouts (for tests of the packers without a
  * device): packs the factor set on the host exactly as mbf_op_create does before it
  * uploads, then applies the packed data in FP64 as the layout defines it.  path 0: the
- * FP32 SIMT arena (items of complex64 entries), forward (adjoint = 0, eq. gbf) or
- * adjoint (1); path 1: the tensor path, forward only: the split-BF16 tiles of the G / H
- * levels (each entry hi + lo) with the leaf items of the SIMT arena.  in / out: host
+ * FP32 SIMT arena (items of complex64 entries); path 1: the tensor path, the split-BF16
+ * tiles of the G / H levels (each entry hi + lo) with the leaf items of the SIMT arena, the
+ * adjoint through the adjoint tile plan with the tiles read conjugate-transposed.  Forward
+ * (adjoint = 0, eq. gbf) or adjoint (1).  in / out: host
  * complex128 (interleaved doubles), [nrhs][n_in] -> [nrhs][n_out] (adjoint: n_out ->
  * n_in), out fully overwritten.  MBF_ERR_INVALID for an invalid factor set, a tensor
- * path the tiles do not fit (the reason in mbf_last_error), or a packed layout that
+ * path (or adjoint) the tiles do not fit (the reason in mbf_last_error), or a packed layout that
  * breaks its own definition (an entry outside the arena, a nonzero in the tiles' rank
  * padding, a leaf point outside its group). */
 mbf_status mbf_debug_layout_apply(const mbf_factors_t* f, int32_t path, int32_t adjoint, const void* in,

@@ -629,8 +629,8 @@ class MsBF:
 
 def layout_apply(factors, g, path=0, adjoint=False):
     """Host FP64 apply of the packed device layout (mbf_debug_layout_apply): path 0 the
-    SIMT arena (forward or adjoint), path 1 the tensor tiles (forward).  g: complex
-    [nrhs, n] -> complex128 [nrhs, n']."""
+    SIMT arena, path 1 the tensor tiles; forward or adjoint.  g: complex [nrhs, n] ->
+    complex128 [nrhs, n']."""
     g = np.ascontiguousarray(np.atleast_2d(g), dtype=np.complex128)
     v = factors.view
     n_dst = v.n_in if adjoint else v.n_out

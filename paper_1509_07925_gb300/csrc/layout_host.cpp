@@ -255,6 +255,65 @@ struct Interp {
       std::swap(cur, nxt);
     }
   }
+
+  // Tensor adjoint: (U^L)^* from the leaf items of the last stage, then the stages of the
+  // adjoint plan, stage e reading forward stage S - 1 - e's tile of the same group
+  // conjugate-transposed (the device converts the tiles once; here they are read in
+  // place), then V^L to natural Omega order.
+  void tc_adjoint(const cd* u, cd* g) const {
+    const mbf::TCPlan& fp = ph.tcplan;
+    const mbf::TCPlan& ap = ph.tcplan_adj;
+    const int S = ph.plan.n_stages;
+    if (ap.n_stages != fp.n_stages || ap.n_stages != S - 1) fail(MBF_ERR_INVALID, "layout: adjoint plan size");
+    std::vector<cd> cur(size_t(nL * rmax), 0.0), nxt(cur.size());
+    const Stage& sl = ph.plan.st[S - 1];
+    const TCStage& a0 = ap.st[0];
+    for (int64_t grp = 0; grp < sl.n_groups; ++grp) {
+      const Item& lx = item(sl, grp, 1);
+      for (int a = 0; a < (lx.nlines ? lx.len : 0); ++a) {
+        const int64_t p = lx.base + a;
+        const int t = leaf_child(f.x_off, grp, c, p);
+        const int64_t o = seg(a0.in_pat, grp, t, a0.B, a0.ch, a0.R_in, c);
+        for (int k = 0; k < lx.nlines; ++k) cur[size_t(o + k)] += std::conj(item_at(ph.arena, lx, k, a)) * u[f.x_perm[p]];
+      }
+    }
+    for (int e = 0; e < ap.n_stages; ++e) {
+      const TCStage& as = ap.st[e];
+      const TCStage& fs = fp.st[fp.n_stages - 1 - e];
+      if (as.M_t != fs.K_t || as.K_pad != fs.M_t || as.R_in != fs.R_out || as.R_out != fs.R_in ||
+          as.R8_in != fs.R8_out || as.R8_out != fs.R8_in || as.in_pat != fs.out_pat || as.out_pat != fs.in_pat ||
+          as.B != fs.B || as.ch != fs.ch || as.n_groups != fs.n_groups)
+        fail(MBF_ERR_INVALID, "layout: adjoint stage is not the transposed forward stage");
+      std::fill(nxt.begin(), nxt.end(), cd(0.0));
+      std::vector<cd> y(size_t(as.M_t));
+      for (int64_t grp = 0; grp < as.n_groups; ++grp) {
+        const uint8_t* tile = ph.tc_arena.data() + size_t(fs.base) + size_t(grp) * size_t(fs.tile_bytes);
+        std::fill(y.begin(), y.end(), cd(0.0));
+        for (int k = 0; k < as.K_pad; ++k) {
+          const int tp = k / as.R8_in, kk = k % as.R8_in;
+          if (kk >= as.R_in) continue;
+          const cd x = cur[size_t(seg(as.in_pat, grp, tp, as.B, as.ch, as.R_in, c) + kk)];
+          for (int m = 0; m < as.M_t; ++m) y[size_t(m)] += std::conj(tile_at(tile, fs, k, m)) * x;
+        }
+        if (as.last) {   // V^L: the leaf stage's items hold conj(V)
+          const Stage& s0 = ph.plan.st[0];
+          const Item& it = item(s0, grp, 0);
+          for (int b = 0; b < it.nlines; ++b) {
+            const int64_t p = it.base + b;
+            const int t = leaf_child(f.w_off, grp, c, p);
+            cd s = 0;
+            for (int k = 0; k < it.len; ++k) s += std::conj(item_at(ph.arena, it, b, k)) * y[size_t(t * as.R8_out + k)];
+            g[f.w_perm[p]] += s;
+          }
+        } else {
+          for (int t = 0; t < c; ++t)
+            for (int k2 = 0; k2 < as.R_out; ++k2)
+              nxt[size_t(seg(as.out_pat, grp, t, as.B, as.ch, as.R_out, c) + k2)] += y[size_t(t * as.R8_out + k2)];
+        }
+      }
+      std::swap(cur, nxt);
+    }
+  }
 };
 
 }  // namespace
@@ -267,10 +326,11 @@ mbf_status mbf_debug_layout_apply(const mbf_factors_t* f, int32_t path, int32_t 
     if (!f || (nrhs > 0 && (!in || !out))) fail(MBF_ERR_INVALID, "NULL argument");
     if (nrhs < 0) fail(MBF_ERR_INVALID, "nrhs < 0");
     if (path != 0 && path != 1) fail(MBF_ERR_INVALID, "path must be 0 (SIMT arena) or 1 (tensor tiles)");
-    if (path == 1 && adjoint) fail(MBF_ERR_INVALID, "the tile interpreter is forward only");
     mbf::PackedHost ph;
     mbf::pack_host(*f, ph);
     if (path == 1 && !ph.tc_unavailable.empty()) fail(MBF_ERR_INVALID, "tensor tiles unavailable: " + ph.tc_unavailable);
+    if (path == 1 && adjoint && !ph.tc_adj_unavailable.empty())
+      fail(MBF_ERR_INVALID, "tensor adjoint unavailable: " + ph.tc_adj_unavailable);
     const Interp ip(*f, ph);
     const int64_t n_src = adjoint ? f->n_out : f->n_in, n_dst = adjoint ? f->n_in : f->n_out;
     const cd* src = static_cast<const cd*>(in);
@@ -279,7 +339,7 @@ mbf_status mbf_debug_layout_apply(const mbf_factors_t* f, int32_t path, int32_t 
       cd* o = dst + r * n_dst;
       std::fill(o, o + n_dst, cd(0.0));
       if (path == 1)
-        ip.tc_forward(src + r * n_src, o);
+        adjoint ? ip.tc_adjoint(src + r * n_src, o) : ip.tc_forward(src + r * n_src, o);
       else if (adjoint)
         ip.simt_adjoint(src + r * n_src, o);
       else

@@ -348,6 +348,33 @@ void pack_tc(const mbf_factors_t& f, const Plan& sp, TCPlan& tp, std::vector<uin
   tp.n_stages = n;
 }
 
+// The tensor adjoint's plan: stage e of it is forward stage S - 1 - e with its tile
+// conjugate-transposed (M_t <-> K_t), reading where the forward stage writes and writing
+// where it reads (same pattern parameters).  Throws where a forward tile's shape has no
+// adjoint tile of the same bytes (K_pad != K_t).
+void adjoint_tile_plan(const TCPlan& fp, TCPlan& ap) {
+  ap = fp;
+  for (int e = 0; e < fp.n_stages; ++e) {
+    const TCStage& fs = fp.st[fp.n_stages - 1 - e];
+    TCStage& as = ap.st[e];
+    as = fs;
+    as.M_t = fs.K_t;
+    as.K_t = fs.M_t;
+    as.K_pad = fs.M_t;
+    as.in_pat = fs.out_pat;
+    as.out_pat = fs.in_pat;
+    as.R_in = fs.R_out;
+    as.R_out = fs.R_in;
+    as.R8_in = fs.R8_out;
+    as.R8_out = fs.R8_in;
+    as.plane_bytes = as.M_t * 32;
+    as.last = e == fp.n_stages - 1;
+    if (fs.K_pad != fs.K_t || as.M_t > kTcMaxRows || as.K_pad % 16 != 0 ||
+        int64_t(as.K_pad / 16) * 4 * as.plane_bytes != fs.tile_bytes)
+      fail(MBF_ERR_INVALID, "tile shape not supported by the tensor adjoint");
+  }
+}
+
 void validate_factors(const mbf_factors_t& f) {
   if (f.dim != 2 && f.dim != 3) fail(MBF_ERR_INVALID, "dim must be 2 or 3");
   if (f.L < 2 || f.L % 2 || f.L > 20) fail(MBF_ERR_INVALID, "L must be even, 2..20");
@@ -655,32 +682,10 @@ mbf_op_s* op_create(const mbf_factors_t& f) {
         sm = std::max(smem(nsa), size_t(optin) / 2 + 1024);
       };
       config(op->tc_mt_max, op->tc_kpad_max, op->tc_nsets, op->tc_nxb, op->tc_nsa, op->tc_smem);
-      // the adjoint plan: stage e of it is forward stage S - 1 - e with its tile
-      // conjugate-transposed (M_t <-> K_t), reading where the forward stage writes and
-      // writing where it reads (same pattern parameters)
+      // the tensor adjoint: its plan (adjoint_tile_plan) and launch configuration
       try {
-        const TCPlan& fp = op->tcplan;
-        TCPlan& ap = op->tcplan_adj;
-        ap = fp;
-        for (int e = 0; e < fp.n_stages; ++e) {
-          const TCStage& fs = fp.st[fp.n_stages - 1 - e];
-          TCStage& as = ap.st[e];
-          as = fs;
-          as.M_t = fs.K_t;
-          as.K_t = fs.M_t;
-          as.K_pad = fs.M_t;
-          as.in_pat = fs.out_pat;
-          as.out_pat = fs.in_pat;
-          as.R_in = fs.R_out;
-          as.R_out = fs.R_in;
-          as.R8_in = fs.R8_out;
-          as.R8_out = fs.R8_in;
-          as.plane_bytes = as.M_t * 32;
-          as.last = e == fp.n_stages - 1;
-          if (fs.K_pad != fs.K_t || as.M_t > kTcMaxRows || as.K_pad % 16 != 0 ||
-              int64_t(as.K_pad / 16) * 4 * as.plane_bytes != fs.tile_bytes)
-            fail(MBF_ERR_INVALID, "tile shape not supported by the tensor adjoint");
-        }
+        const TCPlan& ap = op->tcplan_adj;
+        adjoint_tile_plan(op->tcplan, op->tcplan_adj);
         op->tca_mt_max = op->tc_kpad_max;
         op->tca_kpad_max = op->tc_mt_max;
         if (!leaf_fits(ap.st[0].R8_in, op->c) || leaf_smem_bytes(op->RV[size_t(op->L)], op->c, true) > size_t(optin) ||
@@ -1125,6 +1130,12 @@ void pack_host(const mbf_factors_t& f, PackedHost& out) {
   } catch (const Error& err) {
     out.tc_unavailable = err.what();
     out.tc_arena.clear();
+    return;
+  }
+  try {
+    adjoint_tile_plan(out.tcplan, out.tcplan_adj);
+  } catch (const Error& err) {
+    out.tc_adj_unavailable = err.what();
   }
 }
 

@@ -140,7 +140,8 @@ struct PackedHost {
   std::vector<uint8_t> arena;
   TCPlan tcplan{};
   std::vector<uint8_t> tc_arena;
-  std::string simt_unavailable, tc_unavailable;
+  TCPlan tcplan_adj{};   // the tensor adjoint's plan over the same tiles, transposed
+  std::string simt_unavailable, tc_unavailable, tc_adj_unavailable;
 };
 void pack_host(const mbf_factors_t& f, PackedHost& out);
 // The error estimator of §3.3 (estimate.cpp); keeps the result in op->eps.

@@ -1,8 +1,8 @@
 """The packed device layouts checked on the CPU (mbf_debug_layout_apply): the factor
 set is packed on the host by the same packers mbf_op_create uses, and the packed data
 applied in FP64 as the layout defines it must give the oracle's FP64 apply of the same
-factors.  Path 0 is the FP32 SIMT arena (forward and adjoint); path 1 the split-BF16x3
-tiles of the tensor path (forward), whose rank padding must hold zeros.  The cases span
+factors.  Path 0 is the FP32 SIMT arena, path 1 the split-BF16x3 tiles of the tensor path
+(whose rank padding must hold zeros) with the adjoint plan over them; forward and adjoint.  The cases span
 2-D / 3-D, uniform and polar Omega trees (ragged and empty leaves), the corner turn with
 S folded into G^h, several tile chunks and the largest tile (c r = 256)."""
 import numpy as np
@@ -53,7 +53,9 @@ def test_simt_arena_forward_and_adjoint(bd, case):
 
 
 @pytest.mark.parametrize("case", CASES)
-def test_tensor_tiles_forward(bd, case):
+def test_tensor_tiles_forward_and_adjoint(bd, case):
+    """Forward through the tile plan; adjoint through the adjoint plan over the same tiles
+    read conjugate-transposed (stage e of it = forward stage S - 1 - e)."""
     fs, sb = oracle_case(*case)
     hf = import_factors(bd, fs)
     g = complex_normal(fs.n_in, 2, seed=13)
@@ -61,6 +63,11 @@ def test_tensor_tiles_forward(bd, case):
     ref = sb.apply(g)
     for k in range(2):
         assert rel(u[k], ref[k]) <= TOL_TILES, (k, rel(u[k], ref[k]))
+    w = complex_normal(fs.n_out, 2, seed=14)
+    gt = bd.layout_apply(hf, w, path=1, adjoint=True)
+    ref_t = sb.adjoint(w)
+    for k in range(2):
+        assert rel(gt[k], ref_t[k]) <= TOL_TILES, (k, rel(gt[k], ref_t[k]))
 
 
 def test_layout_arguments(bd):
@@ -70,7 +77,7 @@ def test_layout_arguments(bd):
     with pytest.raises(bd.MbfError):
         bd.layout_apply(hf, g, path=2)
     with pytest.raises(bd.MbfError):
-        bd.layout_apply(hf, complex_normal(fs.n_out, 1, seed=1), path=1, adjoint=True)   # tiles: forward only
+        bd.layout_apply(hf, complex_normal(fs.n_out, 1, seed=1), path=-1, adjoint=True)
     assert bd.layout_apply(hf, np.zeros((0, fs.n_in)), path=0).shape == (0, fs.n_out)
 
 
@@ -96,10 +103,11 @@ def _check_library_factors(bd, hf, rhs=2):
         for k in range(rhs):
             assert rel(u[k], ref[k]) <= tol, (path, k, rel(u[k], ref[k]))
     w = complex_normal(v.n_out, rhs, seed=22)
-    gt = bd.layout_apply(hf, w, path=0, adjoint=True)
     ref_t = sb.adjoint(w)
-    for k in range(rhs):
-        assert rel(gt[k], ref_t[k]) <= TOL_SIMT
+    for path, tol in ((0, TOL_SIMT), (1, TOL_TILES)):
+        gt = bd.layout_apply(hf, w, path=path, adjoint=True)
+        for k in range(rhs):
+            assert rel(gt[k], ref_t[k]) <= tol, (path, k, rel(gt[k], ref_t[k]))
 
 
 def test_layouts_of_explicit_point_sets(bd):
