@@ -202,6 +202,12 @@ mbf_status mbf_factors_load(const char* path, mbf_factors_h* out);
  * layout on the current CUDA device and return a resident operator.  The factor
  * arrays are only read during the call. */
 mbf_status mbf_op_create(const mbf_factors_t* f, mbf_op_t* out);
+/* The device bytes the packed factors of f will take, without a device: *simt_bytes the
+ * FP32 SIMT arena and its item table, *tensor_bytes the split-BF16 tiles (0 when the
+ * tensor path cannot take the operator).  The tensor adjoint adds tensor_bytes again on
+ * its first use, TF32 applies likewise; workspaces come on top.  Packs on the host to
+ * count (host memory and time of the packing itself).  Either pointer may be NULL. */
+mbf_status mbf_factors_device_bytes(const mbf_factors_t* f, int64_t* simt_bytes, int64_t* tensor_bytes);
 /* mbf_build_factors + mbf_op_create + mbf_factors_destroy, then the error estimate
  * below on 256 sampled outputs (needs the device; kept for mbf_op_info). */
 mbf_status mbf_build_from_entries(const mbf_problem_t* prob, mbf_entry_fn fn, void* ctx,

@@ -161,6 +161,7 @@ SIGNATURES = {
                                        C.c_int32, C.c_int32, C.POINTER(ServerOpts), C.POINTER(C.c_int32)]),
     "mbf_debug_split_sms": (C.c_int, [C.POINTER(C.c_double), C.c_int32, C.c_int32, C.POINTER(C.c_int32)]),
     "mbf_debug_layout_apply": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_int64]),
+    "mbf_factors_device_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "mbf_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                              C.POINTER(C.c_int64)]),
     "mbf_poll": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(RequestStatus)]),
@@ -362,6 +363,13 @@ class HostFactors:
         out["H"] = [carr(v.H[q], (c ** l, c ** (L - l - 1), c, RV[l + 1], c, RV[l]))
                     for q, l in enumerate(range(h, L))]
         return out
+
+    def device_bytes(self):
+        """(SIMT arena + item table, tensor tiles) bytes an operator of these factors takes
+        on the device (mbf_factors_device_bytes; no device needed)."""
+        a, b = C.c_int64(), C.c_int64()
+        _check(lib().mbf_factors_device_bytes(C.byref(self.view), C.byref(a), C.byref(b)))
+        return a.value, b.value
 
     def close(self):
         if self._handle is not None:

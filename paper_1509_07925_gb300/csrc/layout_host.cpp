@@ -348,4 +348,14 @@ mbf_status mbf_debug_layout_apply(const mbf_factors_t* f, int32_t path, int32_t 
   });
 }
 
+mbf_status mbf_factors_device_bytes(const mbf_factors_t* f, int64_t* simt_bytes, int64_t* tensor_bytes) {
+  return mbf::abi_guard([&] {
+    if (!f) fail(MBF_ERR_INVALID, "NULL argument");
+    mbf::PackedHost ph;
+    mbf::pack_host(*f, ph);
+    if (simt_bytes) *simt_bytes = int64_t(ph.arena.size() + ph.items.size() * sizeof(Item));
+    if (tensor_bytes) *tensor_bytes = ph.tc_unavailable.empty() ? int64_t(ph.tc_arena.size()) : 0;
+  });
+}
+
 }  // extern "C"

@@ -130,3 +130,28 @@ def test_layouts_of_a_multiscale_corona(bd):
     hf = bd.HostFactors.build(2, n, 4, r, tree=bd.MBF_TREE_SQUARE, kernel="fio_iso", seed=7 + 101 * (t + 1),
                               w_index=idx, w_lo=-half, w_side=2 * half)
     _check_library_factors(bd, hf)
+
+
+@pytest.mark.parametrize("case", [CASES[1], CASES[2], CASES[3]])
+def test_device_bytes_before_creation(bd, case):
+    """mbf_factors_device_bytes: the tiles take sum over the 2 (L - h) G / H stages of
+    c^(L-1) groups x (K_pad / 16) chunks x 4 planes x M_t rows x 32 bytes (M_t = c R8_out,
+    K_pad = c R8_in rounded up to 16); the SIMT arena holds at least 8 bytes per nonzero
+    and at most the full blocks' lines (2 x 4 bytes per entry, plus chunk padding)."""
+    fs, _ = oracle_case(*case)
+    hf = import_factors(bd, fs)
+    simt, tc = hf.device_bytes()
+    c, L = 2 ** fs.d, fs.L
+    h = L // 2
+    r8 = lambda r: (int(r) + 7) // 8 * 8
+    want = 0
+    for l in range(h, L):
+        for R_in, R_out in ((fs.RV[l + 1], fs.RV[l]), (fs.RU[l], fs.RU[l + 1])):
+            M_t, K_pad = c * r8(R_out), (c * r8(R_in) + 15) // 16 * 16
+            want += c ** (L - 1) * (K_pad // 16) * 4 * M_t * 32
+    assert tc == want
+    nnz = sum(int(np.count_nonzero(a)) for a in list(fs.G) + list(fs.H) + [fs.UL, fs.VL])
+    full = sum(c ** (L - 1) * (c * int(fs.RV[l + 1])) * (c * int(fs.RV[l])) +
+               c ** (L - 1) * (c * int(fs.RU[l])) * (c * int(fs.RU[l + 1])) for l in range(h, L))
+    full += fs.UL.size + fs.VL.size
+    assert 8 * nnz <= simt <= 8 * full * 1.1 + 16 * 4 * c ** L
